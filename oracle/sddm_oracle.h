@@ -1,0 +1,107 @@
+/*
+ * FP64 CPU oracle of the spectral domain-decomposition path tracer
+ * (Gbikpi-Benissan, Callet, Magoules, arXiv:1912.06474).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or
+ * load this code: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do. It shares no source, header, table or helper with the
+ * CUDA path; the two meet only in the seeded input arrays.
+ *
+ * What it computes, in the paper's terms:
+ *   - Eq. 1: complex index n + ik feeding Fresnel's equations for metals and
+ *     glass (Sec. 2), the glass as an absorbing slab with multiple internal
+ *     reflections; coloration state s sets the absorption alpha + s*dalpha.
+ *   - Eq. 2 estimated by Monte Carlo path tracing (Sec. 4), Eq. 3's light sum
+ *     as next-event estimation toward area lights, shadow rays to the light
+ *     (Sec. 4, "Local illumination"), reflection/refraction continuation and a
+ *     bounce limit (same passage).
+ *   - The domain decomposition of Sec. 5 hands a ray on across interfaces with
+ *     its properties unchanged, so its closest hit is that of a single global
+ *     domain: the oracle traces against one global structure (FP64 median-split
+ *     BVH, or brute force over all triangles).
+ *
+ * Every floating-point quantity is double except the glass branch proxy, which
+ * decides an integer (reflect or transmit) and is therefore evaluated in the
+ * kernel's precision (float, no contraction), and the inputs, which are the
+ * caller's float32 arrays widened to double.
+ *
+ * Parity unpinned: the bit-level Philox4x32-10 definition (no known-answer
+ * vectors are available offline; the stream is pinned statistically only).
+ */
+#ifndef SDDM_ORACLE_H
+#define SDDM_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_LAMBERT = 0, ORC_CONDUCTOR = 1, ORC_GLASS = 2, ORC_EMITTER = 3, ORC_DIFFUSE_EMITTER = 4 };
+
+/* Scene as plain arrays (the caller keeps ownership; everything is copied). */
+typedef struct {
+    int L;
+    const float *lam_nm;      /* [L] */
+    const float *quad_w;      /* [L] nm */
+    const float *cmf;         /* [L][3] */
+    int n_mat;
+    const int32_t *mat_kind;  /* [n_mat] */
+    const float *mat_a;       /* [n_mat][L]: rho | n | n (glass) | Le (emitters) */
+    const float *mat_b;       /* [n_mat][L]: -   | k | alpha_clear | rho (diffuse emitter) */
+    const float *mat_c;       /* [n_mat][L]: -   | - | dalpha      | - */
+    const float *mat_thick;   /* [n_mat] slab thickness, m */
+    const float *mat_s;       /* [n_mat] default coloration state */
+    int nv;
+    const float *V;           /* [nv][3] */
+    int nt;
+    const uint32_t *F;        /* [nt][3] */
+    const uint32_t *mat_id;   /* [nt] */
+    const uint32_t *obj_id;   /* [nt] */
+} orc_scene_desc;
+
+typedef struct {
+    int width, height, spp, max_depth;
+    uint32_t seed, render_id;
+    int nee;                  /* 1: next-event estimation on; 0: emission counted at every vertex */
+    double cam_pos[3], cam_look[3], cam_up[3];
+    double vfov_deg;
+    double ortho_height;      /* > 0: orthographic camera of this height */
+    const float *s_override;  /* [n_mat] or NULL; a negative entry keeps the default */
+    int brute_force;          /* 1: test every triangle and compute decision margins */
+} orc_render_desc;
+
+int  orc_create(void **out, const orc_scene_desc *d);
+void orc_destroy(void *ctx);
+
+/* Mean XYZ over spp for each listed pixel (linear index y*W+x).
+ * xyz_out [n_pix][3]; optional per-sample outputs (NULL to skip):
+ *   sample_xyz [n_pix][spp][3], first_prim [n_pix][spp] (-1 = miss),
+ *   margin [n_pix][spp] (smallest decision margin on the path; brute_force only).
+ * seg_out[0] += extension segments, seg_out[1] += shadow segments. */
+int orc_render_pixels(void *ctx, const orc_render_desc *r, int64_t n_pix, const int64_t *pix,
+                      double *xyz_out, double *sample_xyz, int32_t *first_prim, double *margin,
+                      int n_threads, int64_t *seg_out);
+
+/* Test hooks ------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u01(uint32_t x);
+void orc_fresnel(double c, double n, double k, double *Rs, double *Rp);
+void orc_slab(double c, double lam_nm, double n, double alpha_per_m, double thick_m,
+              double *R, double *T);
+double orc_conductor(double c, double n, double k);
+float orc_branch_proxy(float c, int L, const float *n);
+void orc_cosine_dir(const double ns[3], double u0, double u1, double out[3]);
+void orc_camera_ray(const orc_render_desc *r, double px, double py, double o[3], double d[3]);
+/* Closest hit of one ray; returns the triangle id or -1; t_out, b_out[3] barycentrics. */
+int orc_closest_hit(void *ctx, const double o[3], const double d[3], int brute_force,
+                    double *t_out, double b_out[3]);
+/* Shadow query: returns 1 if occluded; crossings (object, cos) written to cross_obj/cross_cos. */
+int orc_shadow(void *ctx, const double o[3], const double d[3], double tmax, int excl_prim,
+               int brute_force, int *n_cross, int32_t cross_obj[4], double cross_cos[4]);
+int orc_num_lights(void *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
