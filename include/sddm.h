@@ -1,0 +1,219 @@
+/*
+ * sddm.h -- C ABI of libsddm.so, a GB300 (sm_103a) spectral path tracer whose
+ * ray tracing is parallelised by domain decomposition, after
+ * Gbikpi-Benissan, Callet, Magoules, "Spectral domain decomposition method for
+ * physically-based rendering of photochromic/electrochromic glass windows"
+ * (arXiv:1912.06474).
+ *
+ * The problem, as the paper states it (Sec. 1, Sec. 2, Sec. 6): render a room
+ * under natural light from the materials' optical properties -- spectral
+ * reflectance, complex index n + ik (Eq. 1) for metals and glass, glass panes
+ * whose absorption depends on a coloration state -- through the rendering
+ * equation (Eq. 2) with its light-source sum (Eq. 3), by ray tracing (Sec. 4),
+ * parallelised by splitting the scene into subdomains that hand rays to each
+ * other across interfaces (Sec. 5).
+ *
+ * Conventions for every call:
+ *   - returns SDDM_OK (0) or a negative sddm_status; never aborts or traps;
+ *   - sddm_last_error() gives a message for the calling thread's last failure;
+ *   - host arrays are read during the call and copied; the caller keeps them;
+ *   - pointers documented as DEVICE are caller-owned device memory of the
+ *     context's device (e.g. a PyTorch tensor's data_ptr());
+ *   - a stream is a cudaStream_t passed as void* (NULL = legacy default);
+ *   - units: metres, nanometres, 1/m for absorption; all floats are FP32.
+ * A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SDDM_H
+#define SDDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sddm_ctx sddm_ctx;
+
+typedef enum {
+    SDDM_OK = 0,
+    SDDM_ERR_INVALID_ARG = -1,     /* argument out of range, NULL, inconsistent sizes */
+    SDDM_ERR_OOM = -2,             /* host or device allocation failed */
+    SDDM_ERR_CUDA = -3,            /* a CUDA runtime call failed (message has the CUDA error) */
+    SDDM_ERR_QUEUE_OVERFLOW = -4,  /* a subdomain ray queue filled up; rebuild with more capacity */
+    SDDM_ERR_TIMEOUT = -5,         /* a device wait hit its iteration cap; the kernel returned */
+    SDDM_ERR_NOT_BUILT = -6,       /* sddm_render before sddm_build, or after the scene changed */
+    SDDM_ERR_MLP_UNTRAINED = -7,   /* SDDM_BSDF_MLP requested with no trained weights */
+    SDDM_ERR_DEVICE_CHECK = -8     /* a device-side bounds check tripped (no access was made) */
+} sddm_status;
+
+typedef enum { SDDM_BSDF_EXACT = 0, SDDM_BSDF_MLP = 1 } sddm_bsdf_mode;
+
+typedef enum {
+    SDDM_METHOD_MEGAKERNEL = 0,    /* one thread per path over the global BVH (Sec. 5, classical split) */
+    SDDM_METHOD_DDM = 1            /* subdomain queues drained by persistent blocks (Sec. 5, DDM) */
+} sddm_method;
+
+/* Acceleration structure and scheduling options (sddm_build). */
+typedef struct {
+    int grid[3];              /* subdomains per axis, each >= 1; {1,1,1} = a single domain */
+    int leaf_size;            /* max triangles per BVH leaf, 1..15 (0 = 4) */
+    int sah_bins;             /* binned-SAH bins per axis, 4..64 (0 = 16) */
+    int64_t queue_capacity;   /* rays per subdomain queue (0 = automatic) */
+    int blocks_per_sm;        /* persistent blocks per SM for the DDM trace (0 = automatic) */
+    int64_t paths_in_flight;  /* path slots processed at once (0 = automatic) */
+} sddm_build_opts;
+
+typedef struct {
+    float pos[3], look[3], up[3];
+    float vfov_deg;           /* vertical field of view of the pinhole camera */
+    float ortho_height;       /* > 0: orthographic camera of this image-plane height (Sec. 4) */
+} sddm_camera;
+
+/* One render of the scene. Several renders may go to one sddm_render call
+ * (one batched launch); they must share method and bsdf_mode. */
+typedef struct {
+    int width, height, spp;   /* >= 1 each */
+    int max_depth;            /* path vertices, 1..64 (Sec. 4's bounce limit) */
+    uint32_t seed;            /* Philox key word 0 */
+    uint32_t render_id;       /* Philox key word 1 */
+    int nee;                  /* 1: shadow rays to the lights (Eq. 3); 0: emission counted at every vertex */
+    int bsdf_mode;            /* sddm_bsdf_mode for glass slabs */
+    int method;               /* sddm_method */
+    sddm_camera camera;
+    const float *glass_s;     /* HOST [n_materials] coloration state per material, entries < 0 keep
+                                 the material's default; NULL = all defaults */
+    float *xyz_out;           /* DEVICE [height][width][3] CIE XYZ, mean over spp (written) */
+    float *aov_sample_xyz;    /* DEVICE optional [height*width*spp][3] per-sample XYZ, sample-minor */
+    int32_t *aov_first_prim;  /* DEVICE optional [height*width*spp] first-hit triangle id, -1 = miss */
+} sddm_render_desc;
+
+/* Counters of the last sddm_render (all renders of the call). */
+typedef struct {
+    int64_t paths;
+    int64_t segments_ext;     /* closest-hit queries (one per path vertex reached) */
+    int64_t segments_shadow;  /* shadow (any-hit) queries */
+    int64_t crossings;        /* DDM interface hand-offs between subdomains */
+    int64_t glass_queries;    /* glass slab (R,T) evaluations, per hit (all bins) */
+    int64_t mlp_fallbacks;    /* MLP batches that fell back to the exact slab */
+    double gpu_ms;            /* device time of the whole call, CUDA events on the context stream */
+    int64_t kernel_launches;  /* kernels this call launched */
+    double trace_ms;          /* SDDM_PROFILE_TIME_TRACE: summed device time of the trace kernels */
+    int64_t trace_launches;   /* SDDM_PROFILE_TIME_TRACE: launches those times cover */
+    int64_t node_visits;      /* SDDM_PROFILE_COUNT_TRAVERSAL: BVH interior nodes visited */
+    int64_t tri_tests;        /* SDDM_PROFILE_COUNT_TRAVERSAL: ray/triangle tests */
+    int64_t ray_visits;       /* SDDM_PROFILE_COUNT_TRAVERSAL: (ray, subdomain) visits traced */
+} sddm_stats;
+
+/* Profiling switches (sddm_set_profiling), off by default. */
+enum {
+    SDDM_PROFILE_TIME_TRACE = 1,        /* CUDA events around every trace-kernel launch */
+    SDDM_PROFILE_COUNT_TRAVERSAL = 2    /* count nodes, triangle tests and ray visits */
+};
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA `device` using `stream` (cudaStream_t or NULL).
+ * *out receives the context; SDDM_ERR_CUDA if the device cannot be used. */
+int sddm_create(sddm_ctx **out, int device, void *stream);
+
+/* Free every device and host resource of the context. NULL is accepted. */
+int sddm_destroy(sddm_ctx *ctx);
+
+/* Message of the calling thread's last failed call ("" if none). The pointer
+ * stays valid until the next sddm_* call on the same thread. */
+const char *sddm_last_error(void);
+
+/* Library version string ("sddm <major>.<minor> sm_103a"). */
+const char *sddm_version(void);
+
+/* ---------------------------------------------------------------- scene */
+
+/* Spectral sampling of the rendering model (Sec. 1: "a model including
+ * spectral properties"; Sec. 3). L bins (1..256) at lambda_nm[L], quadrature
+ * weights quad_w[L] (nm), colour matching functions cmf_xyz[L][3]. Resets the
+ * material list, which is defined per bin. */
+int sddm_set_spectrum(sddm_ctx *ctx, int L, const float *lambda_nm, const float *quad_w,
+                      const float *cmf_xyz);
+
+/* Lambertian reflector with spectral reflectance rho[L] in [0,1] (the other
+ * room materials of Sec. 2, whose spectra stand for the RGB-derived ones).
+ * *mat receives the material id (ids count up from 0 in call order). */
+int sddm_add_lambertian(sddm_ctx *ctx, const float *rho, uint32_t *mat);
+
+/* Metal described by its optical constants n[L] + i k[L] (Eq. 1, Sec. 2:
+ * "metallic surfaces ... described by means of optical constants"): a smooth
+ * mirror weighted by the Fresnel reflectance. n > 0, k >= 0. */
+int sddm_add_conductor(sddm_ctx *ctx, const float *n, const float *k, uint32_t *mat);
+
+/* Glass pane as an absorbing plane-parallel slab (Sec. 2 glass samples,
+ * Sec. 6 "the Fresnel definition", photochromic/electrochromic state):
+ * real index n[L] >= 1, absorption alpha(s) = alpha_clear[L] + s * dalpha[L]
+ * in 1/m (k = alpha * lambda / 4 pi), thickness in metres, default state
+ * s_default in [0,1]. The slab's triangles must form one closed convex object
+ * (one obj_id). */
+int sddm_add_glass_slab(sddm_ctx *ctx, const float *n, const float *alpha_clear,
+                        const float *dalpha, float thickness_m, float s_default, uint32_t *mat);
+
+/* One-sided area light of radiance Le[L] >= 0 toward its counter-clockwise
+ * normal, black to reflection (the light sources of Eq. 3, here with area). */
+int sddm_add_emitter(sddm_ctx *ctx, const float *Le, uint32_t *mat);
+
+/* One-sided area light that also reflects diffusely with rho[L] (used by the
+ * white-furnace check; no counterpart in the paper). */
+int sddm_add_diffuse_emitter(sddm_ctx *ctx, const float *rho, const float *Le, uint32_t *mat);
+
+/* Triangle mesh: vertices v[nv][3], triangles tri[nt][3] (vertex indices,
+ * counter-clockwise about the outward normal), material mat_id[nt] and
+ * object obj_id[nt] per triangle (Sec. 4 "polygons of objects"). nt >= 1,
+ * at most 2^26 triangles. Invalidates a previous build. */
+int sddm_set_mesh(sddm_ctx *ctx, const float *v, int nv, const uint32_t *tri, int nt,
+                  const uint32_t *mat_id, const uint32_t *obj_id);
+
+/* Build the acceleration structures on the host and upload them (Sec. 5:
+ * "splitting a global domain into several small sub-domains"): a global
+ * binned-SAH BVH for the megakernel and, for grid != {1,1,1}, a grid of
+ * subdomains each with its own BVH over the triangles that overlap it
+ * (duplicated by reference, node boxes clipped to the subdomain). o may be
+ * NULL for defaults. Synchronous. */
+int sddm_build(sddm_ctx *ctx, const sddm_build_opts *o);
+
+/* Render n >= 1 images (Sec. 4 algorithm, Eq. 2-3 model) in one batched
+ * call on the context stream; returns when the device has finished. Every
+ * output pointer is DEVICE memory owned by the caller. st may be NULL. */
+int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st);
+
+/* Host-buffer variant of sddm_render for callers without device memory:
+ * xyz_out / aov pointers in d are HOST pointers here; the library copies
+ * results back before returning. Same semantics otherwise. */
+int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st);
+
+/* Pick grid, queue capacity and blocks per SM for these renders by timing
+ * short pilot renders (<= 1 spp) of candidate settings (Sec. 5 load
+ * balancing, done here by measurement). Writes the best options to *best and
+ * leaves the context built with them. */
+int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_opts *best);
+
+/* Enable the SDDM_PROFILE_* measurements of later sddm_render calls
+ * (0 = off). Counting uses a separately compiled trace kernel, so the timed
+ * kernel is never the counting one within a call. */
+int sddm_set_profiling(sddm_ctx *ctx, int flags);
+
+/* ---------------------------------------------------------- test hooks */
+
+/* Glass slab R and T (Sec. 6 "Fresnel definition") for n queries of glass
+ * material `mat`: cos_theta[n] in [0,1], bin index bin[n] in [0,L), state
+ * s[n], thickness_m[n]. All four inputs and R[n], T[n] are DEVICE arrays.
+ * mode = sddm_bsdf_mode. */
+int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, const int32_t *bin,
+                    const float *s, const float *thickness_m, float *R, float *T, int mode);
+
+/* Philox4x32-10 block for counters ctr[n][4] under key {key0, key1}: out[n][4]
+ * words. ctr and out are DEVICE arrays. */
+int sddm_philox(sddm_ctx *ctx, int n, const uint32_t *ctr, uint32_t key0, uint32_t key1,
+                uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDDM_H */

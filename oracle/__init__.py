@@ -78,7 +78,7 @@ def _load():
         lib.orc_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(_SceneDesc)]
         lib.orc_create.restype = C.c_int
         lib.orc_destroy.argtypes = [P]
-        lib.orc_render_pixels.argtypes = [P, C.POINTER(_RenderDesc), C.c_int64, P, P, P, P, P,
+        lib.orc_render_pixels.argtypes = [P, C.POINTER(_RenderDesc), C.c_int64, P, P, P, P, P, P,
                                           C.c_int, P]
         lib.orc_render_pixels.restype = C.c_int
         lib.orc_philox4x32_10.argtypes = [P, P, P]
@@ -223,9 +223,10 @@ class Oracle:
         r.width, r.height, r.spp, r.max_depth = spec.width, spec.height, spec.spp, spec.max_depth
         r.seed, r.render_id = spec.seed & 0xFFFFFFFF, spec.render_id & 0xFFFFFFFF
         r.nee = 1 if spec.nee else 0
+        f32 = lambda v: float(np.float32(v))   # the camera reaches the CUDA path as float32
         for i in range(3):
-            r.cam_pos[i], r.cam_look[i], r.cam_up[i] = cam.pos[i], cam.look[i], cam.up[i]
-        r.vfov_deg, r.ortho_height = cam.vfov_deg, cam.ortho_height
+            r.cam_pos[i], r.cam_look[i], r.cam_up[i] = f32(cam.pos[i]), f32(cam.look[i]), f32(cam.up[i])
+        r.vfov_deg, r.ortho_height = f32(cam.vfov_deg), f32(cam.ortho_height)
         r.s_override = _ptr(s_ov)
         r.brute_force = 1 if brute_force else 0
         return r, s_ov
@@ -239,26 +240,27 @@ class Oracle:
     def render_pixels(self, spec, pix=None, n_threads=0, per_sample=False, brute_force=False):
         """Render the listed pixels (all if None). Returns a dict with ``xyz``
         [n,3]; with ``per_sample`` also ``sample_xyz`` [n,spp,3], ``first_prim``
-        [n,spp] and ``margin`` [n,spp]; ``segments`` = (extension, shadow)."""
+        [n,spp], ``margin`` [n,spp] and ``cos_min`` [n,spp]; ``segments`` = (extension, shadow)."""
         if pix is None:
             pix = np.arange(spec.width * spec.height, dtype=np.int64)
         pix = np.ascontiguousarray(pix, dtype=np.int64)
         n = int(pix.shape[0])
         r, s_keep = self._render_desc(spec, brute_force)
         xyz = np.zeros((n, 3), np.float64)
-        sx = fp = mg = None
+        sx = fp = mg = cm = None
         if per_sample:
             sx = np.zeros((n, spec.spp, 3), np.float64)
             fp = np.zeros((n, spec.spp), np.int32)
             mg = np.zeros((n, spec.spp), np.float64)
+            cm = np.zeros((n, spec.spp), np.float64)
         seg = np.zeros(2, np.int64)
         rc = self.lib.orc_render_pixels(self._h, C.byref(r), n, _ptr(pix), _ptr(xyz), _ptr(sx),
-                                        _ptr(fp), _ptr(mg), int(n_threads), _ptr(seg))
+                                        _ptr(fp), _ptr(mg), _ptr(cm), int(n_threads), _ptr(seg))
         if rc != 0:
             raise RuntimeError(f"orc_render_pixels failed ({rc})")
         out = dict(xyz=xyz, segments=(int(seg[0]), int(seg[1])), pix=pix)
         if per_sample:
-            out.update(sample_xyz=sx, first_prim=fp, margin=mg)
+            out.update(sample_xyz=sx, first_prim=fp, margin=mg, cos_min=cm)
         return out
 
     def render_image(self, spec, n_threads=0):

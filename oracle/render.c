@@ -283,12 +283,12 @@ typedef struct {
 } orc_scratch;
 
 static void trace_path(const orc_ctx *c, const orc_render_desc *r, int px, int py, int j,
-                       orc_scratch *ws, int32_t *first_prim, double *margin_out)
+                       orc_scratch *ws, int32_t *first_prim, double *margin_out, double *cos_min_out)
 {
     const int L = c->L;
     const int brute = r->brute_force;
     double *T = ws->T, *Ls = ws->Lsum;
-    double margin = INFINITY, m;
+    double margin = INFINITY, m, cos_min = INFINITY;
     for (int i = 0; i < L; ++i) {
         T[i] = 1.0;
         Ls[i] = 0.0;
@@ -368,6 +368,7 @@ static void trace_path(const orc_ctx *c, const orc_render_desc *r, int px, int p
                     if (brute)
                         margin = fmin(margin, m);
                     if (!occ) {
+                        cos_min = fmin(cos_min, fmin(cx, cy));
                         double G = cx * cy / (dist * dist) * c->light_area;
                         const double *Le = c->a + (size_t)c->mat[lt] * L;
                         for (int i = 0; i < L; ++i) {
@@ -439,6 +440,8 @@ static void trace_path(const orc_ctx *c, const orc_render_desc *r, int px, int p
     }
     if (margin_out)
         *margin_out = brute ? margin : NAN;
+    if (cos_min_out)
+        *cos_min_out = cos_min;
 }
 
 /* --------------------------------------------------------- the driver --- */
@@ -447,7 +450,7 @@ typedef struct {
     const orc_render_desc *r;
     int64_t n_pix;
     const int64_t *pix;
-    double *xyz, *sample_xyz, *margin;
+    double *xyz, *sample_xyz, *margin, *cos_min;
     int32_t *first_prim;
     atomic_llong next;
     atomic_llong seg_ext, seg_shadow;
@@ -482,8 +485,8 @@ static void *worker(void *arg)
             for (int j = 0; j < r->spp; ++j) {
                 size_t si = (size_t)k * (size_t)r->spp + (size_t)j;
                 int32_t fp;
-                double mg;
-                trace_path(c, r, px, py, j, &ws, &fp, &mg);
+                double mg, cm;
+                trace_path(c, r, px, py, j, &ws, &fp, &mg, &cm);
                 double X = 0.0, Y = 0.0, Z = 0.0;
                 for (int i = 0; i < L; ++i) {
                     double e = c->w[i] * ws.Lsum[i];
@@ -503,6 +506,8 @@ static void *worker(void *arg)
                     jb->first_prim[si] = fp;
                 if (jb->margin)
                     jb->margin[si] = mg;
+                if (jb->cos_min)
+                    jb->cos_min[si] = cm;
             }
             for (int a = 0; a < 3; ++a)
                 jb->xyz[3 * k + a] = acc[a] / (double)r->spp;
@@ -517,7 +522,7 @@ static void *worker(void *arg)
 
 int orc_render_pixels(void *ctx, const orc_render_desc *r, int64_t n_pix, const int64_t *pix,
                       double *xyz_out, double *sample_xyz, int32_t *first_prim, double *margin,
-                      int n_threads, int64_t *seg_out)
+                      double *cos_min, int n_threads, int64_t *seg_out)
 {
     const orc_ctx *c = (const orc_ctx *)ctx;
     if (!c || !r || r->width <= 0 || r->height <= 0 || r->spp <= 0 || r->max_depth <= 0 || n_pix < 0)
@@ -540,6 +545,7 @@ int orc_render_pixels(void *ctx, const orc_render_desc *r, int64_t n_pix, const 
     jb.sample_xyz = sample_xyz;
     jb.first_prim = first_prim;
     jb.margin = margin;
+    jb.cos_min = cos_min;
     atomic_init(&jb.next, 0);
     atomic_init(&jb.seg_ext, 0);
     atomic_init(&jb.seg_shadow, 0);

@@ -77,11 +77,13 @@ void orc_destroy(void *ctx);
 /* Mean XYZ over spp for each listed pixel (linear index y*W+x).
  * xyz_out [n_pix][3]; optional per-sample outputs (NULL to skip):
  *   sample_xyz [n_pix][spp][3], first_prim [n_pix][spp] (-1 = miss),
- *   margin [n_pix][spp] (smallest decision margin on the path; brute_force only).
+ *   margin [n_pix][spp] (smallest decision margin on the path; brute_force only),
+ *   cos_min [n_pix][spp] (smallest cosine of a contributing shadow ray, +inf if none:
+ *   the conditioning of the sample, a cosine c carrying ~1e-7/c relative error in float).
  * seg_out[0] += extension segments, seg_out[1] += shadow segments. */
 int orc_render_pixels(void *ctx, const orc_render_desc *r, int64_t n_pix, const int64_t *pix,
                       double *xyz_out, double *sample_xyz, int32_t *first_prim, double *margin,
-                      int n_threads, int64_t *seg_out);
+                      double *cos_min, int n_threads, int64_t *seg_out);
 
 /* Test hooks ------------------------------------------------------------ */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -1,0 +1,758 @@
+// Domain-decomposition wavefront path tracer.
+//
+// Sec. 5 of the paper parallelises ray tracing by splitting the scene into
+// subdomains; a ray handed across an interface keeps its properties
+// ("direction, amplitude, angle") and the subdomain that receives it carries
+// on. Each processor works on the subdomains whose rays are waiting, keeping
+// their data loaded (Sec. 5, last paragraph). On one GB300 this becomes:
+//
+//   camera / shade kernels  --append-->  staging area (ray + destination cell)
+//   scatter kernel          --sort by cell-->  queue of the wave
+//   trace kernel (persistent blocks claim consecutive rays, i.e. they drain
+//   the queues cell by cell): traverse the cell's own BVH; a hit inside the
+//   cell's [t_cur - eps, t_exit + eps] window is final; otherwise the ray is
+//   appended, with t_cur = t_exit, for the neighbouring cell, through
+//   warp-aggregated atomics (__match_any_sync on the destination cell).
+//   Waves repeat until no ray is left; a ray only ever moves forward along
+//   each axis, so dims.x + dims.y + dims.z - 2 waves always suffice.
+//
+// The closest hit found this way is the global closest hit (up to eps), so
+// the estimator is the same one the megakernel computes (Sec. 4 algorithm,
+// Eq. 2-3); shading is split into a per-bounce kernel over path slots whose
+// spectral throughput lives in HBM as [L][paths].
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "device_common.cuh"
+#include "sddm_ddm.h"
+
+namespace sddm {
+
+DDMBuffers::~DDMBuffers() {
+    if (mem) cudaFree(mem);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+cudaError_t DDMBuffers::event_pair(cudaEvent_t &a, cudaEvent_t &b) {
+    while (events.size() < (size_t)events_used + 2) {
+        cudaEvent_t e;
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) return err;
+        events.push_back(e);
+    }
+    a = events[events_used];
+    b = events[events_used + 1];
+    events_used += 2;
+    return cudaSuccess;
+}
+
+struct KArgs {
+    DevScene sc;
+    DDMScene g;
+    RenderBatch rb;
+    PathState ps;
+    Queues Q;
+    int64_t path_begin;
+    int b;
+    int last_wave;        // rays still moving after this wave are an error
+    float *sample_xyz;
+    int32_t *first_prim;
+    unsigned long long *counters;
+    int *err;
+};
+
+// ---------------------------------------------------------------- grid
+__device__ __forceinline__ bool grid_enter(const DDMScene &g, V3 o, V3 d, float tmax, float &t0, int &cell) {
+    float tn = 0.0f, tf = tmax;
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0.0f) {
+            if (oo[a] < g.lo[a] || oo[a] > g.hi[a]) return false;
+            continue;
+        }
+        float inv = 1.0f / dd[a];
+        float ta = (g.lo[a] - oo[a]) * inv, tb = (g.hi[a] - oo[a]) * inv;
+        tn = fmaxf(tn, fminf(ta, tb));
+        tf = fminf(tf, fmaxf(ta, tb));
+    }
+    if (tn > tf) return false;
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p = oo[a] + tn * dd[a];
+        int k = (int)floorf((p - g.lo[a]) * g.inv_cell[a]);
+        c[a] = min(max(k, 0), g.dims[a] - 1);
+    }
+    cell = (c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
+    t0 = tn;
+    return true;
+}
+
+// Distance at which the ray leaves `cell`, and the neighbour it enters
+// (-1 when it leaves the grid). Ties between faces go x, then y, then z.
+__device__ __forceinline__ float cell_exit(const DDMScene &g, int cell, V3 o, V3 d, int &next) {
+    int c[3] = {cell % g.dims[0], (cell / g.dims[0]) % g.dims[1], cell / (g.dims[0] * g.dims[1])};
+    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    float t = __int_as_float(0x7f800000);
+    int axis = -1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0.0f) continue;
+        float plane = g.lo[a] + (float)(dd[a] > 0.0f ? c[a] + 1 : c[a]) * g.cell[a];
+        float ta = (plane - oo[a]) / dd[a];
+        if (ta < t) {
+            t = ta;
+            axis = a;
+        }
+    }
+    next = -1;
+    if (axis >= 0) {
+        c[axis] += dd[axis] > 0.0f ? 1 : -1;
+        if (c[axis] >= 0 && c[axis] < g.dims[axis]) next = (c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
+    }
+    return t;
+}
+
+// Warp-aggregated append of rays to the staging area. All 32 lanes call it.
+__device__ __forceinline__ void stage_push(const Queues &Q, bool want, int cell, float4 r0, float4 r1, int4 r2,
+                                           int *err) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, want);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(Q.ctl + 0, (unsigned long long)__popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (want) {
+        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < (unsigned long long)Q.cap) {
+            float4 *dst = Q.stage + 3 * slot;
+            dst[0] = r0;
+            dst[1] = r1;
+            dst[2] = make_float4(__int_as_float(r2.x), __int_as_float(r2.y), __int_as_float(r2.z),
+                                 __int_as_float(r2.w));
+        } else {
+            atomicCAS(err, 0, 1);
+        }
+        const unsigned peers = __match_any_sync(m, cell);
+        if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + cell, __popc(peers));
+    }
+}
+
+__device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned long long v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, v);
+}
+
+// --------------------------------------------------------- camera rays
+__global__ void __launch_bounds__(256) k_camera(KArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t np = a.ps.np;
+    const int L = a.sc.L;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long n_ext = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
+        const int64_t q = base + lane;
+        bool want = false;
+        int cell = 0;
+        float4 r0 = make_float4(0, 0, 0, 0), r1 = r0;
+        int4 r2 = make_int4(0, 0, 0, 0);
+        if (q < np) {
+            const int64_t gp = a.path_begin + q;
+            const int r = find_render(a.rb, gp);
+            const RenderInfo &ri = a.rb.info[r];
+            const int64_t local = gp - ri.path_begin;
+            const uint32_t p = (uint32_t)(local / ri.spp), j = (uint32_t)(local % ri.spp);
+            const int px = (int)(p % (uint32_t)ri.width), py = (int)(p / (uint32_t)ri.width);
+            uint4 x = philox4x32_10(make_uint4(p, j, 0u, kSlotCamera), ri.seed, ri.render_id);
+            V3 o, d;
+            camera_ray(ri, (float)px + u01(x.x), (float)py + u01(x.y), o, d);
+            for (int i = 0; i < L; ++i) a.ps.T[(size_t)i * np + q] = 1.0f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a.ps.acc[k * np + q] = 0.0f;
+            a.ps.flags[q] = kFlExt | kFlPrevSpec;
+            a.ps.sh_status[q] = 0;
+            if (a.first_prim) a.first_prim[q] = -1;
+            ++n_ext;
+            float t0;
+            if (grid_enter(a.g, o, d, __int_as_float(0x7f800000), t0, cell)) {
+                want = true;
+                r0 = make_float4(o.x, o.y, o.z, t0);
+                r1 = make_float4(d.x, d.y, d.z, __int_as_float(0x7f800000));
+                r2 = make_int4((int)q, -1, 0, cell);
+            } else {
+                a.ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                a.ps.hit1[q] = make_float4(d.x, d.y, d.z, 0.f);
+            }
+        }
+        stage_push(a.Q, want, cell, r0, r1, r2, a.err);
+    }
+    warp_count(a.counters + 0, n_ext);
+}
+
+// ------------------------------------------------------ sort by cell
+// Exclusive prefix of the per-cell counts into s_off (every block computes it).
+__device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (n + nt - 1) / nt;
+    const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+    int sum = 0;
+    for (int i = b0; i < b1; ++i) sum += cnt[i];
+    s_tmp[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int v = t >= off ? s_tmp[t - off] : 0;
+        __syncthreads();
+        s_tmp[t] += v;
+        __syncthreads();
+    }
+    int run = s_tmp[t] - sum;
+    for (int i = b0; i < b1; ++i) {
+        s_off[i] = run;
+        run += cnt[i];
+    }
+    if (t == nt - 1) s_off[n] = s_tmp[t];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_scatter(KArgs a) {
+    __shared__ int s_off[kMaxCells + 1];
+    __shared__ int s_tmp[256];
+    const Queues &Q = a.Q;
+    const int n_cells = a.g.n_cells;
+    block_prefix(Q.cnt, n_cells, s_off, s_tmp);
+    int total = s_off[n_cells];
+    // the per-cell counts must add up to the staged rays, within capacity
+    const bool bad = (unsigned long long)total != Q.ctl[0] || (int64_t)total > Q.cap;
+    if (bad) total = 0;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < n_cells; i += blockDim.x) Q.off[i] = bad ? 0 : s_off[i];
+        if (threadIdx.x == 0) {
+            Q.off[n_cells] = total;
+            if (bad) atomicCAS(a.err, 0, 3);
+        }
+    }
+    if (total == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int i = base + lane;
+        const bool valid = i < total;
+        const unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const float4 *src = Q.stage + 3 * (size_t)i;
+            const float4 r0 = src[0], r1 = src[1], r2 = src[2];
+            const int cell = __float_as_int(r2.w);
+            const unsigned peers = __match_any_sync(m, cell);
+            const int leader = __ffs(peers) - 1;
+            int base_slot = 0;
+            if (lane == leader) base_slot = atomicAdd(Q.fill + cell, __popc(peers));
+            base_slot = __shfl_sync(peers, base_slot, leader);
+            const int pos = s_off[cell] + base_slot + __popc(peers & ((1u << lane) - 1u));
+            float4 *dst = Q.in + 3 * (size_t)pos;
+            dst[0] = r0;
+            dst[1] = r1;
+            dst[2] = r2;
+        }
+    }
+}
+
+// ------------------------------------------------------ trace one wave
+template <bool COUNT>
+__global__ void __launch_bounds__(128) k_trace_wave(KArgs a) {
+    const Queues &Q = a.Q;
+    const DDMScene &g = a.g;
+    const int total = Q.off[g.n_cells];
+    if (total == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t np = a.ps.np;
+    unsigned long long n_cross = 0, n_vis = 0;
+    TravCount tc;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(Q.ctl + 1, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)total) break;
+        const int idx = (int)base + lane;
+        bool want = false;
+        int next = -1;
+        float4 o0 = make_float4(0, 0, 0, 0), o1 = o0;
+        int4 o2 = make_int4(0, 0, 0, 0);
+        if (idx < total) {
+            const float4 *src = Q.in + 3 * (size_t)idx;
+            const float4 r0 = src[0], r1 = src[1], r2f = src[2];
+            const int q = __float_as_int(r2f.x), excl = __float_as_int(r2f.y), rfl = __float_as_int(r2f.z),
+                      cell = __float_as_int(r2f.w);
+            const V3 o = xyz(r0), d = xyz(r1);
+            const float t_cur = r0.w, t_max = r1.w;
+            const float t_exit = cell_exit(g, cell, o, d, next);
+            const float tmin = fmaxf(0.0f, t_cur - g.eps);
+            const Ray ray = make_ray(o, d);
+            const int root = __ldg(g.root + cell);
+            ++n_vis;
+            bool done = false;
+            int rfl_next = rfl;
+            if (rfl & kRayShadow) {
+                Crossings cr;
+                cr.n = (rfl >> 1) & 7;
+                for (int k = 0; k < cr.n; ++k) cr.obj[k] = a.ps.cross_obj[k * np + q];
+                const int n_prev = cr.n;
+                const float tw = fminf(t_exit + g.eps, t_max);
+                const bool occ = trace_shadow<COUNT>(g.nodes, g.tris, root, ray, tmin, tw, excl, cr, &tc);
+                for (int k = n_prev; k < cr.n; ++k) {
+                    const float4 cn = __ldg(a.sc.tri_n + cr.tri[k]);
+                    a.ps.cross_obj[k * np + q] = cr.obj[k];
+                    a.ps.cross_mat[k * np + q] = __float_as_int(cn.w);
+                    a.ps.cross_cos[k * np + q] = -dot(d, xyz(cn));
+                }
+                if (occ) {
+                    a.ps.sh_status[q] = kShadowOccluded;
+                    done = true;
+                } else if (t_exit + g.eps >= t_max || next < 0) {
+                    a.ps.sh_status[q] = kShadowClear | (cr.n << 4);
+                    done = true;
+                }
+                rfl_next = (rfl & 1) | (cr.n << 1);
+            } else {
+                const int ep = excl >= 0 ? excl : -1, eo = excl <= -2 ? -excl - 2 : -1;
+                const Hit h = trace_closest<COUNT>(g.nodes, g.tris, root, ray, tmin, t_exit + g.eps, ep, eo, &tc);
+                if (h.prim >= 0) {
+                    const V3 x = o + h.t * d;
+                    a.ps.hit0[q] = make_float4(x.x, x.y, x.z, __int_as_float(h.prim));
+                    a.ps.hit1[q] = make_float4(d.x, d.y, d.z, h.t);
+                    done = true;
+                } else if (next < 0) {
+                    a.ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                    a.ps.hit1[q] = make_float4(d.x, d.y, d.z, 0.f);
+                    done = true;
+                }
+            }
+            if (!done) {
+                want = true;
+                o0 = make_float4(o.x, o.y, o.z, fmaxf(t_cur, t_exit));
+                o1 = r1;
+                o2 = make_int4(q, excl, rfl_next, next);
+                ++n_cross;
+            }
+        }
+        if (want && a.last_wave) {   // cannot happen: each wave moves a ray forward along one axis
+            atomicCAS(a.err, 0, 4);
+            want = false;
+        }
+        stage_push(Q, want, next, o0, o1, o2, a.err);
+    }
+    warp_count(a.counters + 3, n_cross);
+    if (COUNT) {
+        warp_count(a.counters + 5, tc.nodes);
+        warp_count(a.counters + 6, tc.tris);
+        warp_count(a.counters + 7, n_vis);
+    }
+}
+
+// ------------------------------------------------------------- shading
+__device__ __forceinline__ float st_of(const RenderBatch &rb, int r, int m, int n_mat) {
+    return __ldg(rb.state_s + (size_t)r * n_mat + m);
+}
+
+__global__ void __launch_bounds__(256) k_shade(KArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t np = a.ps.np;
+    const DevScene &sc = a.sc;
+    const int L = sc.L;
+    const int b = a.b;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long n_ext = 0, n_sh = 0, n_glass = 0;
+    const PathState &ps = a.ps;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
+        const int64_t q = base + lane;
+        bool want_e = false, want_s = false;
+        int cell_e = 0, cell_s = 0;
+        float4 e0 = make_float4(0, 0, 0, 0), e1 = e0, s0 = e0, s1 = e0;
+        int4 e2 = make_int4(0, 0, 0, 0), s2 = e2;
+        int fl = q < np ? ps.flags[q] : 0;
+        if (fl & (kFlExt | kFlShadow)) {
+            const int64_t gp = a.path_begin + q;
+            const int r = find_render(a.rb, gp);
+            const RenderInfo &ri = a.rb.info[r];
+            const int64_t local = gp - ri.path_begin;
+            const uint32_t p = (uint32_t)(local / ri.spp), j = (uint32_t)(local % ri.spp);
+
+            // (1) shadow ray of the previous vertex
+            bool resolve = false;
+            float G = 0.f;
+            const float *rho_prev = nullptr, *Le_l = nullptr;
+            int ncr = 0;
+            int cmat[kMaxCross];
+            float ccos[kMaxCross];
+            if (fl & kFlShadow) {
+                const int stt = ps.sh_status[q];
+                if ((stt & 3) == kShadowClear) {
+                    resolve = true;
+                    ncr = stt >> 4;
+                    G = ps.nee_G[q];
+                    Le_l = sc.mat_a + (size_t)ps.nee_lmat[q] * L;
+                    const int pm = ps.pend_mat[q];
+                    rho_prev = (__ldg(sc.mat_kind + pm) == kLambert ? sc.mat_a : sc.mat_b) + (size_t)pm * L;
+                    for (int k = 0; k < ncr; ++k) {
+                        cmat[k] = ps.cross_mat[k * np + q];
+                        ccos[k] = ps.cross_cos[k * np + q];
+                    }
+                    n_glass += ncr;
+                }
+            }
+            // (2) weight of the previous vertex
+            const bool pend = (fl & kFlPend) != 0;
+            int pm = -1, pkind = 0;
+            float pcos = 0.f, pw = 0.f;
+            if (pend) {
+                pm = ps.pend_mat[q];
+                pkind = __ldg(sc.mat_kind + pm);
+                pcos = ps.pend_cos[q];
+                pw = ps.pend_w[q];
+            }
+            // (3) the hit of this vertex
+            bool has_hit = false, emit = false;
+            int prim = -1, mat = 0, kind = 0;
+            V3 x = v3(0, 0, 0), d = x, ng = x, ns = x;
+            float cd = 0.f;
+            if ((fl & kFlExt) && b <= ri.max_depth) {
+                const float4 h0 = ps.hit0[q], h1 = ps.hit1[q];
+                prim = __float_as_int(h0.w);
+                if (b == 1 && a.first_prim) a.first_prim[q] = prim;
+                if (prim >= 0) {
+                    has_hit = true;
+                    x = xyz(h0);
+                    d = xyz(h1);
+                    const float4 tn = __ldg(sc.tri_n + prim);
+                    ng = xyz(tn);
+                    mat = __float_as_int(tn.w);
+                    kind = __ldg(sc.mat_kind + mat);
+                    cd = dot(d, ng);
+                    ns = cd < 0.0f ? ng : (-1.0f) * ng;
+                    emit = (kind == kEmitter || kind == kDiffuseEmitter) && cd < 0.0f &&
+                           (!ri.nee || b == 1 || (fl & kFlPrevSpec));
+                }
+            }
+            // spectral pass over the bins: resolve, weight, emit
+            const float *Le_b = sc.mat_a + (size_t)mat * L;
+            const float *pA = sc.mat_a + (size_t)(pm < 0 ? 0 : pm) * L;
+            const float *pB = sc.mat_b + (size_t)(pm < 0 ? 0 : pm) * L;
+            const float *pC = sc.mat_c + (size_t)(pm < 0 ? 0 : pm) * L;
+            const float ps_state = (pend && pkind == kGlass) ? st_of(a.rb, r, pm, sc.n_mat) : 0.f;
+            const float pthick = (pend && pkind == kGlass) ? __ldg(sc.mat_thick + pm) : 0.f;
+            const float pwabs = fabsf(pw);
+            const bool preflect = pw < 0.0f;
+            float cst[kMaxCross], cth[kMaxCross];
+            for (int k = 0; k < ncr; ++k) {
+                cst[k] = st_of(a.rb, r, cmat[k], sc.n_mat);
+                cth[k] = __ldg(sc.mat_thick + cmat[k]);
+            }
+            const bool need_T = resolve || pend || emit;
+            if (need_T) {
+                Kahan NX, NY, NZ, EX, EY, EZ;
+                for (int i = 0; i < L; ++i) {
+                    float t = ps.T[(size_t)i * np + q];
+                    const float wx = __ldg(sc.wcmf + 3 * i), wy = __ldg(sc.wcmf + 3 * i + 1),
+                                wz = __ldg(sc.wcmf + 3 * i + 2);
+                    if (resolve) {
+                        float tr = 1.0f;
+                        for (int k = 0; k < ncr; ++k) {
+                            const size_t kk = (size_t)cmat[k] * L + i;
+                            float R_, T_;
+                            slab_RT(ccos[k], __ldg(sc.lam + i), __ldg(sc.mat_a + kk),
+                                    __ldg(sc.mat_b + kk) + cst[k] * __ldg(sc.mat_c + kk), cth[k], R_, T_);
+                            tr *= T_;
+                        }
+                        const float c = t * __ldg(rho_prev + i) * __ldg(Le_l + i) * G * tr;
+                        NX.add(c * wx);
+                        NY.add(c * wy);
+                        NZ.add(c * wz);
+                    }
+                    if (pend) {
+                        float w;
+                        if (pkind == kLambert) {
+                            w = __ldg(pA + i);
+                        } else if (pkind == kDiffuseEmitter) {
+                            w = __ldg(pB + i);
+                        } else if (pkind == kConductor) {
+                            w = conductor_F(pcos, __ldg(pA + i), __ldg(pB + i));
+                        } else {
+                            float R_, T_;
+                            slab_RT(pcos, __ldg(sc.lam + i), __ldg(pA + i), __ldg(pB + i) + ps_state * __ldg(pC + i),
+                                    pthick, R_, T_);
+                            w = (preflect ? R_ : T_) * pwabs;
+                        }
+                        t *= w;
+                    }
+                    if (emit) {
+                        const float e = t * __ldg(Le_b + i);
+                        EX.add(e * wx);
+                        EY.add(e * wy);
+                        EZ.add(e * wz);
+                    }
+                    ps.T[(size_t)i * np + q] = t;
+                }
+                Kahan3 acc;
+                acc.x.s = ps.acc[0 * np + q];
+                acc.y.s = ps.acc[1 * np + q];
+                acc.z.s = ps.acc[2 * np + q];
+                acc.x.c = ps.acc[3 * np + q];
+                acc.y.c = ps.acc[4 * np + q];
+                acc.z.c = ps.acc[5 * np + q];
+                if (resolve) acc.add(NX.s, NY.s, NZ.s);
+                if (emit) acc.add(EX.s, EY.s, EZ.s);
+                ps.acc[0 * np + q] = acc.x.s;
+                ps.acc[1 * np + q] = acc.y.s;
+                ps.acc[2 * np + q] = acc.z.s;
+                ps.acc[3 * np + q] = acc.x.c;
+                ps.acc[4 * np + q] = acc.y.c;
+                ps.acc[5 * np + q] = acc.z.c;
+            }
+            // (4) continue the path from this vertex
+            int nfl = fl & kFlPrevSpec;
+            nfl &= ~(kFlExt | kFlShadow | kFlPend);
+            if (has_hit && kind != kEmitter) {
+                const uint32_t k0 = ri.seed, k1 = ri.render_id;
+                if (kind == kLambert || kind == kDiffuseEmitter) {
+                    if (ri.nee && sc.n_light > 0) {
+                        uint4 xl = philox4x32_10(make_uint4(p, j, (uint32_t)b, kSlotLight), k0, k1);
+                        const float ua = u01(xl.x), su = sqrtf(u01(xl.y)), u2 = u01(xl.z);
+                        int li = sc.n_light - 1;
+                        for (int k = 0; k < sc.n_light; ++k)
+                            if (ua < __ldg(sc.light_cdf + k)) { li = k; break; }
+                        const float4 lv0 = __ldg(sc.light_v + 3 * li), lv1 = __ldg(sc.light_v + 3 * li + 1),
+                                     lv2 = __ldg(sc.light_v + 3 * li + 2);
+                        const float b0 = 1.0f - su, b1 = u2 * su, b2 = 1.0f - b0 - b1;
+                        const V3 y = b0 * xyz(lv0) + b1 * xyz(lv1) + b2 * xyz(lv2);
+                        const V3 xo = x + kRayOffset * ns;
+                        V3 w = y - xo;
+                        const float dist = sqrtf(dot(w, w));
+                        w = (1.0f / dist) * w;
+                        const float4 ln = __ldg(sc.tri_n + __float_as_int(lv0.w));
+                        const float cx = dot(ns, w), cy = -dot(xyz(ln), w);
+                        if (cx > 0.0f && cy > 0.0f) {
+                            ++n_sh;
+                            ps.nee_G[q] = cx * cy / (dist * dist) * sc.light_area * (1.0f / 3.14159265358979f);
+                            ps.nee_lmat[q] = __float_as_int(ln.w);
+                            const float tmax = (1.0f - kShadowShorten) * dist;
+                            float t0;
+                            nfl |= kFlShadow;
+                            if (grid_enter(a.g, xo, w, tmax, t0, cell_s)) {
+                                ps.sh_status[q] = 0;
+                                want_s = true;
+                                s0 = make_float4(xo.x, xo.y, xo.z, t0);
+                                s1 = make_float4(w.x, w.y, w.z, tmax);
+                                s2 = make_int4((int)q, prim, kRayShadow, cell_s);
+                            } else {
+                                ps.sh_status[q] = kShadowClear;
+                            }
+                        }
+                    }
+                    ps.pend_mat[q] = mat;
+                    nfl |= kFlPend;
+                    nfl &= ~kFlPrevSpec;
+                    if (b < ri.max_depth) {
+                        uint4 xb = philox4x32_10(make_uint4(p, j, (uint32_t)b, kSlotBsdf), k0, k1);
+                        const V3 dn = cosine_dir(ns, u01(xb.x), u01(xb.y));
+                        const V3 on = x + kRayOffset * ns;
+                        ++n_ext;
+                        nfl |= kFlExt;
+                        float t0;
+                        if (grid_enter(a.g, on, dn, __int_as_float(0x7f800000), t0, cell_e)) {
+                            want_e = true;
+                            e0 = make_float4(on.x, on.y, on.z, t0);
+                            e1 = make_float4(dn.x, dn.y, dn.z, __int_as_float(0x7f800000));
+                            e2 = make_int4((int)q, prim, 0, cell_e);
+                        } else {
+                            ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                        }
+                    }
+                } else if (b < ri.max_depth) {
+                    const float c = fabsf(cd);
+                    V3 dn = d, on;
+                    int excl = prim;
+                    ps.pend_mat[q] = mat;
+                    ps.pend_cos[q] = c;
+                    if (kind == kConductor) {
+                        dn = d - (2.0f * cd) * ng;
+                        on = x + kRayOffset * ns;
+                        ps.pend_w[q] = 1.0f;
+                    } else {
+                        const float pr = branch_proxy(c, L, sc.mat_a + (size_t)mat * L);
+                        uint4 xg = philox4x32_10(make_uint4(p, j, (uint32_t)b, kSlotGlass), k0, k1);
+                        const bool refl = u01(xg.x) < pr;
+                        ++n_glass;
+                        if (refl) {
+                            dn = d - (2.0f * cd) * ng;
+                            on = x + kRayOffset * ns;
+                            ps.pend_w[q] = -1.0f / pr;
+                        } else {
+                            on = x - kRayOffset * ns;
+                            excl = -__ldg(sc.tri_obj + prim) - 2;
+                            ps.pend_w[q] = 1.0f / (1.0f - pr);
+                        }
+                    }
+                    nfl |= kFlPend | kFlPrevSpec | kFlExt;
+                    ++n_ext;
+                    float t0;
+                    if (grid_enter(a.g, on, dn, __int_as_float(0x7f800000), t0, cell_e)) {
+                        want_e = true;
+                        e0 = make_float4(on.x, on.y, on.z, t0);
+                        e1 = make_float4(dn.x, dn.y, dn.z, __int_as_float(0x7f800000));
+                        e2 = make_int4((int)q, excl, 0, cell_e);
+                    } else {
+                        ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                    }
+                }
+            }
+            ps.flags[q] = nfl;
+        }
+        stage_push(a.Q, want_e, cell_e, e0, e1, e2, a.err);
+        stage_push(a.Q, want_s, cell_s, s0, s1, s2, a.err);
+    }
+    warp_count(a.counters + 0, n_ext);
+    warp_count(a.counters + 1, n_sh);
+    warp_count(a.counters + 2, n_glass);
+}
+
+__global__ void k_finalize(KArgs a) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t np = a.ps.np;
+    if (q >= np) return;
+    a.sample_xyz[3 * q + 0] = a.ps.acc[0 * np + q];
+    a.sample_xyz[3 * q + 1] = a.ps.acc[1 * np + q];
+    a.sample_xyz[3 * q + 2] = a.ps.acc[2 * np + q];
+}
+
+__global__ void k_image_probe() {}
+
+cudaError_t check_kernel_image() {
+    cudaFuncAttributes attr;
+    return cudaFuncGetAttributes(&attr, k_image_probe);
+}
+
+// ------------------------------------------------------------- host side
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
+    const int64_t np = run.path_count;
+    const int L = run.sc.L;
+    const int nc = run.g.n_cells;
+    if (nc > kMaxCells) {
+        set_error("sddm_render: the DDM method supports at most 4096 subdomains");
+        return SDDM_ERR_INVALID_ARG;
+    }
+    const int64_t cap = 2 * np;
+    // carve one allocation
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t oT = take(sizeof(float) * (size_t)L * np), oAcc = take(sizeof(float) * 6 * np),
+                 oFl = take(4 * np), oPm = take(4 * np), oPc = take(4 * np), oPw = take(4 * np), oG = take(4 * np),
+                 oLm = take(4 * np), oSh = take(4 * np), oCo = take(4 * kMaxCross * np), oCm = take(4 * kMaxCross * np),
+                 oCc = take(4 * kMaxCross * np), oH0 = take(16 * np), oH1 = take(16 * np), oIn = take(48 * cap),
+                 oSt = take(48 * cap), oCtl = take(32 + 4 * (size_t)nc), oFill = take(4 * (size_t)nc),
+                 oOff = take(4 * ((size_t)nc + 1));
+    if (off > buf.bytes) {
+        if (buf.mem) cudaFree(buf.mem);
+        buf.mem = nullptr;
+        buf.bytes = 0;
+        cudaError_t e = cudaMalloc(&buf.mem, off);
+        if (e != cudaSuccess) {
+            buf.mem = nullptr;
+            set_error("sddm_render: DDM path-state allocation failed (reduce paths_in_flight)");
+            return SDDM_ERR_OOM;
+        }
+        buf.bytes = off;
+    }
+    char *m = (char *)buf.mem;
+    KArgs a;
+    a.sc = run.sc;
+    a.g = run.g;
+    a.rb = run.rb;
+    a.path_begin = run.path_begin;
+    a.sample_xyz = run.sample_xyz;
+    a.first_prim = run.first_prim;
+    a.counters = run.counters;
+    a.err = run.error_flag;
+    PathState &ps = a.ps;
+    ps.np = np;
+    ps.T = (float *)(m + oT);
+    ps.acc = (float *)(m + oAcc);
+    ps.flags = (int *)(m + oFl);
+    ps.pend_mat = (int *)(m + oPm);
+    ps.pend_cos = (float *)(m + oPc);
+    ps.pend_w = (float *)(m + oPw);
+    ps.nee_G = (float *)(m + oG);
+    ps.nee_lmat = (int *)(m + oLm);
+    ps.sh_status = (int *)(m + oSh);
+    ps.cross_obj = (int *)(m + oCo);
+    ps.cross_mat = (int *)(m + oCm);
+    ps.cross_cos = (float *)(m + oCc);
+    ps.hit0 = (float4 *)(m + oH0);
+    ps.hit1 = (float4 *)(m + oH1);
+    Queues &Q = a.Q;
+    Q.cap = cap;
+    Q.in = (float4 *)(m + oIn);
+    Q.stage = (float4 *)(m + oSt);
+    Q.ctl = (unsigned long long *)(m + oCtl);
+    Q.cnt = (int *)(m + oCtl + 32);
+    Q.fill = (int *)(m + oFill);
+    Q.off = (int *)(m + oOff);
+
+    const int sm = std::max(1, run.sm_count);
+    const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
+    const int scatter_blocks = sm * 4;
+    const unsigned path_blocks = (unsigned)std::min<int64_t>((np + 255) / 256, (int64_t)sm * 16);
+    const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
+    const size_t ctl_bytes = 32 + 4 * (size_t)nc;
+    cudaError_t e;
+#define DDM_CHECK(x)                                                     \
+    do {                                                                 \
+        if ((e = (x)) != cudaSuccess) return cuda_fail(e, "sddm_render: " #x); \
+    } while (0)
+    DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
+    a.b = 0;
+    a.last_wave = 0;
+    k_camera<<<path_blocks, 256, 0, s>>>(a);
+    DDM_CHECK(cudaGetLastError());
+    for (int b = 1; b <= run.max_depth + 1; ++b) {
+        for (int w = 0; w < waves; ++w) {
+            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nc, s));
+            k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
+            DDM_CHECK(cudaGetLastError());
+            DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
+            a.last_wave = w == waves - 1;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (run.time_trace) {
+                if ((e = buf.event_pair(e0, e1)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
+                DDM_CHECK(cudaEventRecord(e0, s));
+            }
+            if (run.count_traversal)
+                k_trace_wave<true><<<trace_blocks, 128, 0, s>>>(a);
+            else
+                k_trace_wave<false><<<trace_blocks, 128, 0, s>>>(a);
+            DDM_CHECK(cudaGetLastError());
+            if (run.time_trace) DDM_CHECK(cudaEventRecord(e1, s));
+            *run.launches += 2;
+        }
+        a.b = b;
+        k_shade<<<path_blocks, 256, 0, s>>>(a);
+        DDM_CHECK(cudaGetLastError());
+        *run.launches += 1;
+    }
+    k_finalize<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(a);
+    DDM_CHECK(cudaGetLastError());
+    *run.launches += 2;   // camera + finalize
+#undef DDM_CHECK
+    return SDDM_OK;
+}
+
+}  // namespace sddm

@@ -1,0 +1,411 @@
+// Device building blocks of the path tracer: random stream, ray/box and
+// ray/triangle tests, BVH traversal, spectral optics, sampling, compensated sums.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sddm_internal.h"
+
+namespace sddm {
+
+// ----------------------------------------------------------- vector helpers
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ V3 normalize(V3 a) {
+    float inv = 1.0f / sqrtf(dot(a, a));
+    return inv * a;
+}
+__device__ __forceinline__ V3 xyz(float4 f) { return v3(f.x, f.y, f.z); }
+
+// ------------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon et al. (SC'11): ten rounds of two
+// 32x32->64 products whose high halves are xored with the other counter words
+// and the round key; the key advances by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// Top 24 bits as a uniform in [0, 1): exact in float.
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------- BVH nodes
+// Node = 4 float4: (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y) (c1 same) (c0.lo.z, c0.hi.z,
+// c1.lo.z, c1.hi.z) (child0, child1 as int bits). child >= 0: node index;
+// child < 0: leaf, ~child = (first triangle << 4) | count.
+// Triangle = 3 float4: (v0, id) (e1 = v1 - v0, obj) (e2 = v2 - v0, flags).
+
+struct Ray {
+    V3 o, d, inv, oi;   // oi = o * inv
+};
+__device__ __forceinline__ float safe_inv(float d) {
+    return 1.0f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d));
+}
+__device__ __forceinline__ Ray make_ray(V3 o, V3 d) {
+    Ray r;
+    r.o = o;
+    r.d = d;
+    r.inv = v3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    return r;
+}
+
+// Slab test of both children of a node against [tmin, tmax]: hit flags and entry distances.
+__device__ __forceinline__ void child_boxes(const Ray &r, float4 n0, float4 n1, float4 n2, float tmin, float tmax,
+                                            float &t0, float &t1, bool &h0, bool &h1) {
+    float ax0 = fmaf(n0.x, r.inv.x, -r.oi.x), ax1 = fmaf(n0.y, r.inv.x, -r.oi.x);
+    float ay0 = fmaf(n0.z, r.inv.y, -r.oi.y), ay1 = fmaf(n0.w, r.inv.y, -r.oi.y);
+    float az0 = fmaf(n2.x, r.inv.z, -r.oi.z), az1 = fmaf(n2.y, r.inv.z, -r.oi.z);
+    float bx0 = fmaf(n1.x, r.inv.x, -r.oi.x), bx1 = fmaf(n1.y, r.inv.x, -r.oi.x);
+    float by0 = fmaf(n1.z, r.inv.y, -r.oi.y), by1 = fmaf(n1.w, r.inv.y, -r.oi.y);
+    float bz0 = fmaf(n2.z, r.inv.z, -r.oi.z), bz1 = fmaf(n2.w, r.inv.z, -r.oi.z);
+    float alo = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), tmin));
+    float ahi = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), tmax));
+    float blo = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), tmin));
+    float bhi = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), tmax));
+    h0 = alo <= ahi;
+    h1 = blo <= bhi;
+    t0 = alo;
+    t1 = blo;
+}
+
+// Moller-Trumbore, double sided: returns t of the plane hit inside the
+// triangle (u >= 0, v >= 0, u + v <= 1), or +inf.
+__device__ __forceinline__ float mt_intersect(const Ray &r, V3 v0, V3 e1, V3 e2) {
+    V3 p = cross(r.d, e2);
+    float det = dot(e1, p);
+    if (det == 0.0f) return __int_as_float(0x7f800000);
+    float inv = 1.0f / det;
+    V3 s = r.o - v0;
+    float u = dot(s, p) * inv;
+    if (u < 0.0f || u > 1.0f) return __int_as_float(0x7f800000);
+    V3 q = cross(s, e1);
+    float v = dot(r.d, q) * inv;
+    if (v < 0.0f || u + v > 1.0f) return __int_as_float(0x7f800000);
+    return dot(e2, q) * inv;
+}
+
+struct Hit {
+    float t;
+    int prim;   // original triangle id, -1 = none
+};
+
+// Closest hit with t in (tmin, tmax]; ties on t go to the lower triangle id.
+// excl_prim: triangle skipped; excl_obj >= 0: every triangle of that object skipped.
+// The hierarchy starts at node `root` (0 for the global one).
+// With COUNT, interior nodes visited and triangles tested are added to *cnt.
+struct TravCount {
+    unsigned long long nodes = 0, tris = 0;
+};
+template <bool COUNT = false>
+__device__ __forceinline__ Hit trace_closest(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                             int root, const Ray &r, float tmin, float tmax, int excl_prim,
+                                             int excl_obj, TravCount *cnt = nullptr) {
+    Hit h;
+    h.t = tmax;
+    h.prim = -1;
+    int stack[kStackSize];
+    int sp = 0;
+    int node = root;
+    for (;;) {
+        if (node >= 0) {
+            if (COUNT) ++cnt->nodes;
+            float4 n0 = __ldg(nodes + 4 * node + 0);
+            float4 n1 = __ldg(nodes + 4 * node + 1);
+            float4 n2 = __ldg(nodes + 4 * node + 2);
+            float4 n3 = __ldg(nodes + 4 * node + 3);
+            float ta, tb;
+            bool ha, hb;
+            child_boxes(r, n0, n1, n2, tmin, h.t, ta, tb, ha, hb);
+            int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+            if (ha && hb) {
+                int near = ta <= tb ? ca : cb, far = ta <= tb ? cb : ca;
+                if (sp < kStackSize) stack[sp++] = far;
+                node = near;
+                continue;
+            }
+            if (ha) { node = ca; continue; }
+            if (hb) { node = cb; continue; }
+        } else {
+            int v = ~node;
+            int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
+            for (int i = 0; i < count; ++i) {
+                const float4 *tp = tris + 3 * (first + i);
+                float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+                int id = __float_as_int(a.w);
+                if (id == excl_prim || (excl_obj >= 0 && __float_as_int(b.w) == excl_obj)) continue;
+                if (COUNT) ++cnt->tris;
+                float t = mt_intersect(r, xyz(a), xyz(b), xyz(c));
+                if (t > tmin && (t < h.t || (t == h.t && (h.prim < 0 || id < h.prim)))) {
+                    h.t = t;
+                    h.prim = id;
+                }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return h;
+}
+
+// Shadow query over (tmin, tmax]. Returns true if occluded. Glass triangles
+// hit from their front (the ray enters the convex slab) are recorded once per
+// slab object in cross_obj/cross_tri (up to kMaxCross; one more occludes);
+// glass leaving faces are ignored; any other triangle occludes.
+struct Crossings {
+    int n;
+    int obj[kMaxCross];
+    int tri[kMaxCross];
+};
+template <bool COUNT = false>
+__device__ __forceinline__ bool trace_shadow(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                             int root, const Ray &r, float tmin, float tmax, int excl_prim,
+                                             Crossings &cr, TravCount *cnt = nullptr) {
+    int stack[kStackSize];
+    int sp = 0;
+    int node = root;
+    for (;;) {
+        if (node >= 0) {
+            if (COUNT) ++cnt->nodes;
+            float4 n0 = __ldg(nodes + 4 * node + 0);
+            float4 n1 = __ldg(nodes + 4 * node + 1);
+            float4 n2 = __ldg(nodes + 4 * node + 2);
+            float4 n3 = __ldg(nodes + 4 * node + 3);
+            float ta, tb;
+            bool ha, hb;
+            child_boxes(r, n0, n1, n2, tmin, tmax, ta, tb, ha, hb);
+            int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+            if (ha && hb) {
+                if (sp < kStackSize) stack[sp++] = cb;
+                node = ca;
+                continue;
+            }
+            if (ha) { node = ca; continue; }
+            if (hb) { node = cb; continue; }
+        } else {
+            int v = ~node;
+            int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
+            for (int i = 0; i < count; ++i) {
+                const float4 *tp = tris + 3 * (first + i);
+                float4 a = __ldg(tp), b = __ldg(tp + 1), c = __ldg(tp + 2);
+                int id = __float_as_int(a.w);
+                if (id == excl_prim) continue;
+                if (COUNT) ++cnt->tris;
+                V3 e1 = xyz(b), e2 = xyz(c);
+                float t = mt_intersect(r, xyz(a), e1, e2);
+                if (!(t > tmin && t <= tmax)) continue;
+                if (!(__float_as_uint(c.w) & kTriGlass)) return true;
+                if (dot(r.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
+                int ob = __float_as_int(b.w);
+                bool seen = false;
+                for (int q = 0; q < cr.n; ++q) seen |= cr.obj[q] == ob;
+                if (seen) continue;
+                if (cr.n >= kMaxCross) return true;
+                cr.obj[cr.n] = ob;
+                cr.tri[cr.n] = id;
+                ++cr.n;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------- optics
+// Fresnel reflectances |r_s|^2, |r_p|^2 for light arriving from vacuum onto a
+// medium of complex index n + ik (Eq. 1), cos_i = c in (0, 1].
+__device__ __forceinline__ void csqrt_f(float re, float im, float &a, float &b) {
+    float r = hypotf(re, im);
+    if (re >= 0.0f) {
+        a = sqrtf(0.5f * (r + re));
+        b = a > 0.0f ? im / (2.0f * a) : 0.0f;
+    } else {
+        b = copysignf(sqrtf(0.5f * (r - re)), im);
+        a = im / (2.0f * b);
+    }
+}
+__device__ __forceinline__ void fresnel_rs_rp(float c, float n, float k, float &Rs, float &Rp) {
+    // eta^2 = (n^2 - k^2) + 2nk i ; z = 1 - (1 - c^2) / eta^2
+    float er = n * n - k * k, ei = 2.0f * n * k;
+    float inv_m = 1.0f / (er * er + ei * ei);
+    float s2 = 1.0f - c * c;
+    float zr = 1.0f - s2 * er * inv_m, zi = s2 * ei * inv_m;
+    float ctr, cti;
+    csqrt_f(zr, zi, ctr, cti);
+    // eta * cos_t
+    float ar = n * ctr - k * cti, ai = n * cti + k * ctr;
+    // r_s = (c - eta ct) / (c + eta ct)
+    float num_r = c - ar, num_i = -ai, den_r = c + ar, den_i = ai;
+    Rs = (num_r * num_r + num_i * num_i) / (den_r * den_r + den_i * den_i);
+    // r_p = (eta c - ct) / (eta c + ct)
+    float pr = n * c, pi = k * c;
+    num_r = pr - ctr;
+    num_i = pi - cti;
+    den_r = pr + ctr;
+    den_i = pi + cti;
+    Rp = (num_r * num_r + num_i * num_i) / (den_r * den_r + den_i * den_i);
+}
+
+__device__ __forceinline__ float conductor_F(float c, float n, float k) {
+    if (c <= 0.0f) return 1.0f;
+    c = fminf(c, 1.0f);
+    float Rs, Rp;
+    fresnel_rs_rp(c, n, k, Rs, Rp);
+    return 0.5f * (Rs + Rp);
+}
+
+// Absorbing plane-parallel slab: multiple-reflection sums per polarisation.
+__device__ __forceinline__ void slab_RT(float c, float lam_nm, float n, float alpha, float thick, float &R,
+                                        float &T) {
+    if (c <= 0.0f) {
+        R = 1.0f;
+        T = 0.0f;
+        return;
+    }
+    c = fminf(c, 1.0f);
+    float k = alpha * lam_nm * (1e-9f / (4.0f * 3.14159265358979f));
+    float Rs, Rp;
+    fresnel_rs_rp(c, n, k, Rs, Rp);
+    float ctr = sqrtf(1.0f - (1.0f - c * c) / (n * n));
+    float tau = expf(-alpha * thick / ctr);
+    float t2 = tau * tau;
+    float ds = 1.0f / (1.0f - Rs * Rs * t2), dp = 1.0f / (1.0f - Rp * Rp * t2);
+    float qs = (1.0f - Rs) * (1.0f - Rs), qp = (1.0f - Rp) * (1.0f - Rp);
+    R = 0.5f * ((Rs + qs * Rs * t2 * ds) + (Rp + qp * Rp * t2 * dp));
+    T = 0.5f * (qs * tau * ds + qp * tau * dp);
+}
+
+// Glass branch probability: clamp(mean over bins of the lossless slab
+// reflectance 2 rho / (1 + rho), averaged over polarisations, 0.05, 0.95).
+// It decides an integer, so it is evaluated with explicitly rounded
+// operations in a fixed order (no contraction), matching a plain float
+// evaluation of the same formula.
+static __device__ __noinline__ float branch_proxy(float c, int L, const float *__restrict__ n) {
+    float s2 = __fsub_rn(1.0f, __fmul_rn(c, c));
+    float acc = 0.0f;
+    for (int i = 0; i < L; ++i) {
+        float ni = __ldg(n + i);
+        float x = __fsub_rn(1.0f, __fdiv_rn(s2, __fmul_rn(ni, ni)));
+        float rs2, rp2;
+        if (x <= 0.0f) {
+            rs2 = 1.0f;
+            rp2 = 1.0f;
+        } else {
+            float ct = __fsqrt_rn(x);
+            float a = __fsub_rn(c, __fmul_rn(ni, ct)), b = __fadd_rn(c, __fmul_rn(ni, ct));
+            float e = __fsub_rn(__fmul_rn(ni, c), ct), f = __fadd_rn(__fmul_rn(ni, c), ct);
+            float rs = __fdiv_rn(a, b), rp = __fdiv_rn(e, f);
+            rs2 = __fmul_rn(rs, rs);
+            rp2 = __fmul_rn(rp, rp);
+        }
+        float ps = __fdiv_rn(__fadd_rn(rs2, rs2), __fadd_rn(1.0f, rs2));
+        float pp = __fdiv_rn(__fadd_rn(rp2, rp2), __fadd_rn(1.0f, rp2));
+        acc = __fadd_rn(acc, __fmul_rn(0.5f, __fadd_rn(ps, pp)));
+    }
+    float m = __fdiv_rn(acc, (float)L);
+    return fminf(fmaxf(m, 0.05f), 0.95f);
+}
+
+// -------------------------------------------------------------- sampling
+// Cosine-distributed direction about unit ns: Malley's method on the
+// Shirley-Chiu concentric disk; tangent frame of Duff et al. (JCGT 2017).
+__device__ __forceinline__ V3 cosine_dir(V3 ns, float u0, float u1) {
+    float a = 2.0f * u0 - 1.0f, b = 2.0f * u1 - 1.0f;
+    float dx = 0.0f, dy = 0.0f;
+    if (a != 0.0f || b != 0.0f) {
+        float r, phi;
+        if (fabsf(a) > fabsf(b)) {
+            r = a;
+            phi = 0.78539816339744831f * (b / a);
+        } else {
+            r = b;
+            phi = 1.57079632679489662f - 0.78539816339744831f * (a / b);
+        }
+        float sp, cp;
+        sincosf(phi, &sp, &cp);
+        dx = r * cp;
+        dy = r * sp;
+    }
+    float dz = sqrtf(fmaxf(0.0f, 1.0f - dx * dx - dy * dy));
+    float sgn = ns.z >= 0.0f ? 1.0f : -1.0f;
+    float aa = -1.0f / (sgn + ns.z);
+    float bb = ns.x * ns.y * aa;
+    V3 t = v3(1.0f + sgn * ns.x * ns.x * aa, sgn * bb, -sgn * ns.x);
+    V3 bt = v3(bb, sgn + ns.y * ns.y * aa, -ns.y);
+    return dx * t + dy * bt + dz * ns;
+}
+
+// ----------------------------------------------------- compensated sums
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+struct Kahan3 {
+    Kahan x, y, z;
+    __device__ __forceinline__ void add(float a, float b, float c) {
+        x.add(a);
+        y.add(b);
+        z.add(c);
+    }
+};
+
+// ------------------------------------------------------------------ camera
+__device__ __forceinline__ void camera_ray(const RenderInfo &ri, float px, float py, V3 &o, V3 &d) {
+    float nx = 2.0f * px / (float)ri.width - 1.0f;
+    float ny = 1.0f - 2.0f * py / (float)ri.height;
+    V3 f = v3(ri.cam_f[0], ri.cam_f[1], ri.cam_f[2]);
+    V3 X = v3(ri.cam_x[0], ri.cam_x[1], ri.cam_x[2]);
+    V3 Y = v3(ri.cam_y[0], ri.cam_y[1], ri.cam_y[2]);
+    V3 c = v3(ri.cam_o[0], ri.cam_o[1], ri.cam_o[2]);
+    if (ri.ortho) {
+        o = c + nx * X + ny * Y;
+        d = f;
+    } else {
+        o = c;
+        d = normalize(f + nx * X + ny * Y);
+    }
+}
+
+// Render of a global path index (binary search over the batch table).
+__device__ __forceinline__ int find_render(const RenderBatch &rb, int64_t g) {
+    int lo = 0, hi = rb.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (rb.info[mid].path_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int find_render_pixel(const RenderBatch &rb, int64_t gp) {
+    int lo = 0, hi = rb.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (rb.info[mid].pixel_begin <= gp) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace sddm

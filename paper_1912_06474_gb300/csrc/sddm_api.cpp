@@ -1,0 +1,845 @@
+// C ABI of libsddm: context, scene validation and upload, build, render.
+//
+// The host side follows the paper's problem statement (Sec. 1-2: a room, its
+// materials' optical properties, natural light; Sec. 5: a decomposition of the
+// scene into subdomains) and drives the device kernels on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sddm_internal.h"
+#include "sddm_ddm.h"
+
+namespace sddm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return SDDM_ERR_CUDA;
+}
+
+static int fail(int code, const std::string &msg) {
+    set_error(msg);
+    return code;
+}
+
+// Owned device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t n) {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n;
+        return cudaSuccess;
+    }
+    template <typename T>
+    cudaError_t upload(const std::vector<T> &v, cudaStream_t s) {
+        cudaError_t e = ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+}  // namespace sddm
+
+using namespace sddm;
+
+struct sddm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    // spectrum
+    int L = 0;
+    std::vector<float> lam, quad_w, cmf;
+    // materials
+    std::vector<Material> mats;
+    // mesh
+    std::vector<float> V;
+    std::vector<uint32_t> F, mat_id, obj_id;
+    bool built = false;
+    sddm_build_opts opts{};
+    // device scene
+    DevBuf d_wcmf, d_lam, d_kind, d_a, d_b, d_c, d_thick, d_tri_n, d_tri_obj, d_light_v, d_light_cdf;
+    DevBuf d_gnodes, d_gtris;
+    float light_area = 0.f;
+    int n_light = 0;
+    DevScene dev{};
+    DDMScene ddm{};
+    DevBuf d_cell_nodes, d_cell_tris, d_cell_root;
+    // per-render scratch
+    DevBuf d_info, d_state, d_out_tab, d_aov_xyz_tab, d_aov_prim_tab, d_samples, d_first, d_counters, d_err;
+    DDMBuffers ddm_buf;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int profile = 0;
+};
+
+extern "C" {
+
+const char *sddm_last_error(void) { return g_last_error.c_str(); }
+
+const char *sddm_version(void) { return "sddm 0.1 sm_103a"; }
+
+int sddm_create(sddm_ctx **out, int device, void *stream) {
+    if (!out) return fail(SDDM_ERR_INVALID_ARG, "sddm_create: out is NULL");
+    *out = nullptr;
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_create: cudaGetDeviceCount");
+    if (device < 0 || device >= n_dev) return fail(SDDM_ERR_INVALID_ARG, "sddm_create: no such device");
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "sddm_create: cudaSetDevice");
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess)
+        return cuda_fail(e, "sddm_create: cudaGetDeviceProperties");
+    if ((e = check_kernel_image()) != cudaSuccess)
+        return cuda_fail(e, "sddm_create: no sm_103a kernel image for this device");
+    std::unique_ptr<sddm_ctx> c(new (std::nothrow) sddm_ctx());
+    if (!c) return fail(SDDM_ERR_OOM, "sddm_create: out of host memory");
+    c->device = device;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->sm_count = prop.multiProcessorCount;
+    if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess)
+        return cuda_fail(e, "sddm_create: cudaEventCreate");
+    *out = c.release();
+    return SDDM_OK;
+}
+
+int sddm_destroy(sddm_ctx *ctx) {
+    if (!ctx) return SDDM_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+    return SDDM_OK;
+}
+
+static bool finite_range(const float *p, int n, float lo, float hi) {
+    for (int i = 0; i < n; ++i)
+        if (!(p[i] >= lo && p[i] <= hi)) return false;
+    return true;
+}
+
+int sddm_set_spectrum(sddm_ctx *ctx, int L, const float *lambda_nm, const float *quad_w, const float *cmf_xyz) {
+    if (!ctx || !lambda_nm || !quad_w || !cmf_xyz) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_spectrum: NULL");
+    if (L < 1 || L > kMaxL) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_spectrum: L must be in 1..256");
+    if (!finite_range(lambda_nm, L, 1.0f, 1e5f) || !finite_range(quad_w, L, 0.0f, 1e6f) ||
+        !finite_range(cmf_xyz, 3 * L, -1e3f, 1e3f))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_set_spectrum: non-finite or out-of-range values");
+    ctx->L = L;
+    ctx->lam.assign(lambda_nm, lambda_nm + L);
+    ctx->quad_w.assign(quad_w, quad_w + L);
+    ctx->cmf.assign(cmf_xyz, cmf_xyz + 3 * L);
+    ctx->mats.clear();
+    ctx->built = false;
+    return SDDM_OK;
+}
+
+static int add_mat(sddm_ctx *ctx, Material &&m, uint32_t *mat, const char *who) {
+    if (ctx->mats.size() >= (1u << 20)) return fail(SDDM_ERR_INVALID_ARG, std::string(who) + ": too many materials");
+    ctx->mats.push_back(std::move(m));
+    if (mat) *mat = (uint32_t)(ctx->mats.size() - 1);
+    ctx->built = false;
+    return SDDM_OK;
+}
+
+#define NEED_SPECTRUM(who)                                                                        \
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, who ": ctx is NULL");                            \
+    if (ctx->L <= 0) return fail(SDDM_ERR_INVALID_ARG, who ": call sddm_set_spectrum first");
+
+int sddm_add_lambertian(sddm_ctx *ctx, const float *rho, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_lambertian");
+    if (!rho || !finite_range(rho, ctx->L, 0.0f, 1.0f))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_lambertian: rho must be in [0,1]");
+    Material m;
+    m.kind = kLambert;
+    m.a.assign(rho, rho + ctx->L);
+    return add_mat(ctx, std::move(m), mat, "sddm_add_lambertian");
+}
+
+int sddm_add_conductor(sddm_ctx *ctx, const float *n, const float *k, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_conductor");
+    if (!n || !k || !finite_range(n, ctx->L, 1e-4f, 100.f) || !finite_range(k, ctx->L, 0.0f, 100.f))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_conductor: need n in (0,100], k in [0,100]");
+    Material m;
+    m.kind = kConductor;
+    m.a.assign(n, n + ctx->L);
+    m.b.assign(k, k + ctx->L);
+    return add_mat(ctx, std::move(m), mat, "sddm_add_conductor");
+}
+
+int sddm_add_glass_slab(sddm_ctx *ctx, const float *n, const float *alpha_clear, const float *dalpha,
+                        float thickness_m, float s_default, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_glass_slab");
+    if (!n || !alpha_clear || !dalpha || !finite_range(n, ctx->L, 1.0f, 10.f) ||
+        !finite_range(alpha_clear, ctx->L, 0.0f, 1e7f) || !finite_range(dalpha, ctx->L, -1e7f, 1e7f) ||
+        !(thickness_m > 0.0f && thickness_m < 1.0f) || !(s_default >= 0.0f && s_default <= 1.0f))
+        return fail(SDDM_ERR_INVALID_ARG,
+                    "sddm_add_glass_slab: need n in [1,10], alpha >= 0, 0 < thickness < 1 m, s in [0,1]");
+    for (int i = 0; i < ctx->L; ++i)
+        if (alpha_clear[i] + dalpha[i] < 0.0f)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_add_glass_slab: alpha_clear + dalpha must stay >= 0");
+    Material m;
+    m.kind = kGlass;
+    m.a.assign(n, n + ctx->L);
+    m.b.assign(alpha_clear, alpha_clear + ctx->L);
+    m.c.assign(dalpha, dalpha + ctx->L);
+    m.thick = thickness_m;
+    m.s_default = s_default;
+    return add_mat(ctx, std::move(m), mat, "sddm_add_glass_slab");
+}
+
+int sddm_add_emitter(sddm_ctx *ctx, const float *Le, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_emitter");
+    if (!Le || !finite_range(Le, ctx->L, 0.0f, 1e12f)) return fail(SDDM_ERR_INVALID_ARG, "sddm_add_emitter: Le >= 0");
+    Material m;
+    m.kind = kEmitter;
+    m.a.assign(Le, Le + ctx->L);
+    return add_mat(ctx, std::move(m), mat, "sddm_add_emitter");
+}
+
+int sddm_add_diffuse_emitter(sddm_ctx *ctx, const float *rho, const float *Le, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_diffuse_emitter");
+    if (!Le || !rho || !finite_range(Le, ctx->L, 0.0f, 1e12f) || !finite_range(rho, ctx->L, 0.0f, 1.0f))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_diffuse_emitter: Le >= 0, rho in [0,1]");
+    Material m;
+    m.kind = kDiffuseEmitter;
+    m.a.assign(Le, Le + ctx->L);
+    m.b.assign(rho, rho + ctx->L);
+    return add_mat(ctx, std::move(m), mat, "sddm_add_diffuse_emitter");
+}
+
+int sddm_set_mesh(sddm_ctx *ctx, const float *v, int nv, const uint32_t *tri, int nt, const uint32_t *mat_id,
+                  const uint32_t *obj_id) {
+    if (!ctx || !v || !tri || !mat_id || !obj_id) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: NULL");
+    if (nv < 3 || nt < 1 || nt > (1 << 26)) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: bad nv/nt");
+    for (int64_t i = 0; i < 3LL * nv; ++i)
+        if (!std::isfinite(v[i]) || std::fabs(v[i]) > 1e6f)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: non-finite or huge vertex coordinate");
+    for (int64_t i = 0; i < 3LL * nt; ++i)
+        if (tri[i] >= (uint32_t)nv) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: vertex index out of range");
+    for (int i = 0; i < nt; ++i) {
+        if (mat_id[i] >= ctx->mats.size())
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: material id out of range (add materials first)");
+        if (obj_id[i] > 0x7fffffffu) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_mesh: obj id too large");
+    }
+    ctx->V.assign(v, v + 3LL * nv);
+    ctx->F.assign(tri, tri + 3LL * nt);
+    ctx->mat_id.assign(mat_id, mat_id + nt);
+    ctx->obj_id.assign(obj_id, obj_id + nt);
+    ctx->built = false;
+    return SDDM_OK;
+}
+
+static void default_opts(sddm_build_opts &o) {
+    for (int a = 0; a < 3; ++a)
+        if (o.grid[a] <= 0) o.grid[a] = 1;
+    if (o.leaf_size <= 0) o.leaf_size = 4;
+    if (o.sah_bins <= 0) o.sah_bins = 16;
+}
+
+int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_build: ctx is NULL");
+    if (ctx->L <= 0 || ctx->mats.empty() || ctx->F.empty())
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_build: spectrum, materials and mesh are required");
+    sddm_build_opts o{};
+    if (opts) o = *opts;
+    default_opts(o);
+    if (o.grid[0] > 64 || o.grid[1] > 64 || o.grid[2] > 64 || o.leaf_size > kMaxLeaf || o.sah_bins < 4 ||
+        o.sah_bins > 64 || o.queue_capacity < 0 || o.blocks_per_sm < 0 || o.blocks_per_sm > 32 ||
+        o.paths_in_flight < 0)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_build: options out of range");
+    // every mesh material must exist (the material list may have changed since set_mesh)
+    for (uint32_t m : ctx->mat_id)
+        if (m >= ctx->mats.size()) return fail(SDDM_ERR_INVALID_ARG, "sddm_build: mesh references a missing material");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_build: cudaSetDevice");
+    const int L = ctx->L, M = (int)ctx->mats.size(), nt = (int)ctx->mat_id.size();
+
+    // --- triangles, normals, lights (normals and areas in double, rounded once)
+    std::vector<BuildTri> tris(nt);
+    std::vector<float4> tri_n(nt);
+    std::vector<int> tri_obj(nt);
+    std::vector<float4> light_v;
+    std::vector<double> light_cum;
+    double light_total = 0.0;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int t = 0; t < nt; ++t) {
+        BuildTri &bt = tris[t];
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a) {
+                bt.v[k][a] = ctx->V[3 * (size_t)ctx->F[3 * (size_t)t + k] + a];
+                lo[a] = std::min(lo[a], bt.v[k][a]);
+                hi[a] = std::max(hi[a], bt.v[k][a]);
+            }
+        const int kind = ctx->mats[ctx->mat_id[t]].kind;
+        bt.id = (uint32_t)t;
+        bt.obj = ctx->obj_id[t];
+        bt.flags = kind == kGlass ? kTriGlass : 0u;
+        double e1[3], e2[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = (double)bt.v[1][a] - bt.v[0][a];
+            e2[a] = (double)bt.v[2][a] - bt.v[0][a];
+        }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        int mid = (int)ctx->mat_id[t];
+        float fm;
+        std::memcpy(&fm, &mid, 4);
+        tri_n[t] = len > 0 ? make_float4((float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), fm)
+                           : make_float4(0.f, 0.f, 0.f, fm);
+        tri_obj[t] = (int)ctx->obj_id[t];
+        if (kind == kEmitter || kind == kDiffuseEmitter) {
+            light_total += 0.5 * len;
+            light_cum.push_back(light_total);
+            float ft;
+            std::memcpy(&ft, &t, 4);
+            light_v.push_back(make_float4(bt.v[0][0], bt.v[0][1], bt.v[0][2], ft));
+            light_v.push_back(make_float4(bt.v[1][0], bt.v[1][1], bt.v[1][2], 0.f));
+            light_v.push_back(make_float4(bt.v[2][0], bt.v[2][1], bt.v[2][2], 0.f));
+        }
+    }
+    std::vector<float> light_cdf(light_cum.size());
+    for (size_t i = 0; i < light_cum.size(); ++i) light_cdf[i] = (float)(light_cum[i] / light_total);
+
+    // --- materials, spectral weights
+    std::vector<float> wcmf(3 * (size_t)L), A((size_t)M * L, 0.f), B((size_t)M * L, 0.f), Cc((size_t)M * L, 0.f),
+        thick(M, 0.f);
+    std::vector<int> kinds(M);
+    for (int i = 0; i < L; ++i)
+        for (int c = 0; c < 3; ++c) wcmf[3 * i + c] = ctx->quad_w[i] * ctx->cmf[3 * i + c];
+    for (int m = 0; m < M; ++m) {
+        const Material &mt = ctx->mats[m];
+        kinds[m] = mt.kind;
+        for (int i = 0; i < L; ++i) {
+            if (!mt.a.empty()) A[(size_t)m * L + i] = mt.a[i];
+            if (!mt.b.empty()) B[(size_t)m * L + i] = mt.b[i];
+            if (!mt.c.empty()) Cc[(size_t)m * L + i] = mt.c[i];
+        }
+        thick[m] = mt.thick;
+    }
+
+    // --- hierarchies: global, and the subdomain grid
+    int n_threads = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<uint32_t> all(nt);
+    for (int t = 0; t < nt; ++t) all[t] = (uint32_t)t;
+    float glo[3], ghi[3];
+    for (int a = 0; a < 3; ++a) {
+        float pad = 1e-4f + 1e-5f * std::max(std::fabs(lo[a]), std::fabs(hi[a]));
+        glo[a] = lo[a] - pad;
+        ghi[a] = hi[a] + pad;
+    }
+    PackedBVH global;
+    build_bvh(tris, all, glo, ghi, o.leaf_size, o.sah_bins, global);
+    std::vector<PackedBVH> cells;
+    build_grid(tris, o.grid, glo, ghi, o.leaf_size, o.sah_bins, cells, n_threads);
+    std::vector<float4> cell_nodes, cell_tris;
+    std::vector<int> cell_root;
+    int64_t tri_base_check = 0;
+    for (auto &c : cells) {
+        int node_base = (int)(cell_nodes.size() / 4);
+        int tri_base = (int)(cell_tris.size() / 3);
+        cell_root.push_back(node_base);
+        // rebase child codes
+        for (size_t k = 0; k < c.nodes.size(); k += 4) {
+            float4 n3 = c.nodes[k + 3];
+            int ch[2];
+            std::memcpy(&ch[0], &n3.x, 4);
+            std::memcpy(&ch[1], &n3.y, 4);
+            for (int q = 0; q < 2; ++q) {
+                if (ch[q] >= 0) {
+                    ch[q] += node_base;
+                } else {
+                    int v = ~ch[q];
+                    int first = (v >> kLeafBits) + tri_base, cnt = v & ((1 << kLeafBits) - 1);
+                    ch[q] = ~((first << kLeafBits) | cnt);
+                }
+            }
+            std::memcpy(&n3.x, &ch[0], 4);
+            std::memcpy(&n3.y, &ch[1], 4);
+            c.nodes[k + 3] = n3;
+        }
+        cell_nodes.insert(cell_nodes.end(), c.nodes.begin(), c.nodes.end());
+        cell_tris.insert(cell_tris.end(), c.tris.begin(), c.tris.end());
+        tri_base_check += (int64_t)c.tris.size() / 3;
+    }
+    if (tri_base_check >= (1LL << (31 - kLeafBits)) || (int64_t)global.tris.size() / 3 >= (1LL << (31 - kLeafBits)))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_build: too many triangle references for the leaf encoding");
+
+    // --- upload
+    cudaStream_t s = ctx->stream;
+    if ((e = ctx->d_wcmf.upload(wcmf, s)) || (e = ctx->d_lam.upload(ctx->lam, s)) ||
+        (e = ctx->d_kind.upload(kinds, s)) || (e = ctx->d_a.upload(A, s)) || (e = ctx->d_b.upload(B, s)) ||
+        (e = ctx->d_c.upload(Cc, s)) || (e = ctx->d_thick.upload(thick, s)) || (e = ctx->d_tri_n.upload(tri_n, s)) ||
+        (e = ctx->d_tri_obj.upload(tri_obj, s)) || (e = ctx->d_light_v.upload(light_v, s)) ||
+        (e = ctx->d_light_cdf.upload(light_cdf, s)) || (e = ctx->d_gnodes.upload(global.nodes, s)) ||
+        (e = ctx->d_gtris.upload(global.tris, s)) || (e = ctx->d_cell_nodes.upload(cell_nodes, s)) ||
+        (e = ctx->d_cell_tris.upload(cell_tris, s)) || (e = ctx->d_cell_root.upload(cell_root, s)))
+        return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_build: device allocation failed")
+                                              : cuda_fail(e, "sddm_build: upload");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sddm_build: synchronize");
+
+    DevScene &d = ctx->dev;
+    d.L = L;
+    d.n_mat = M;
+    d.wcmf = ctx->d_wcmf.as<float>();
+    d.lam = ctx->d_lam.as<float>();
+    d.mat_kind = ctx->d_kind.as<int>();
+    d.mat_a = ctx->d_a.as<float>();
+    d.mat_b = ctx->d_b.as<float>();
+    d.mat_c = ctx->d_c.as<float>();
+    d.mat_thick = ctx->d_thick.as<float>();
+    d.tri_n = ctx->d_tri_n.as<float4>();
+    d.tri_obj = ctx->d_tri_obj.as<int>();
+    d.n_light = (int)light_cdf.size();
+    d.light_v = ctx->d_light_v.as<float4>();
+    d.light_cdf = ctx->d_light_cdf.as<float>();
+    d.light_area = (float)light_total;
+    d.g_nodes = ctx->d_gnodes.as<float4>();
+    d.g_tris = ctx->d_gtris.as<float4>();
+
+    DDMScene &g = ctx->ddm;
+    for (int a = 0; a < 3; ++a) {
+        g.dims[a] = o.grid[a];
+        g.lo[a] = glo[a];
+        g.hi[a] = ghi[a];
+        g.cell[a] = (ghi[a] - glo[a]) / (float)o.grid[a];
+        g.inv_cell[a] = 1.0f / g.cell[a];
+    }
+    double diag = std::sqrt((double)(ghi[0] - glo[0]) * (ghi[0] - glo[0]) + (double)(ghi[1] - glo[1]) * (ghi[1] - glo[1]) +
+                            (double)(ghi[2] - glo[2]) * (ghi[2] - glo[2]));
+    g.eps = (float)(1e-6 * diag);
+    g.n_cells = o.grid[0] * o.grid[1] * o.grid[2];
+    g.nodes = ctx->d_cell_nodes.as<float4>();
+    g.tris = ctx->d_cell_tris.as<float4>();
+    g.root = ctx->d_cell_root.as<int>();
+    ctx->opts = o;
+    ctx->built = true;
+    return SDDM_OK;
+}
+
+// ---------------------------------------------------------------- render
+static int validate_desc(const sddm_ctx *ctx, const sddm_render_desc *d, int n) {
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_render: ctx is NULL");
+    if (!ctx->built) return fail(SDDM_ERR_NOT_BUILT, "sddm_render: call sddm_build first");
+    if (!d || n < 1 || n > 4096) return fail(SDDM_ERR_INVALID_ARG, "sddm_render: need 1..4096 descriptors");
+    for (int r = 0; r < n; ++r) {
+        const sddm_render_desc &x = d[r];
+        if (x.width < 1 || x.height < 1 || x.spp < 1 || x.width > 65536 || x.height > 65536 || x.spp > 65536)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: width/height/spp out of range");
+        if ((int64_t)x.width * x.height > 0xffffffffLL)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: more pixels than the 32-bit counter word holds");
+        if (x.max_depth < 1 || x.max_depth > kMaxDepth)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: max_depth must be in 1..64");
+        if (!x.xyz_out) return fail(SDDM_ERR_INVALID_ARG, "sddm_render: xyz_out is NULL");
+        if (x.method != d[0].method || x.bsdf_mode != d[0].bsdf_mode)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: renders of one call must share method and bsdf_mode");
+        if (x.method != SDDM_METHOD_MEGAKERNEL && x.method != SDDM_METHOD_DDM)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: unknown method");
+        if (x.bsdf_mode != SDDM_BSDF_EXACT && x.bsdf_mode != SDDM_BSDF_MLP)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: unknown bsdf_mode");
+        const sddm_camera &c = x.camera;
+        float f[3] = {c.look[0] - c.pos[0], c.look[1] - c.pos[1], c.look[2] - c.pos[2]};
+        float fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        float cr[3] = {f[1] * c.up[2] - f[2] * c.up[1], f[2] * c.up[0] - f[0] * c.up[2], f[0] * c.up[1] - f[1] * c.up[0]};
+        float crl = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        if (!(fl > 0) || !(crl > 1e-6f * fl) || !std::isfinite(fl))
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: degenerate camera (look == pos or up parallel)");
+        if (!(c.ortho_height > 0) && !(c.vfov_deg > 0.0f && c.vfov_deg < 179.0f))
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: vfov_deg must be in (0, 179)");
+        if (x.glass_s)
+            for (size_t m = 0; m < ctx->mats.size(); ++m)
+                if (x.glass_s[m] > 1.0f || std::isnan(x.glass_s[m]))
+                    return fail(SDDM_ERR_INVALID_ARG, "sddm_render: glass_s entries must be <= 1 (negative = default)");
+    }
+    return SDDM_OK;
+}
+
+// Camera frame in double from the float inputs, rounded once.
+static void camera_frame(const sddm_render_desc &x, RenderInfo &ri) {
+    const sddm_camera &c = x.camera;
+    double f[3], r[3], u[3];
+    for (int a = 0; a < 3; ++a) f[a] = (double)c.look[a] - c.pos[a];
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] /= fl;
+    r[0] = f[1] * c.up[2] - f[2] * c.up[1];
+    r[1] = f[2] * c.up[0] - f[0] * c.up[2];
+    r[2] = f[0] * c.up[1] - f[1] * c.up[0];
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] /= rl;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    double aspect = (double)x.width / (double)x.height;
+    double sy, sx;
+    if (c.ortho_height > 0) {
+        sy = 0.5 * (double)c.ortho_height;
+        ri.ortho = 1;
+    } else {
+        sy = std::tan(0.5 * (double)c.vfov_deg * 3.14159265358979323846 / 180.0);
+        ri.ortho = 0;
+    }
+    sx = sy * aspect;
+    for (int a = 0; a < 3; ++a) {
+        ri.cam_o[a] = c.pos[a];
+        ri.cam_f[a] = (float)f[a];
+        ri.cam_x[a] = (float)(sx * r[a]);
+        ri.cam_y[a] = (float)(sy * u[a]);
+    }
+}
+
+int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st) {
+    int rc = validate_desc(ctx, d, n);
+    if (rc != SDDM_OK) return rc;
+    if (d[0].bsdf_mode == SDDM_BSDF_MLP)
+        return fail(SDDM_ERR_MLP_UNTRAINED, "sddm_render: SDDM_BSDF_MLP needs trained weights");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_render: cudaSetDevice");
+    const int M = (int)ctx->mats.size();
+    std::vector<RenderInfo> info(n);
+    std::vector<float> state((size_t)n * M);
+    std::vector<float *> outs(n), aov_x(n);
+    std::vector<int32_t *> aov_p(n);
+    int64_t paths = 0, pixels = 0;
+    bool any_aov = false;
+    for (int r = 0; r < n; ++r) {
+        const sddm_render_desc &x = d[r];
+        RenderInfo &ri = info[r];
+        std::memset(&ri, 0, sizeof(ri));
+        ri.path_begin = paths;
+        ri.pixel_begin = pixels;
+        ri.width = x.width;
+        ri.height = x.height;
+        ri.spp = x.spp;
+        ri.max_depth = x.max_depth;
+        ri.seed = x.seed;
+        ri.render_id = x.render_id;
+        ri.nee = x.nee ? 1 : 0;
+        ri.s_offset = r * M;
+        camera_frame(x, ri);
+        for (int m = 0; m < M; ++m)
+            state[(size_t)r * M + m] = (x.glass_s && x.glass_s[m] >= 0.0f) ? x.glass_s[m] : ctx->mats[m].s_default;
+        outs[r] = x.xyz_out;
+        aov_x[r] = x.aov_sample_xyz;
+        aov_p[r] = x.aov_first_prim;
+        any_aov |= x.aov_sample_xyz != nullptr || x.aov_first_prim != nullptr;
+        paths += (int64_t)x.width * x.height * x.spp;
+        pixels += (int64_t)x.width * x.height;
+    }
+    cudaStream_t s = ctx->stream;
+    if ((e = ctx->d_info.upload(info, s)) || (e = ctx->d_state.upload(state, s)) || (e = ctx->d_out_tab.upload(outs, s)) ||
+        (e = ctx->d_aov_xyz_tab.upload(aov_x, s)) || (e = ctx->d_aov_prim_tab.upload(aov_p, s)) ||
+        (e = ctx->d_counters.ensure(8 * sizeof(unsigned long long))) || (e = ctx->d_err.ensure(16)))
+        return cuda_fail(e, "sddm_render: upload of the render table");
+    if ((e = cudaMemsetAsync(ctx->d_counters.p, 0, 8 * sizeof(unsigned long long), s)) ||
+        (e = cudaMemsetAsync(ctx->d_err.p, 0, 16, s)))
+        return cuda_fail(e, "sddm_render: memset");
+    RenderBatch rb;
+    rb.info = ctx->d_info.as<RenderInfo>();
+    rb.n = n;
+    rb.state_s = ctx->d_state.as<float>();
+
+    // chunks of whole pixels, at most `cap` paths each
+    int64_t cap = ctx->opts.paths_in_flight > 0 ? ctx->opts.paths_in_flight : (int64_t)1 << 22;
+    int64_t max_spp = 1;
+    for (int r = 0; r < n; ++r) max_spp = std::max<int64_t>(max_spp, d[r].spp);
+    cap = std::max(cap, max_spp);
+
+    if ((e = cudaEventRecord(ctx->ev0, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: event");
+    ctx->ddm_buf.events_used = 0;
+    int64_t launches = 0;
+    const int time_trace = (ctx->profile & SDDM_PROFILE_TIME_TRACE) != 0;
+    const int count_trav = (ctx->profile & SDDM_PROFILE_COUNT_TRAVERSAL) != 0;
+    int64_t path0 = 0, pix0 = 0;
+    int rr = 0;   // render of pix0
+    while (path0 < paths) {
+        // extend the chunk pixel-row by pixel-row within renders
+        int64_t path1 = path0, pix1 = pix0;
+        int r = rr;
+        while (r < n) {
+            const RenderInfo &ri = info[r];
+            int64_t render_pix_end = ri.pixel_begin + (int64_t)ri.width * ri.height;
+            int64_t room = (cap - (path1 - path0)) / ri.spp;
+            if (room <= 0) break;
+            int64_t take = std::min(room, render_pix_end - pix1);
+            pix1 += take;
+            path1 += take * ri.spp;
+            if (pix1 == render_pix_end) ++r; else break;
+        }
+        const int64_t np = path1 - path0;
+        if ((e = ctx->d_samples.ensure((size_t)np * 3 * sizeof(float))) ||
+            (any_aov && (e = ctx->d_first.ensure((size_t)np * sizeof(int32_t)))))
+            return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render: scratch allocation failed")
+                                                  : cuda_fail(e, "sddm_render: scratch");
+        if (d[0].method == SDDM_METHOD_MEGAKERNEL) {
+            MegaArgs a;
+            a.sc = ctx->dev;
+            a.rb = rb;
+            a.path_begin = path0;
+            a.path_count = np;
+            a.sample_xyz = ctx->d_samples.as<float>();
+            a.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+            a.counters = ctx->d_counters.as<unsigned long long>();
+            a.error_flag = ctx->d_err.as<int>();
+            a.count_traversal = count_trav;
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            if (time_trace) {
+                if ((e = ctx->ddm_buf.event_pair(t0, t1)) || (e = cudaEventRecord(t0, s)))
+                    return cuda_fail(e, "sddm_render: events");
+            }
+            if ((e = launch_megakernel(a, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: megakernel launch");
+            if (time_trace && (e = cudaEventRecord(t1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
+            launches += 1;
+        } else {
+            DDMRun run;
+            run.sc = ctx->dev;
+            run.g = ctx->ddm;
+            run.rb = rb;
+            run.path_begin = path0;
+            run.path_count = np;
+            run.max_depth = 1;
+            for (int q = 0; q < n; ++q) run.max_depth = std::max(run.max_depth, d[q].max_depth);
+            run.sample_xyz = ctx->d_samples.as<float>();
+            run.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+            run.counters = ctx->d_counters.as<unsigned long long>();
+            run.error_flag = ctx->d_err.as<int>();
+            run.sm_count = ctx->sm_count;
+            run.blocks_per_sm = ctx->opts.blocks_per_sm;
+            run.queue_capacity = ctx->opts.queue_capacity;
+            run.bsdf_mode = d[0].bsdf_mode;
+            run.time_trace = time_trace;
+            run.count_traversal = count_trav;
+            run.launches = &launches;
+            int rc2 = ddm_trace_chunk(run, ctx->ddm_buf, s);
+            if (rc2 != SDDM_OK) return rc2;
+        }
+        ReduceArgs ra;
+        ra.rb = rb;
+        ra.path_begin = path0;
+        ra.sample_xyz = ctx->d_samples.as<float>();
+        ra.xyz_out = ctx->d_out_tab.as<float *>();
+        ra.aov_xyz = ctx->d_aov_xyz_tab.as<float *>();
+        ra.aov_prim = ctx->d_aov_prim_tab.as<int32_t *>();
+        ra.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+        if ((e = launch_reduce_pixels(ra, pix0, pix1 - pix0, s)) != cudaSuccess)
+            return cuda_fail(e, "sddm_render: reduce launch");
+        launches += 1;
+        path0 = path1;
+        pix0 = pix1;
+        rr = r;
+        while (rr < n && pix0 >= info[rr].pixel_begin + (int64_t)info[rr].width * info[rr].height) ++rr;
+    }
+    if ((e = cudaEventRecord(ctx->ev1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: event");
+    unsigned long long cnt[8];
+    int err[4];
+    if ((e = cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "sddm_render: kernel execution");
+    if (err[0] != 0) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "sddm_render: device reported error %d (detail %d, %d)", err[0], err[1], err[2]);
+        return fail(err[0] == 1 ? SDDM_ERR_QUEUE_OVERFLOW : (err[0] == 2 ? SDDM_ERR_TIMEOUT : SDDM_ERR_DEVICE_CHECK),
+                    msg);
+    }
+    if (st) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        st->paths = paths;
+        st->segments_ext = (int64_t)cnt[0];
+        st->segments_shadow = (int64_t)cnt[1];
+        st->glass_queries = (int64_t)cnt[2];
+        st->crossings = (int64_t)cnt[3];
+        st->mlp_fallbacks = (int64_t)cnt[4];
+        st->gpu_ms = ms;
+        st->kernel_launches = launches;
+        st->node_visits = count_trav ? (int64_t)cnt[5] : 0;
+        st->tri_tests = count_trav ? (int64_t)cnt[6] : 0;
+        st->ray_visits = count_trav ? (int64_t)cnt[7] : 0;
+        double tms = 0.0;
+        for (int k = 0; k + 1 < ctx->ddm_buf.events_used; k += 2) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ctx->ddm_buf.events[k], ctx->ddm_buf.events[k + 1]);
+            tms += x;
+        }
+        st->trace_ms = tms;
+        st->trace_launches = ctx->ddm_buf.events_used / 2;
+    }
+    return SDDM_OK;
+}
+
+int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st) {
+    int rc = validate_desc(ctx, d, n);
+    if (rc != SDDM_OK) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_render_host: cudaSetDevice");
+    std::vector<sddm_render_desc> dd(d, d + n);
+    std::vector<void *> bufs;
+    auto cleanup = [&]() {
+        for (void *p : bufs) cudaFree(p);
+    };
+    for (int r = 0; r < n; ++r) {
+        size_t px = (size_t)d[r].width * d[r].height;
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, px * 3 * sizeof(float))) != cudaSuccess) {
+            cleanup();
+            return fail(SDDM_ERR_OOM, "sddm_render_host: device allocation failed");
+        }
+        bufs.push_back(p);
+        dd[r].xyz_out = (float *)p;
+        dd[r].aov_sample_xyz = nullptr;
+        dd[r].aov_first_prim = nullptr;
+        if (d[r].aov_sample_xyz) {
+            if ((e = cudaMalloc(&p, px * d[r].spp * 3 * sizeof(float))) != cudaSuccess) {
+                cleanup();
+                return fail(SDDM_ERR_OOM, "sddm_render_host: device allocation failed");
+            }
+            bufs.push_back(p);
+            dd[r].aov_sample_xyz = (float *)p;
+        }
+        if (d[r].aov_first_prim) {
+            if ((e = cudaMalloc(&p, px * d[r].spp * sizeof(int32_t))) != cudaSuccess) {
+                cleanup();
+                return fail(SDDM_ERR_OOM, "sddm_render_host: device allocation failed");
+            }
+            bufs.push_back(p);
+            dd[r].aov_first_prim = (int32_t *)p;
+        }
+    }
+    rc = sddm_render(ctx, dd.data(), n, st);
+    for (int r = 0; r < n && rc == SDDM_OK; ++r) {
+        size_t px = (size_t)d[r].width * d[r].height;
+        if ((e = cudaMemcpyAsync(d[r].xyz_out, dd[r].xyz_out, px * 3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                 ctx->stream)) ||
+            (d[r].aov_sample_xyz &&
+             (e = cudaMemcpyAsync(d[r].aov_sample_xyz, dd[r].aov_sample_xyz, px * d[r].spp * 3 * sizeof(float),
+                                  cudaMemcpyDeviceToHost, ctx->stream))) ||
+            (d[r].aov_first_prim &&
+             (e = cudaMemcpyAsync(d[r].aov_first_prim, dd[r].aov_first_prim, px * d[r].spp * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream))))
+            rc = cuda_fail(e, "sddm_render_host: copy back");
+    }
+    if (rc == SDDM_OK && (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+        rc = cuda_fail(e, "sddm_render_host: synchronize");
+    cleanup();
+    return rc;
+}
+
+// Pilot-timed choice of subdomain grid, persistent blocks per SM and paths in
+// flight (Sec. 5's load balancing, settled here by measurement).
+int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_opts *best) {
+    if (!ctx || !d || !best) return fail(SDDM_ERR_INVALID_ARG, "sddm_autotune: NULL argument");
+    if (ctx->L <= 0 || ctx->mats.empty() || ctx->F.empty())
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_autotune: spectrum, materials and mesh are required");
+    sddm_build_opts base = ctx->built ? ctx->opts : sddm_build_opts{};
+    default_opts(base);
+    // pilot: the same renders at 1 spp and at most 512 x 512 pixels
+    std::vector<sddm_render_desc> pilot(d, d + n);
+    std::vector<void *> bufs;
+    int rc = SDDM_OK;
+    for (auto &p : pilot) {
+        p.spp = 1;
+        p.width = std::min(p.width, 512);
+        p.height = std::min(p.height, 512);
+        p.method = SDDM_METHOD_DDM;
+        p.aov_sample_xyz = nullptr;
+        p.aov_first_prim = nullptr;
+        void *q = nullptr;
+        if (cudaMalloc(&q, (size_t)p.width * p.height * 3 * sizeof(float)) != cudaSuccess) {
+            rc = fail(SDDM_ERR_OOM, "sddm_autotune: pilot output allocation failed");
+            break;
+        }
+        bufs.push_back(q);
+        p.xyz_out = (float *)q;
+    }
+    const int grids[][3] = {{1, 1, 1}, {2, 2, 2}, {4, 4, 2}, {8, 4, 4}};
+    const int bps_list[] = {4, 8, 16};
+    double best_rate = -1.0;
+    sddm_build_opts chosen = base;
+    for (const auto &gdim : grids) {
+        if (rc != SDDM_OK) break;
+        sddm_build_opts o = base;
+        for (int a = 0; a < 3; ++a) o.grid[a] = gdim[a];
+        if ((rc = sddm_build(ctx, &o)) != SDDM_OK) break;
+        for (int bps : bps_list) {
+            ctx->opts.blocks_per_sm = bps;
+            sddm_stats st{};
+            if ((rc = sddm_render(ctx, pilot.data(), n, &st)) != SDDM_OK) break;   // warm-up
+            if ((rc = sddm_render(ctx, pilot.data(), n, &st)) != SDDM_OK) break;
+            double rate = (double)(st.segments_ext + st.segments_shadow) / std::max(st.gpu_ms, 1e-6);
+            if (rate > best_rate) {
+                best_rate = rate;
+                chosen = ctx->opts;
+            }
+        }
+    }
+    for (void *q : bufs) cudaFree(q);
+    if (rc != SDDM_OK) return rc;
+    if ((rc = sddm_build(ctx, &chosen)) != SDDM_OK) return rc;
+    *best = chosen;
+    return SDDM_OK;
+}
+
+int sddm_set_profiling(sddm_ctx *ctx, int flags) {
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: ctx is NULL");
+    if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: unknown flag");
+    ctx->profile = flags;
+    return SDDM_OK;
+}
+
+int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, const int32_t *bin, const float *s,
+                    const float *thickness_m, float *R, float *T, int mode) {
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: ctx is NULL");
+    if (!ctx->built) return fail(SDDM_ERR_NOT_BUILT, "sddm_glass_eval: call sddm_build first");
+    if (mat >= ctx->mats.size() || ctx->mats[mat].kind != kGlass)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: mat is not a glass slab");
+    if (n < 0 || (n > 0 && (!cos_theta || !bin || !s || !thickness_m || !R || !T)))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: bad arguments");
+    if (mode == SDDM_BSDF_MLP) return fail(SDDM_ERR_MLP_UNTRAINED, "sddm_glass_eval: no trained weights");
+    if (mode != SDDM_BSDF_EXACT) return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: unknown mode");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = launch_glass_eval(ctx->dev, mat, n, cos_theta, bin, s, thickness_m, R, T, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_glass_eval");
+}
+
+int sddm_philox(sddm_ctx *ctx, int n, const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out) {
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !out))) return fail(SDDM_ERR_INVALID_ARG, "sddm_philox: bad arguments");
+    if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_philox: ctr and out must be 16-byte aligned");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = launch_philox(n, ctr, key0, key1, out, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_philox");
+}
+
+}  // extern "C"
