@@ -107,13 +107,13 @@ def _dist():
     return world, rank, local
 
 
-def workload(method):
+def workload(method, width=512, height=512, spp=16):
     from paper_1912_06474_gb300 import scenes
     scene = scenes.hotel_room(L=41, seed=0)
-    spec = scenes.hotel_room_render(scene, 512, 512, 16, 5, seed=0)
+    spec = scenes.hotel_room_render(scene, width, height, spp, 5, seed=0)
     grid = (4, 4, 2) if method == "ddm" else (1, 1, 1)
-    cfg = {"workload": "hotel_room_512x512_16spp_d5_L41", "triangles": scene.n_tris, "width": 512,
-           "height": 512, "spp": 16, "max_depth": 5, "lambda_bins": 41, "method": method,
+    cfg = {"workload": f"hotel_room_{width}x{height}_{spp}spp_d5_L41", "triangles": scene.n_tris,
+           "width": width, "height": height, "spp": spp, "max_depth": 5, "lambda_bins": 41, "method": method,
            "grid": list(grid), "bsdf": "exact", "l2": "flushed between steps (256 MiB write)",
            "scaling_mode": "replicas"}
     return scene, spec, grid, cfg
@@ -147,7 +147,7 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    _, _, _, cfg = workload(args.method)
+    _, _, _, cfg = workload(args.method, args.width, args.height, args.spp)
     times, vals = [], []
     base = None
     for k in range(args.warmup + args.steps):
@@ -176,7 +176,7 @@ def run(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    scene, spec, grid, cfg = workload(args.method)
+    scene, spec, grid, cfg = workload(args.method, args.width, args.height, args.spp)
     spec.render_id = rank   # independent replicas: each rank renders its own stream of samples
     stream = torch.cuda.current_stream()
     ctx = sddm.Context(local, stream)
@@ -287,6 +287,9 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--paths-in-flight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--width", type=int, default=512)
+    ap.add_argument("--height", type=int, default=512)
+    ap.add_argument("--spp", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

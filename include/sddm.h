@@ -188,6 +188,21 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
  * results back before returning. Same semantics otherwise. */
 int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st);
 
+/* Render one image with the plain megakernel without allocating any memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc while rendering -- code inside a CUDA stream capture, or render
+ * loops that must not stall on the allocator. All scratch (per-path results,
+ * counters, the render record) lives in one fixed 16 MiB device array that the
+ * library defines and every GPU that loads it holds until exit, so a call is
+ * limited to width * height * spp <= 1,397,418 paths and 1920 materials;
+ * larger renders return SDDM_ERR_INVALID_ARG with a message. d->method must be
+ * SDDM_METHOD_MEGAKERNEL, d->bsdf_mode SDDM_BSDF_EXACT, and the per-sample
+ * outputs NULL. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (several
+ * streams or threads) race on it. Output: d->xyz_out, DEVICE, as sddm_render. */
+int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st);
+
 /* Pick grid, queue capacity and blocks per SM for these renders by timing
  * short pilot renders (<= 1 spp) of candidate settings (Sec. 5 load
  * balancing, done here by measurement). Writes the best options to *best and

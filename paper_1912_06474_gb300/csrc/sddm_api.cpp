@@ -516,6 +516,41 @@ static void camera_frame(const sddm_render_desc &x, RenderInfo &ri) {
     }
 }
 
+}  // extern "C"
+
+namespace sddm {
+// Read-only view of a context for entry points defined in other files.
+int ctx_view(sddm_ctx *ctx, CtxView *v) {
+    if (!ctx || !v) return fail(SDDM_ERR_INVALID_ARG, "ctx is NULL");
+    v->device = ctx->device;
+    v->stream = ctx->stream;
+    v->built = ctx->built;
+    v->dev = ctx->dev;
+    v->n_mat = (int)ctx->mats.size();
+    v->ev0 = ctx->ev0;
+    v->ev1 = ctx->ev1;
+    return SDDM_OK;
+}
+int check_render_desc(const sddm_ctx *ctx, const sddm_render_desc *d, int n) { return validate_desc(ctx, d, n); }
+void render_info_for(const sddm_ctx *ctx, const sddm_render_desc &x, RenderInfo &ri) {
+    std::memset(&ri, 0, sizeof(ri));
+    ri.width = x.width;
+    ri.height = x.height;
+    ri.spp = x.spp;
+    ri.max_depth = x.max_depth;
+    ri.seed = x.seed;
+    ri.render_id = x.render_id;
+    ri.nee = x.nee ? 1 : 0;
+    camera_frame(x, ri);
+    (void)ctx;
+}
+float material_state(const sddm_ctx *ctx, const sddm_render_desc &x, int m) {
+    return (x.glass_s && x.glass_s[m] >= 0.0f) ? x.glass_s[m] : ctx->mats[m].s_default;
+}
+}  // namespace sddm
+
+extern "C" {
+
 int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st) {
     int rc = validate_desc(ctx, d, n);
     if (rc != SDDM_OK) return rc;

@@ -110,6 +110,20 @@ void build_grid(const std::vector<BuildTri> &tris, const int dims[3], const floa
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+// Read-only access to a context from other translation units.
+struct CtxView {
+    int device;
+    cudaStream_t stream;
+    bool built;
+    DevScene dev;
+    int n_mat;
+    cudaEvent_t ev0, ev1;
+};
+int ctx_view(sddm_ctx *ctx, CtxView *v);
+int check_render_desc(const sddm_ctx *ctx, const sddm_render_desc *d, int n);
+void render_info_for(const sddm_ctx *ctx, const sddm_render_desc &x, RenderInfo &ri);
+float material_state(const sddm_ctx *ctx, const sddm_render_desc &x, int m);
+
 }  // namespace sddm
 
 // Kernel launchers (defined in .cu files), all asynchronous on `stream`.

@@ -27,7 +27,8 @@ BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP}
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
             "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
-            "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling"]
+            "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
+            "sddm_render_noalloc"]
 
 
 class SddmError(RuntimeError):
@@ -89,6 +90,7 @@ def _load():
         "sddm_glass_eval": ([P, C.c_uint32, I, P, P, P, P, P, P, I], I),
         "sddm_philox": ([P, I, P, C.c_uint32, C.c_uint32, P], I),
         "sddm_set_profiling": ([P, I], I),
+        "sddm_render_noalloc": ([P, C.POINTER(RenderDesc), C.POINTER(Stats)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +240,15 @@ class Context:
         arr, _keep = self._descs(specs, method, bsdf, [t.data_ptr() for t in outs], None, None)
         st = Stats()
         _check(lib.sddm_render(self._h, arr, len(specs), C.byref(st)))
+        self.last_stats = st.as_dict()
+        return self.last_stats
+
+    def render_noalloc(self, spec, out):
+        """sddm_render_noalloc: one megakernel render into the caller's CUDA tensor
+        ``out`` [H,W,3] float32; the library allocates nothing during the call."""
+        arr, _keep = self._descs([spec], "megakernel", "exact", [out.data_ptr()], None, None)
+        st = Stats()
+        _check(lib.sddm_render_noalloc(self._h, arr, C.byref(st)))
         self.last_stats = st.as_dict()
         return self.last_stats
 
