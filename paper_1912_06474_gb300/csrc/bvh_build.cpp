@@ -312,13 +312,14 @@ void build_bvh(const std::vector<BuildTri> &tris, const std::vector<uint32_t> &i
 }
 
 void build_grid(const std::vector<BuildTri> &tris, const int dims[3], const float lo[3], const float hi[3],
-                int leaf_size, int bins, std::vector<PackedBVH> &cells, int n_threads) {
+                int leaf_size, int bins, float eps, std::vector<PackedBVH> &cells, int n_threads) {
     const int nc = dims[0] * dims[1] * dims[2];
     cells.assign(nc, PackedBVH());
     double cell[3], slack[3];
+    // a triangle within the hit window's slack eps of a cell must be referenced by it
     for (int a = 0; a < 3; ++a) {
         cell[a] = ((double)hi[a] - (double)lo[a]) / dims[a];
-        slack[a] = 1e-5 + 1e-6 * std::max(std::fabs((double)lo[a]), std::fabs((double)hi[a]));
+        slack[a] = 1e-5 + 1e-6 * std::max(std::fabs((double)lo[a]), std::fabs((double)hi[a])) + 2.0 * (double)eps;
     }
     // bin triangles into the cells they overlap (cell boxes widened by the slack)
     std::vector<std::vector<uint32_t>> members(nc);

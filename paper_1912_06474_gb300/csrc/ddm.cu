@@ -138,8 +138,9 @@ __device__ __forceinline__ void stage_push(const Queues &Q, bool want, int cell,
         } else {
             atomicCAS(err, 0, 1);
         }
-        const unsigned peers = __match_any_sync(m, cell);
-        if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + cell, __popc(peers));
+        const int bin = 2 * cell + (r2.z & kRayShadow);   // sort key: cell, then ray kind
+        const unsigned peers = __match_any_sync(m, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + bin, __popc(peers));
     }
 }
 
@@ -219,11 +220,15 @@ __device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp) {
     __syncthreads();
 }
 
+// Sort the staged rays by cell. Each block bins a tile of 1024 rays in shared
+// memory and reserves one range per (tile, cell) with a single global atomic.
+constexpr int kScatterRaysPerThread = 4;
 __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
-    __shared__ int s_off[kMaxCells + 1];
+    __shared__ int s_off[kMaxBins + 1];
+    __shared__ int s_bin[kMaxBins];
     __shared__ int s_tmp[256];
     const Queues &Q = a.Q;
-    const int n_cells = a.g.n_cells;
+    const int n_cells = 2 * a.g.n_cells;   // bins: (cell, ray kind)
     block_prefix(Q.cnt, n_cells, s_off, s_tmp);
     int total = s_off[n_cells];
     // the per-cell counts must add up to the staged rays, within capacity
@@ -237,77 +242,222 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
         }
     }
     if (total == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
-        const int i = base + lane;
-        const bool valid = i < total;
-        const unsigned m = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            const float4 *src = Q.stage + 3 * (size_t)i;
-            const float4 r0 = src[0], r1 = src[1], r2 = src[2];
-            const int cell = __float_as_int(r2.w);
-            const unsigned peers = __match_any_sync(m, cell);
-            const int leader = __ffs(peers) - 1;
-            int base_slot = 0;
-            if (lane == leader) base_slot = atomicAdd(Q.fill + cell, __popc(peers));
-            base_slot = __shfl_sync(peers, base_slot, leader);
-            const int pos = s_off[cell] + base_slot + __popc(peers & ((1u << lane) - 1u));
-            float4 *dst = Q.in + 3 * (size_t)pos;
-            dst[0] = r0;
-            dst[1] = r1;
-            dst[2] = r2;
+    const int tile = blockDim.x * kScatterRaysPerThread;
+    for (int base = blockIdx.x * tile; base < total; base += gridDim.x * tile) {
+        for (int c = threadIdx.x; c < n_cells; c += blockDim.x) s_bin[c] = 0;
+        __syncthreads();
+        float4 r0[kScatterRaysPerThread], r1[kScatterRaysPerThread], r2[kScatterRaysPerThread];
+        int cell[kScatterRaysPerThread], rank[kScatterRaysPerThread];
+#pragma unroll
+        for (int k = 0; k < kScatterRaysPerThread; ++k) {
+            const int i = base + k * blockDim.x + threadIdx.x;
+            cell[k] = -1;
+            if (i < total) {
+                const float4 *src = Q.stage + 3 * (size_t)i;
+                r0[k] = src[0];
+                r1[k] = src[1];
+                r2[k] = src[2];
+                cell[k] = 2 * __float_as_int(r2[k].w) + (__float_as_int(r2[k].z) & kRayShadow);
+                rank[k] = atomicAdd(s_bin + cell[k], 1);
+            }
         }
+        __syncthreads();
+        for (int c = threadIdx.x; c < n_cells; c += blockDim.x)
+            if (s_bin[c] > 0) s_bin[c] = s_off[c] + atomicAdd(Q.fill + c, s_bin[c]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScatterRaysPerThread; ++k) {
+            if (cell[k] < 0) continue;
+            float4 *dst = Q.in + 3 * (size_t)(s_bin[cell[k]] + rank[k]);
+            dst[0] = r0[k];
+            dst[1] = r1[k];
+            dst[2] = r2[k];
+        }
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------ trace one wave
+// Persistent warps whose lanes are refilled one by one: a lane that finishes
+// its ray (hit, occlusion, or exit from the cell) takes the next ray of the
+// cell-sorted queue while the other lanes carry on, so a warp is not held by
+// its slowest ray. Traversal is a resumable state machine run for at most
+// kTraceSteps node or leaf visits between refills.
+#ifndef SDDM_TRACE_STEPS
+#define SDDM_TRACE_STEPS 32
+#endif
+constexpr int kTraceSteps = SDDM_TRACE_STEPS;
+// Resident 128-thread blocks per SM the trace kernel is compiled for (register budget).
+#ifndef SDDM_TRACE_MIN_BLOCKS
+#define SDDM_TRACE_MIN_BLOCKS 8
+#endif
+
 template <bool COUNT>
-__global__ void __launch_bounds__(128) k_trace_wave(KArgs a) {
+__global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs a) {
     const Queues &Q = a.Q;
     const DDMScene &g = a.g;
-    const int total = Q.off[g.n_cells];
+    const int total = Q.off[2 * g.n_cells];
     if (total == 0) return;
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t np = a.ps.np;
     unsigned long long n_cross = 0, n_vis = 0;
     TravCount tc;
+
+    int idx = -1;              // queue index of this lane's ray, -1 = none
+    bool exhausted = false;    // no ray left for this lane
+    Ray ray;
+    float t_cur = 0.f, t_max = 0.f, t_exit = 0.f, tmin = 0.f, tw = 0.f;
+    int q = 0, excl = -1, rfl = 0, next = -1, node = 0, sp = 0, best = -1, ep = -1, eo = -1, n_prev = 0;
+    bool occ = false;
+    Crossings cr;
+    cr.n = 0;
+    int stack[kStackSize];
+
     for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(Q.ctl + 1, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= (unsigned long long)total) break;
-        const int idx = (int)base + lane;
+        // 1. idle lanes take the next rays of the queue
+        const bool need = idx < 0 && !exhausted;
+        const unsigned m = __ballot_sync(full, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(Q.ctl + 1, (unsigned long long)__popc(m));
+            base = __shfl_sync(full, base, leader);
+            if (need) {
+                const unsigned long long my = base + __popc(m & lt_mask);
+                if (my < (unsigned long long)total) {
+                    idx = (int)my;
+                    const float4 *src = Q.in + 3 * (size_t)idx;
+                    const float4 r0 = src[0], r1 = src[1], r2f = src[2];
+                    q = __float_as_int(r2f.x);
+                    excl = __float_as_int(r2f.y);
+                    rfl = __float_as_int(r2f.z);
+                    const int cell = __float_as_int(r2f.w);
+                    ray = make_ray(xyz(r0), xyz(r1));
+                    t_cur = r0.w;
+                    t_max = r1.w;
+                    t_exit = cell_exit(g, cell, ray.o, ray.d, next);
+                    tmin = fmaxf(0.0f, t_cur - g.eps);
+                    node = __ldg(g.root + cell);
+                    sp = 0;
+                    best = -1;
+                    occ = false;
+                    ++n_vis;
+                    if (rfl & kRayShadow) {
+                        tw = fminf(t_exit + g.eps, t_max);
+                        cr.n = (rfl >> 1) & 7;
+                        for (int k = 0; k < cr.n; ++k) cr.obj[k] = a.ps.cross_obj[k * np + q];
+                        n_prev = cr.n;
+                    } else {
+                        tw = t_exit + g.eps;
+                        ep = excl >= 0 ? excl : -1;
+                        eo = excl <= -2 ? -excl - 2 : -1;
+                    }
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (__ballot_sync(full, idx >= 0) == 0) break;
+
+        // 2. a bounded number of traversal steps
+        bool fin = false;
+        if (idx >= 0) {
+            const bool shadow = (rfl & kRayShadow) != 0;
+            for (int step = 0; step < kTraceSteps; ++step) {
+                bool pop = false;
+                if (node >= 0) {
+                    if (COUNT) ++tc.nodes;
+                    const float4 n0 = __ldg(g.nodes + 4 * node + 0), n1 = __ldg(g.nodes + 4 * node + 1),
+                                 n2 = __ldg(g.nodes + 4 * node + 2), n3 = __ldg(g.nodes + 4 * node + 3);
+                    float ta, tb;
+                    bool ha, hb;
+                    child_boxes(ray, n0, n1, n2, tmin, tw, ta, tb, ha, hb);
+                    const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+                    if (ha && hb) {
+                        const bool a_first = shadow || ta <= tb;
+                        if (sp < kStackSize) {
+                            stack[sp++] = a_first ? cb : ca;
+                        } else {
+                            atomicCAS(a.err, 0, 5);   // deeper than the builder allows
+                        }
+                        node = a_first ? ca : cb;
+                    } else if (ha) {
+                        node = ca;
+                    } else if (hb) {
+                        node = cb;
+                    } else {
+                        pop = true;
+                    }
+                } else {
+                    const int v = ~node;
+                    const int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
+                    for (int i = 0; i < count; ++i) {
+                        const float4 *tp = g.tris + 3 * (first + i);
+                        const float4 ta4 = __ldg(tp), tb4 = __ldg(tp + 1), tc4 = __ldg(tp + 2);
+                        const int id = __float_as_int(ta4.w);
+                        if (shadow) {
+                            if (id == excl) continue;
+                            if (COUNT) ++tc.tris;
+                            const V3 e1 = xyz(tb4), e2 = xyz(tc4);
+                            const float t = mt_intersect(ray, xyz(ta4), e1, e2);
+                            if (!(t > tmin && t <= tw)) continue;
+                            if (!(__float_as_uint(tc4.w) & kTriGlass)) {
+                                occ = true;
+                                break;
+                            }
+                            if (dot(ray.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
+                            const int ob = __float_as_int(tb4.w);
+                            bool seen = false;
+                            for (int k = 0; k < cr.n; ++k) seen |= cr.obj[k] == ob;
+                            if (seen) continue;
+                            if (cr.n >= kMaxCross) {
+                                occ = true;
+                                break;
+                            }
+                            cr.obj[cr.n] = ob;
+                            cr.tri[cr.n] = id;
+                            ++cr.n;
+                        } else {
+                            if (id == ep || (eo >= 0 && __float_as_int(tb4.w) == eo)) continue;
+                            if (COUNT) ++tc.tris;
+                            const float t = mt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
+                            if (t > tmin && (t < tw || (t == tw && (best < 0 || id < best)))) {
+                                tw = t;
+                                best = id;
+                            }
+                        }
+                    }
+                    if (occ) {
+                        fin = true;
+                        break;
+                    }
+                    pop = true;
+                }
+                if (pop) {
+                    if (sp == 0) {
+                        fin = true;
+                        break;
+                    }
+                    node = stack[--sp];
+                }
+            }
+        }
+
+        // 3. finished lanes: final result, or hand-off to the neighbouring cell
         bool want = false;
-        int next = -1;
         float4 o0 = make_float4(0, 0, 0, 0), o1 = o0;
         int4 o2 = make_int4(0, 0, 0, 0);
-        if (idx < total) {
-            const float4 *src = Q.in + 3 * (size_t)idx;
-            const float4 r0 = src[0], r1 = src[1], r2f = src[2];
-            const int q = __float_as_int(r2f.x), excl = __float_as_int(r2f.y), rfl = __float_as_int(r2f.z),
-                      cell = __float_as_int(r2f.w);
-            const V3 o = xyz(r0), d = xyz(r1);
-            const float t_cur = r0.w, t_max = r1.w;
-            const float t_exit = cell_exit(g, cell, o, d, next);
-            const float tmin = fmaxf(0.0f, t_cur - g.eps);
-            const Ray ray = make_ray(o, d);
-            const int root = __ldg(g.root + cell);
-            ++n_vis;
+        if (fin) {
             bool done = false;
             int rfl_next = rfl;
             if (rfl & kRayShadow) {
-                Crossings cr;
-                cr.n = (rfl >> 1) & 7;
-                for (int k = 0; k < cr.n; ++k) cr.obj[k] = a.ps.cross_obj[k * np + q];
-                const int n_prev = cr.n;
-                const float tw = fminf(t_exit + g.eps, t_max);
-                const bool occ = trace_shadow<COUNT>(g.nodes, g.tris, root, ray, tmin, tw, excl, cr, &tc);
                 for (int k = n_prev; k < cr.n; ++k) {
                     const float4 cn = __ldg(a.sc.tri_n + cr.tri[k]);
                     a.ps.cross_obj[k * np + q] = cr.obj[k];
                     a.ps.cross_mat[k * np + q] = __float_as_int(cn.w);
-                    a.ps.cross_cos[k * np + q] = -dot(d, xyz(cn));
+                    a.ps.cross_cos[k * np + q] = -dot(ray.d, xyz(cn));
                 }
                 if (occ) {
                     a.ps.sh_status[q] = kShadowOccluded;
@@ -318,26 +468,25 @@ __global__ void __launch_bounds__(128) k_trace_wave(KArgs a) {
                 }
                 rfl_next = (rfl & 1) | (cr.n << 1);
             } else {
-                const int ep = excl >= 0 ? excl : -1, eo = excl <= -2 ? -excl - 2 : -1;
-                const Hit h = trace_closest<COUNT>(g.nodes, g.tris, root, ray, tmin, t_exit + g.eps, ep, eo, &tc);
-                if (h.prim >= 0) {
-                    const V3 x = o + h.t * d;
-                    a.ps.hit0[q] = make_float4(x.x, x.y, x.z, __int_as_float(h.prim));
-                    a.ps.hit1[q] = make_float4(d.x, d.y, d.z, h.t);
+                if (best >= 0) {
+                    const V3 x = ray.o + tw * ray.d;
+                    a.ps.hit0[q] = make_float4(x.x, x.y, x.z, __int_as_float(best));
+                    a.ps.hit1[q] = make_float4(ray.d.x, ray.d.y, ray.d.z, tw);
                     done = true;
                 } else if (next < 0) {
                     a.ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
-                    a.ps.hit1[q] = make_float4(d.x, d.y, d.z, 0.f);
+                    a.ps.hit1[q] = make_float4(ray.d.x, ray.d.y, ray.d.z, 0.f);
                     done = true;
                 }
             }
             if (!done) {
                 want = true;
-                o0 = make_float4(o.x, o.y, o.z, fmaxf(t_cur, t_exit));
-                o1 = r1;
+                o0 = make_float4(ray.o.x, ray.o.y, ray.o.z, fmaxf(t_cur, t_exit));
+                o1 = make_float4(ray.d.x, ray.d.y, ray.d.z, t_max);
                 o2 = make_int4(q, excl, rfl_next, next);
                 ++n_cross;
             }
+            idx = -1;
         }
         if (want && a.last_wave) {   // cannot happen: each wave moves a ray forward along one axis
             atomicCAS(a.err, 0, 4);
@@ -454,6 +603,7 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
             const bool need_T = resolve || pend || emit;
             if (need_T) {
                 Kahan NX, NY, NZ, EX, EY, EZ;
+#pragma unroll 2
                 for (int i = 0; i < L; ++i) {
                     float t = ps.T[(size_t)i * np + q];
                     const float wx = __ldg(sc.wcmf + 3 * i), wy = __ldg(sc.wcmf + 3 * i + 1),
@@ -643,7 +793,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     const int L = run.sc.L;
     const int nc = run.g.n_cells;
     if (nc > kMaxCells) {
-        set_error("sddm_render: the DDM method supports at most 4096 subdomains");
+        set_error("sddm_render: the DDM method supports at most 2048 subdomains");
         return SDDM_ERR_INVALID_ARG;
     }
     const int64_t cap = 2 * np;
@@ -658,8 +808,8 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
                  oFl = take(4 * np), oPm = take(4 * np), oPc = take(4 * np), oPw = take(4 * np), oG = take(4 * np),
                  oLm = take(4 * np), oSh = take(4 * np), oCo = take(4 * kMaxCross * np), oCm = take(4 * kMaxCross * np),
                  oCc = take(4 * kMaxCross * np), oH0 = take(16 * np), oH1 = take(16 * np), oIn = take(48 * cap),
-                 oSt = take(48 * cap), oCtl = take(32 + 4 * (size_t)nc), oFill = take(4 * (size_t)nc),
-                 oOff = take(4 * ((size_t)nc + 1));
+                 oSt = take(48 * cap), oCtl = take(32 + 8 * (size_t)nc), oFill = take(8 * (size_t)nc),
+                 oOff = take(4 * (2 * (size_t)nc + 1));
     if (off > buf.bytes) {
         if (buf.mem) cudaFree(buf.mem);
         buf.mem = nullptr;
@@ -712,7 +862,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     const int scatter_blocks = sm * 4;
     const unsigned path_blocks = (unsigned)std::min<int64_t>((np + 255) / 256, (int64_t)sm * 16);
     const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
-    const size_t ctl_bytes = 32 + 4 * (size_t)nc;
+    const size_t ctl_bytes = 32 + 8 * (size_t)nc;
     cudaError_t e;
 #define DDM_CHECK(x)                                                     \
     do {                                                                 \
@@ -725,7 +875,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     DDM_CHECK(cudaGetLastError());
     for (int b = 1; b <= run.max_depth + 1; ++b) {
         for (int w = 0; w < waves; ++w) {
-            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nc, s));
+            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 8 * (size_t)nc, s));
             k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
             DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));

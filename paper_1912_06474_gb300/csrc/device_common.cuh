@@ -232,48 +232,48 @@ __device__ __forceinline__ bool trace_shadow(const float4 *__restrict__ nodes, c
 
 // ------------------------------------------------------------------- optics
 // Fresnel reflectances |r_s|^2, |r_p|^2 for light arriving from vacuum onto a
-// medium of complex index n + ik (Eq. 1), cos_i = c in (0, 1].
-__device__ __forceinline__ void csqrt_f(float re, float im, float &a, float &b) {
-    float r = hypotf(re, im);
-    if (re >= 0.0f) {
-        a = sqrtf(0.5f * (r + re));
-        b = a > 0.0f ? im / (2.0f * a) : 0.0f;
-    } else {
-        b = copysignf(sqrtf(0.5f * (r - re)), im);
-        a = im / (2.0f * b);
-    }
-}
+// medium of complex index n + ik (Eq. 1), cos_i = c in (0, 1], in real
+// arithmetic: with a + ib = n~ cos_t, (a + ib)^2 = n^2 - k^2 - sin^2 + 2ink, so
+// a b = n k, and
+//   Rs = ((a - c)^2 + b^2) / ((a + c)^2 + b^2),
+//   Rp = Rs ((a - q)^2 + b^2) / ((a + q)^2 + b^2),  q = sin^2 / cos.
+// a or b is taken from the larger-magnitude side of the square root so that
+// neither suffers cancellation (k is ~1e-5 for glass, ~1..8 for metals).
 __device__ __forceinline__ void fresnel_rs_rp(float c, float n, float k, float &Rs, float &Rp) {
-    // eta^2 = (n^2 - k^2) + 2nk i ; z = 1 - (1 - c^2) / eta^2
-    float er = n * n - k * k, ei = 2.0f * n * k;
-    float inv_m = 1.0f / (er * er + ei * ei);
-    float s2 = 1.0f - c * c;
-    float zr = 1.0f - s2 * er * inv_m, zi = s2 * ei * inv_m;
-    float ctr, cti;
-    csqrt_f(zr, zi, ctr, cti);
-    // eta * cos_t
-    float ar = n * ctr - k * cti, ai = n * cti + k * ctr;
-    // r_s = (c - eta ct) / (c + eta ct)
-    float num_r = c - ar, num_i = -ai, den_r = c + ar, den_i = ai;
-    Rs = (num_r * num_r + num_i * num_i) / (den_r * den_r + den_i * den_i);
-    // r_p = (eta c - ct) / (eta c + ct)
-    float pr = n * c, pi = k * c;
-    num_r = pr - ctr;
-    num_i = pi - cti;
-    den_r = pr + ctr;
-    den_i = pi + cti;
-    Rp = (num_r * num_r + num_i * num_i) / (den_r * den_r + den_i * den_i);
+    const float s2 = fmaf(-c, c, 1.0f);
+    const float t0 = fmaf(n, n, -fmaf(k, k, s2));
+    const float nk = n * k;
+    const float r = sqrtf(fmaf(t0, t0, 4.0f * nk * nk));
+    float a, b;
+    if (t0 >= 0.0f) {
+        a = sqrtf(0.5f * (r + t0));
+        b = a > 0.0f ? __fdividef(nk, a) : 0.0f;
+    } else {
+        b = sqrtf(0.5f * (r - t0));
+        a = __fdividef(nk, b);
+    }
+    const float b2 = b * b;
+    const float am = a - c, ap = a + c;
+    Rs = __fdividef(fmaf(am, am, b2), fmaf(ap, ap, b2));
+    const float q = __fdividef(s2, c);
+    const float qm = a - q, qp = a + q;
+    Rp = Rs * __fdividef(fmaf(qm, qm, b2), fmaf(qp, qp, b2));
 }
 
 __device__ __forceinline__ float conductor_F(float c, float n, float k) {
     if (c <= 0.0f) return 1.0f;
-    c = fminf(c, 1.0f);
+    c = fminf(fmaxf(c, 1e-8f), 1.0f);
     float Rs, Rp;
     fresnel_rs_rp(c, n, k, Rs, Rp);
     return 0.5f * (Rs + Rp);
 }
 
-// Absorbing plane-parallel slab: multiple-reflection sums per polarisation.
+// Absorbing plane-parallel slab (Sec. 6, "the Fresnel definition" of the
+// glass; Eq. 1 with k = alpha lambda / 4 pi): interface reflectance rho_j per
+// polarisation, internal transmittance tau = exp(-alpha d / cos_t) with the
+// real-index refraction angle, and the multiple-reflection sums
+//   R_j = rho_j + (1 - rho_j)^2 rho_j tau^2 / (1 - rho_j^2 tau^2)
+//   T_j = (1 - rho_j)^2 tau / (1 - rho_j^2 tau^2),   R, T = mean over j.
 __device__ __forceinline__ void slab_RT(float c, float lam_nm, float n, float alpha, float thick, float &R,
                                         float &T) {
     if (c <= 0.0f) {
@@ -281,17 +281,18 @@ __device__ __forceinline__ void slab_RT(float c, float lam_nm, float n, float al
         T = 0.0f;
         return;
     }
-    c = fminf(c, 1.0f);
-    float k = alpha * lam_nm * (1e-9f / (4.0f * 3.14159265358979f));
+    c = fminf(fmaxf(c, 1e-8f), 1.0f);
+    const float k = alpha * lam_nm * (1e-9f / (4.0f * 3.14159265358979f));
     float Rs, Rp;
     fresnel_rs_rp(c, n, k, Rs, Rp);
-    float ctr = sqrtf(1.0f - (1.0f - c * c) / (n * n));
-    float tau = expf(-alpha * thick / ctr);
-    float t2 = tau * tau;
-    float ds = 1.0f / (1.0f - Rs * Rs * t2), dp = 1.0f / (1.0f - Rp * Rp * t2);
-    float qs = (1.0f - Rs) * (1.0f - Rs), qp = (1.0f - Rp) * (1.0f - Rp);
-    R = 0.5f * ((Rs + qs * Rs * t2 * ds) + (Rp + qp * Rp * t2 * dp));
-    T = 0.5f * (qs * tau * ds + qp * tau * dp);
+    const float s2 = fmaf(-c, c, 1.0f);
+    const float ctr = __fdividef(sqrtf(fmaf(n, n, -s2)), n);
+    const float tau = __expf(-__fdividef(alpha * thick, ctr));
+    const float t2 = tau * tau;
+    const float ds = __frcp_rn(fmaf(-Rs * Rs, t2, 1.0f)), dp = __frcp_rn(fmaf(-Rp * Rp, t2, 1.0f));
+    const float qs = (1.0f - Rs) * (1.0f - Rs), qp = (1.0f - Rp) * (1.0f - Rp);
+    R = 0.5f * (fmaf(qs * Rs * t2, ds, Rs) + fmaf(qp * Rp * t2, dp, Rp));
+    T = 0.5f * tau * (qs * ds + qp * dp);
 }
 
 // Glass branch probability: clamp(mean over bins of the lossless slab

@@ -359,8 +359,12 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     }
     PackedBVH global;
     build_bvh(tris, all, glo, ghi, o.leaf_size, o.sah_bins, global);
+    const double diag = std::sqrt((double)(ghi[0] - glo[0]) * (ghi[0] - glo[0]) +
+                                  (double)(ghi[1] - glo[1]) * (ghi[1] - glo[1]) +
+                                  (double)(ghi[2] - glo[2]) * (ghi[2] - glo[2]));
+    const float eps = (float)(1e-6 * diag);
     std::vector<PackedBVH> cells;
-    build_grid(tris, o.grid, glo, ghi, o.leaf_size, o.sah_bins, cells, n_threads);
+    build_grid(tris, o.grid, glo, ghi, o.leaf_size, o.sah_bins, eps, cells, n_threads);
     std::vector<float4> cell_nodes, cell_tris;
     std::vector<int> cell_root;
     int64_t tri_base_check = 0;
@@ -434,9 +438,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         g.cell[a] = (ghi[a] - glo[a]) / (float)o.grid[a];
         g.inv_cell[a] = 1.0f / g.cell[a];
     }
-    double diag = std::sqrt((double)(ghi[0] - glo[0]) * (ghi[0] - glo[0]) + (double)(ghi[1] - glo[1]) * (ghi[1] - glo[1]) +
-                            (double)(ghi[2] - glo[2]) * (ghi[2] - glo[2]));
-    g.eps = (float)(1e-6 * diag);
+    g.eps = eps;
     g.n_cells = o.grid[0] * o.grid[1] * o.grid[2];
     g.nodes = ctx->d_cell_nodes.as<float4>();
     g.tris = ctx->d_cell_tris.as<float4>();

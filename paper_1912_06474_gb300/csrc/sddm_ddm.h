@@ -18,7 +18,8 @@
 
 namespace sddm {
 
-constexpr int kMaxCells = 4096;
+constexpr int kMaxCells = 2048;
+constexpr int kMaxBins = 2 * kMaxCells;   // queue sort key: (cell, ray kind)
 
 struct DDMScene {
     int dims[3];
@@ -62,9 +63,9 @@ struct Queues {
     int64_t cap;          // rays per buffer
     float4 *in;           // [cap][3]
     float4 *stage;        // [cap][3]
-    int *cnt;             // [n_cells] rays staged per cell
-    int *fill;            // [n_cells] scatter cursors
-    int *off;             // [n_cells + 1] offsets of the sorted `in`
+    int *cnt;             // [2 n_cells] rays staged per (cell, kind) bin
+    int *fill;            // [2 n_cells] scatter cursors
+    int *off;             // [2 n_cells + 1] offsets of the sorted `in`
     unsigned long long *ctl;   // [4]: stage count, claim cursor, -, -
 };
 

@@ -104,7 +104,7 @@ struct BuildTri {
 void build_bvh(const std::vector<BuildTri> &tris, const std::vector<uint32_t> &refs, const float clip_lo[3],
                const float clip_hi[3], int leaf_size, int bins, PackedBVH &out);
 void build_grid(const std::vector<BuildTri> &tris, const int dims[3], const float lo[3], const float hi[3],
-                int leaf_size, int bins, std::vector<PackedBVH> &cells, int n_threads);
+                int leaf_size, int bins, float eps, std::vector<PackedBVH> &cells, int n_threads);
 
 // Errors
 void set_error(const std::string &msg);
