@@ -26,7 +26,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["philox.c", "optics.c", "geom.c", "render.c"]
+_SOURCES = ["philox.c", "optics.c", "geom.c", "render.c", "mlp.c"]
 _LIB_PATH = os.path.join(_HERE, "_build", "libsddm_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -98,6 +98,14 @@ def _load():
         lib.orc_shadow.restype = C.c_int
         lib.orc_num_lights.argtypes = [P]
         lib.orc_num_lights.restype = C.c_int
+        lib.orc_mlp_n_params.restype = C.c_int
+        lib.orc_mlp_features.argtypes = [C.c_double] * 4 + [P]
+        lib.orc_mlp_forward.argtypes = [P, P, P]
+        lib.orc_mlp_forward_d.argtypes = [P, P, P]
+        lib.orc_mlp_loss_grad.argtypes = [P, C.c_int, P, P, P]
+        lib.orc_mlp_loss_grad.restype = C.c_double
+        lib.orc_mlp_loss_grad_d.argtypes = [P, C.c_int, P, P, P]
+        lib.orc_mlp_loss_grad_d.restype = C.c_double
         _lib = lib
         return lib
 
@@ -149,6 +157,45 @@ def cosine_dir(ns, u0, u1):
     out = np.zeros(3)
     _load().orc_cosine_dir(_ptr(n), float(u0), float(u1), _ptr(out))
     return out
+
+
+# ------------------------------------------------------------------- MLP ---
+MLP_PARAMS = 8770
+
+
+def mlp_features(c, lam_nm, s, d):
+    x = np.zeros(4)
+    _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), _ptr(x))
+    return x
+
+
+def mlp_forward(params, X):
+    """FP64 forward of the surrogate for rows X [n,4]; params float32 (or float64) [8770]."""
+    lib = _load()
+    X = np.ascontiguousarray(np.atleast_2d(X), np.float64)
+    p = np.ascontiguousarray(params)
+    out = np.zeros((X.shape[0], 2))
+    fn = lib.orc_mlp_forward_d if p.dtype == np.float64 else lib.orc_mlp_forward
+    if p.dtype != np.float64:
+        p = np.ascontiguousarray(p, np.float32)
+    for i in range(X.shape[0]):
+        fn(_ptr(p), _ptr(X[i]), out[i:].ctypes.data_as(C.c_void_p))
+    return out
+
+
+def mlp_loss_grad(params, X, Y):
+    """FP64 loss (mean squared error over rows and both outputs) and its gradient."""
+    lib = _load()
+    X = np.ascontiguousarray(X, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    p = np.ascontiguousarray(params)
+    g = np.zeros(MLP_PARAMS)
+    if p.dtype == np.float64:
+        loss = lib.orc_mlp_loss_grad_d(_ptr(p), int(X.shape[0]), _ptr(X), _ptr(Y), _ptr(g))
+    else:
+        p = np.ascontiguousarray(p, np.float32)
+        loss = lib.orc_mlp_loss_grad(_ptr(p), int(X.shape[0]), _ptr(X), _ptr(Y), _ptr(g))
+    return loss, g
 
 
 # ----------------------------------------------------------------- scene ---

@@ -1,0 +1,57 @@
+"""Pins of the oracle's FP64 surrogate network (oracle/mlp.c).
+
+* backpropagation equals FP64 central differences of the loss (rel <= 1e-6);
+* the feature map sends the corners of the trained box to +-1;
+* a network with all weights zero outputs its output bias, whatever the input;
+* with only biases and the last layer set, the output is b4 + W4 silu(b3),
+  silu evaluated at points where it has a closed form (silu(0) = 0).
+"""
+import math
+
+import numpy as np
+
+
+def test_backprop_matches_central_differences(oracle_mod):
+    rng = np.random.default_rng(21)
+    p = rng.normal(0.0, 0.25, oracle_mod.MLP_PARAMS)
+    X = rng.uniform(-1, 1, (6, 4))
+    Y = rng.uniform(0, 1, (6, 2))
+    loss, g = oracle_mod.mlp_loss_grad(p, X, Y)
+    idx = np.concatenate([rng.choice(256, 8, replace=False),               # W1
+                          256 + rng.choice(64, 4, replace=False),          # b1
+                          320 + rng.choice(4096, 12, replace=False),       # W2
+                          4480 + rng.choice(4096, 12, replace=False),      # W3
+                          8576 + rng.choice(64, 4, replace=False),         # b3
+                          8640 + rng.choice(128, 6, replace=False), [8768, 8769]])
+    h = 1e-5
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle_mod.mlp_loss_grad(pp, X, Y)[0] - oracle_mod.mlp_loss_grad(pm, X, Y)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(abs(g[i]), 1e-3), (i, fd, g[i])
+
+
+def test_feature_map_box_corners(oracle_mod):
+    assert np.allclose(oracle_mod.mlp_features(1.0, 780.0, 1.0, 0.010), [1, 1, 1, 1], atol=1e-12)
+    assert np.allclose(oracle_mod.mlp_features(0.0, 380.0, 0.0, 0.002), [-1, -1, -1, -1], atol=1e-12)
+    assert np.allclose(oracle_mod.mlp_features(0.5, 580.0, 0.5, 0.006), [0, 0, 0, 0], atol=1e-12)
+
+
+def test_constant_networks(oracle_mod):
+    p = np.zeros(oracle_mod.MLP_PARAMS)
+    p[8768], p[8769] = 0.25, -0.5
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-1, 1, (5, 4))
+    assert np.allclose(oracle_mod.mlp_forward(p, X), [[0.25, -0.5]] * 5, atol=0)
+    # hidden layers constant: h3 = silu(b3); with b3 = 0 on half the units silu is exactly 0
+    p[8576:8576 + 32] = 0.0
+    p[8576 + 32:8640] = 2.0
+    p[8640:8704] = 1.0            # W4 row 0
+    p[8704:8768] = -1.0           # W4 row 1
+    s2 = 2.0 / (1.0 + math.exp(-2.0))
+    want = np.array([0.25 + 32 * s2, -0.5 - 32 * s2])
+    assert np.allclose(oracle_mod.mlp_forward(p, X), [want] * 5, rtol=1e-12)
+    loss, g = oracle_mod.mlp_loss_grad(p, X, np.zeros((5, 2)))
+    assert abs(loss - (want ** 2).mean()) < 1e-9
+    assert np.all(g[:8576] == 0.0)       # nothing reaches the constant layers' weights
