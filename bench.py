@@ -107,14 +107,14 @@ def _dist():
     return world, rank, local
 
 
-def workload(method, width=512, height=512, spp=16):
+def workload(method, width=512, height=512, spp=16, bsdf="exact"):
     from paper_1912_06474_gb300 import scenes
     scene = scenes.hotel_room(L=41, seed=0)
     spec = scenes.hotel_room_render(scene, width, height, spp, 5, seed=0)
     grid = (4, 4, 2) if method == "ddm" else (1, 1, 1)
     cfg = {"workload": f"hotel_room_{width}x{height}_{spp}spp_d5_L41", "triangles": scene.n_tris,
            "width": width, "height": height, "spp": spp, "max_depth": 5, "lambda_bins": 41, "method": method,
-           "grid": list(grid), "bsdf": "exact", "l2": "flushed between steps (256 MiB write)",
+           "grid": list(grid), "bsdf": bsdf, "l2": "flushed between steps (256 MiB write)",
            "scaling_mode": "replicas"}
     return scene, spec, grid, cfg
 
@@ -176,7 +176,7 @@ def run(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    scene, spec, grid, cfg = workload(args.method, args.width, args.height, args.spp)
+    scene, spec, grid, cfg = workload(args.method, args.width, args.height, args.spp, args.bsdf)
     spec.render_id = rank   # independent replicas: each rank renders its own stream of samples
     stream = torch.cuda.current_stream()
     ctx = sddm.Context(local, stream)
@@ -184,15 +184,19 @@ def run(args):
     t0 = time.perf_counter()
     ctx.build(grid=grid, blocks_per_sm=args.blocks_per_sm, paths_in_flight=args.paths_in_flight)
     build_s = time.perf_counter() - t0
+    train = None
+    if args.bsdf == "mlp":   # the surrogate is trained once, before and outside the timed steps
+        train = ctx.mlp_train(scene.glass_materials()[0], seed=7)
+        cfg["surrogate_training"] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in train.items()}
     out = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     # traversal counts of this exact workload (separately compiled counting kernel, untimed)
     ctx.set_profiling(count_traversal=True)
-    cst = ctx.render_into([spec], [out], method=args.method)
+    cst = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
     ctx.set_profiling(time_trace=True)
     for _ in range(args.warmup):
-        ctx.render_into([spec], [out], method=args.method)
+        ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -204,7 +208,7 @@ def run(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        st = ctx.render_into([spec], [out], method=args.method)
+        st = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
         ev[k][1].record(stream)
         segs += st["segments_ext"] + st["segments_shadow"]
         trace_ms += st["trace_ms"]
@@ -221,7 +225,7 @@ def run(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = ctx.render_host([spec], [host], method=args.method)
+        st = ctx.render_host([spec], [host], method=args.method, bsdf=args.bsdf)
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_segs += st["segments_ext"] + st["segments_shadow"]
     clk = clocks.stop()
@@ -271,6 +275,7 @@ def run(args):
                      "nodes_per_visit": round(cst["node_visits"] / max(visits, 1), 2),
                      "tris_per_visit": round(cst["tri_tests"] / max(visits, 1), 2)},
         "segments_per_step": segs // (args.steps * world), "build_s": round(build_s, 3), "clocks": clk,
+        "mlp_fallback_batches_per_step": st.get("mlp_fallbacks", 0) if args.bsdf == "mlp" else None,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
@@ -284,6 +289,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sddm", choices=["sddm", "reference"])
     ap.add_argument("--method", default="ddm", choices=["ddm", "megakernel"])
+    ap.add_argument("--bsdf", default="exact", choices=["exact", "mlp"])
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--paths-in-flight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -47,7 +47,11 @@ typedef enum {
     SDDM_ERR_DEVICE_CHECK = -8     /* a device-side bounds check tripped (no access was made) */
 } sddm_status;
 
-typedef enum { SDDM_BSDF_EXACT = 0, SDDM_BSDF_MLP = 1 } sddm_bsdf_mode;
+typedef enum {
+    SDDM_BSDF_EXACT = 0,      /* the exact absorbing-slab model */
+    SDDM_BSDF_MLP = 1,        /* the trained surrogate, with probe and exact fallback */
+    SDDM_BSDF_MLP_RAW = 2     /* sddm_glass_eval only: the network output alone (testing) */
+} sddm_bsdf_mode;
 
 typedef enum {
     SDDM_METHOD_MEGAKERNEL = 0,    /* one thread per path over the global BVH (Sec. 5, classical split) */
@@ -208,6 +212,59 @@ int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st
  * balancing, done here by measurement). Writes the best options to *best and
  * leaves the context built with them. */
 int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_opts *best);
+
+/* ------------------------------------------------- learned glass surrogate
+ * A small network stands in for the exact slab R, T of a glass material (the
+ * paper evaluates glass "by the Fresnel definition", Sec. 6): inputs
+ * (cos theta, lambda, s, thickness) mapped to [-1, 1] over the trained box
+ * cos in [0,1], lambda in [380,780] nm, s in [0,1], thickness in
+ * [thick_min, thick_max]; 3 hidden layers of 64 SiLU units; outputs (R, T).
+ * Weights and activations are BF16 with FP32 accumulation and FP32 master
+ * weights; parameters in this order (8770 floats): W1[64][4], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[2][64], b4[2]. */
+#define SDDM_MLP_PARAMS 8770
+
+typedef struct {
+    int64_t samples;          /* exact training samples drawn once (0 = 2^22) */
+    int steps;                /* Adam steps (0 = 20000) */
+    int batch;                /* rows per step, multiple of 64 (0 = 8192) */
+    float lr;                 /* peak learning rate, cosine decay to lr/100 (0 = 1e-3) */
+    uint32_t seed;            /* Philox key of the samples and the initial weights */
+    float thick_min, thick_max; /* trained thickness range, m (0, 0 = 0.002, 0.010) */
+    int resume;               /* 1: continue from the current weights and Adam state */
+} sddm_mlp_train_opts;
+
+typedef struct {
+    double final_loss;        /* mean squared error of the last batch */
+    double max_abs_err_R;     /* on a held-out grid of the trained box, vs the exact slab */
+    double max_abs_err_T;
+    double train_ms;          /* device time of the training steps */
+    double tflops;            /* tensor-core FLOP of forward + backward / train time */
+    int64_t steps;            /* Adam steps taken so far (with resume) */
+} sddm_mlp_report;
+
+/* Train the surrogate of glass material `mat` on samples of its exact slab
+ * model (generated on the device), by the library's own forward, backward and
+ * Adam kernels. The weights serve every glass material with the same n,
+ * alpha_clear and dalpha curves. Requires sddm_build. r may be NULL. */
+int sddm_mlp_train(sddm_ctx *ctx, uint32_t mat, const sddm_mlp_train_opts *o, sddm_mlp_report *r);
+
+/* Copy the FP32 weights of glass material `mat` out (HOST [8770]) or in.
+ * Setting weights makes the material's surrogate usable (Adam state reset). */
+int sddm_mlp_get_weights(sddm_ctx *ctx, uint32_t mat, float *params);
+int sddm_mlp_set_weights(sddm_ctx *ctx, uint32_t mat, const float *params, float thick_min, float thick_max);
+
+/* Checkpoint of the surrogate of `mat`: weights, Adam moments and step, to or
+ * from a file (little-endian binary, magic "SDDMMLP1"). */
+int sddm_mlp_save(sddm_ctx *ctx, uint32_t mat, const char *path);
+int sddm_mlp_load(sddm_ctx *ctx, uint32_t mat, const char *path);
+
+/* Test hook: mean squared error and its gradient (FP32, from the BF16
+ * forward/backward training kernels) of parameters params[8770] on n rows of
+ * features X[n][4] (already mapped to [-1,1]) and targets Y[n][2]. All DEVICE
+ * arrays; grad[8770] and loss[1] written. */
+int sddm_mlp_grad(sddm_ctx *ctx, int n, const float *X, const float *Y, const float *params, float *grad,
+                  float *loss);
 
 /* Enable the SDDM_PROFILE_* measurements of later sddm_render calls
  * (0 = off). Counting uses a separately compiled trace kernel, so the timed

@@ -27,6 +27,7 @@
 
 #include "device_common.cuh"
 #include "sddm_ddm.h"
+#include "sddm_mlp.h"
 
 namespace sddm {
 
@@ -61,6 +62,14 @@ struct KArgs {
     int32_t *first_prim;
     unsigned long long *counters;
     int *err;
+    // learned glass model: queries gathered per bounce, results [query][L] (R, T)
+    int use_mlp;
+    float4 *queries;
+    unsigned long long *n_queries;
+    int64_t q_cap;
+    int *pend_query;      // [np]
+    int *cross_query;     // [kMaxCross][np]
+    const float2 *glass_res;
 };
 
 // ---------------------------------------------------------------- grid
@@ -507,6 +516,64 @@ __device__ __forceinline__ float st_of(const RenderBatch &rb, int r, int m, int 
     return __ldg(rb.state_s + (size_t)r * n_mat + m);
 }
 
+// Glass evaluations the next shading pass needs (the pending glass weight of
+// the last vertex, the slabs an unoccluded shadow ray crossed), compacted into
+// a query list for the learned model; a query index of -1 (list full) makes
+// the shading pass use the exact slab.
+__global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t np = a.ps.np;
+    const PathState &ps = a.ps;
+    const DevScene &sc = a.sc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
+        const int64_t q = base + lane;
+        int fl = q < np ? ps.flags[q] : 0;
+        int n_pend = 0, n_cr = 0, pm = 0;
+        if (fl & (kFlExt | kFlShadow)) {
+            if (fl & kFlPend) {
+                pm = ps.pend_mat[q];
+                n_pend = __ldg(sc.mat_kind + pm) == kGlass;
+            }
+            if (fl & kFlShadow) {
+                const int st = ps.sh_status[q];
+                if ((st & 3) == kShadowClear) n_cr = st >> 4;
+            }
+        }
+        const int cnt = n_pend + n_cr;
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long wb = 0;
+        if (lane == 31 && warp_total > 0) wb = atomicAdd(a.n_queries, (unsigned long long)warp_total);
+        wb = __shfl_sync(0xffffffffu, wb, 31);
+        if (cnt > 0) {
+            const int64_t gp = a.path_begin + q;
+            const int r = find_render(a.rb, gp);
+            int64_t idx = (int64_t)wb + incl - cnt;
+            if (n_pend) {
+                const int my = idx < a.q_cap ? (int)idx : -1;
+                if (my >= 0)
+                    a.queries[my] = make_float4(ps.pend_cos[q], st_of(a.rb, r, pm, sc.n_mat), __ldg(sc.mat_thick + pm),
+                                                __int_as_float(pm));
+                a.pend_query[q] = my;
+                ++idx;
+            }
+            for (int k = 0; k < n_cr; ++k, ++idx) {
+                const int cm = ps.cross_mat[k * np + q];
+                const int my = idx < a.q_cap ? (int)idx : -1;
+                if (my >= 0)
+                    a.queries[my] = make_float4(ps.cross_cos[k * np + q], st_of(a.rb, r, cm, sc.n_mat),
+                                                __ldg(sc.mat_thick + cm), __int_as_float(cm));
+                a.cross_query[k * np + q] = my;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_shade(KArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t np = a.ps.np;
@@ -596,10 +663,13 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
             const float pwabs = fabsf(pw);
             const bool preflect = pw < 0.0f;
             float cst[kMaxCross], cth[kMaxCross];
+            int cq[kMaxCross];
             for (int k = 0; k < ncr; ++k) {
                 cst[k] = st_of(a.rb, r, cmat[k], sc.n_mat);
                 cth[k] = __ldg(sc.mat_thick + cmat[k]);
+                cq[k] = a.use_mlp ? a.cross_query[k * np + q] : -1;
             }
+            const int pq = (a.use_mlp && pend && pkind == kGlass) ? a.pend_query[q] : -1;
             const bool need_T = resolve || pend || emit;
             if (need_T) {
                 Kahan NX, NY, NZ, EX, EY, EZ;
@@ -611,6 +681,10 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
                     if (resolve) {
                         float tr = 1.0f;
                         for (int k = 0; k < ncr; ++k) {
+                            if (cq[k] >= 0) {
+                                tr *= a.glass_res[(size_t)cq[k] * L + i].y;
+                                continue;
+                            }
                             const size_t kk = (size_t)cmat[k] * L + i;
                             float R_, T_;
                             slab_RT(ccos[k], __ldg(sc.lam + i), __ldg(sc.mat_a + kk),
@@ -630,6 +704,9 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
                             w = __ldg(pB + i);
                         } else if (pkind == kConductor) {
                             w = conductor_F(pcos, __ldg(pA + i), __ldg(pB + i));
+                        } else if (pq >= 0) {
+                            const float2 rt = a.glass_res[(size_t)pq * L + i];
+                            w = (preflect ? rt.x : rt.y) * pwabs;
                         } else {
                             float R_, T_;
                             slab_RT(pcos, __ldg(sc.lam + i), __ldg(pA + i), __ldg(pB + i) + ps_state * __ldg(pC + i),
@@ -810,6 +887,10 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
                  oCc = take(4 * kMaxCross * np), oH0 = take(16 * np), oH1 = take(16 * np), oIn = take(48 * cap),
                  oSt = take(48 * cap), oCtl = take(32 + 8 * (size_t)nc), oFill = take(8 * (size_t)nc),
                  oOff = take(4 * (2 * (size_t)nc + 1));
+    const bool use_mlp = run.bsdf_mode == SDDM_BSDF_MLP;
+    const int64_t q_cap = use_mlp ? 2 * np : 0;
+    const size_t oQ = take(16 * (size_t)q_cap + 16), oNq = take(16), oPq = take(use_mlp ? 4 * np : 4),
+                 oCq = take(use_mlp ? 4 * kMaxCross * np : 4), oRes = take(8 * (size_t)q_cap * L + 16);
     if (off > buf.bytes) {
         if (buf.mem) cudaFree(buf.mem);
         buf.mem = nullptr;
@@ -856,6 +937,28 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     Q.cnt = (int *)(m + oCtl + 32);
     Q.fill = (int *)(m + oFill);
     Q.off = (int *)(m + oOff);
+    a.use_mlp = use_mlp;
+    a.queries = (float4 *)(m + oQ);
+    a.n_queries = (unsigned long long *)(m + oNq);
+    a.q_cap = q_cap;
+    a.pend_query = (int *)(m + oPq);
+    a.cross_query = (int *)(m + oCq);
+    a.glass_res = (const float2 *)(m + oRes);
+    MlpRows mr{};
+    if (use_mlp) {
+        mr.params = run.mlp_params;
+        mr.sc = run.sc;
+        mr.thick_min = run.mlp_dmin;
+        mr.thick_max = run.mlp_dmax;
+        mr.probe_key = run.probe_key;
+        mr.queries = a.queries;
+        mr.n_queries = a.n_queries;
+        mr.q_cap = q_cap;
+        mr.results = (float2 *)(m + oRes);
+        mr.mode = 1;
+        mr.raw = 0;
+        mr.fallbacks = run.counters + 4;
+    }
 
     const int sm = std::max(1, run.sm_count);
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
@@ -894,6 +997,13 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
             *run.launches += 2;
         }
         a.b = b;
+        if (use_mlp && b >= 2) {
+            DDM_CHECK(cudaMemsetAsync(a.n_queries, 0, 8, s));
+            k_glass_gather<<<path_blocks, 256, 0, s>>>(a);
+            DDM_CHECK(cudaGetLastError());
+            DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s));
+            *run.launches += 2;
+        }
         k_shade<<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         *run.launches += 1;

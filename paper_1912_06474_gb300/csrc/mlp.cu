@@ -1,0 +1,712 @@
+// Learned surrogate of the glass slab's R and T (a stand-in for the exact
+// "Fresnel definition" of the glass, Sec. 6): a 4 -> 64 -> 64 -> 64 -> 2 SiLU
+// network evaluated and trained with BF16 tensor-core MMAs (m16n8k16, FP32
+// accumulation). The layers are 64 wide, so a warp carries a 16-row tile
+// through the whole network: the accumulator fragments of one layer, after
+// SiLU and rounding to BF16, are exactly the A fragments of the next layer,
+// so activations move through a 2 KB per-warp staging tile and never leave
+// the SM. Layer 1 (K = 4) and the output layer (N = 2) run on the FP32 pipes.
+//
+// Parameters (FP32 master copy, 8770 floats): W1[64][4], b1[64], W2[64][64],
+// b2[64], W3[64][64], b3[64], W4[2][64], b4[2]; z = W h + b. Inputs are mapped
+// to [-1, 1] over the trained box: 2 cos - 1, (lambda - 380) / 200 - 1, 2 s - 1,
+// 2 (d - d_min) / (d_max - d_min) - 1.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "sddm_mlp.h"
+
+namespace sddm {
+namespace {
+
+constexpr int H = 64;
+constexpr int OFF_W1 = 0, OFF_B1 = 256, OFF_W2 = 320, OFF_B2 = 4416, OFF_W3 = 4480, OFF_B3 = 8576, OFF_W4 = 8640,
+              OFF_B4 = 8768;
+static_assert(OFF_B4 + 2 == kMlpParams, "parameter layout");
+constexpr int LD = 72;   // shared-memory row stride (bf16): conflict-free 32-bit fragment loads
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float sigm(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+    const float g = sigm(z);
+    return g * fmaf(z, 1.0f - g, 1.0f);
+}
+
+// D += A B for one m16n8k16 BF16 tile, FP32 accumulators.
+__device__ __forceinline__ void mma16816(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// acc (16 x 64) += A (16 x K) * W^T, A rows and W rows K-contiguous in shared
+// memory with stride LD (W is [64][K], row n = output column n). Fragment
+// ownership: acc[j][0..1] = row g, cols 8j + 2t + {0,1}; acc[j][2..3] = row g + 8.
+template <int K>
+__device__ __forceinline__ void warp_gemm(float acc[8][4], const __nv_bfloat16 *A, const __nv_bfloat16 *W, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < K / 16; ++kk) {
+        const uint32_t *alo = reinterpret_cast<const uint32_t *>(A + g * LD + 16 * kk + 2 * t);
+        const uint32_t *ahi = reinterpret_cast<const uint32_t *>(A + (g + 8) * LD + 16 * kk + 2 * t);
+        const uint32_t a0 = alo[0], a1 = ahi[0], a2 = alo[4], a3 = ahi[4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t *bp = reinterpret_cast<const uint32_t *>(W + (8 * j + g) * LD + 16 * kk + 2 * t);
+            mma16816(acc[j], a0, a1, a2, a3, bp[0], bp[4]);
+        }
+    }
+}
+
+__device__ __forceinline__ void zero_acc(float acc[8][4]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+}
+
+__device__ __forceinline__ void features(float c, float lam, float s, float d, float dmin, float dmax, float x[4]) {
+    x[0] = 2.0f * c - 1.0f;
+    x[1] = (lam - 380.0f) * (1.0f / 200.0f) - 1.0f;
+    x[2] = 2.0f * s - 1.0f;
+    x[3] = 2.0f * (d - dmin) / (dmax - dmin) - 1.0f;
+}
+
+// ------------------------------------------------------------- inference
+struct InferSmem {
+    __nv_bfloat16 w2[H * LD], w3[H * LD];
+    float w1[H * 4], b1[H], b2[H], b3[H], w4[2 * H], b4[2];
+};
+
+__device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
+        const int r = i >> 6, c = i & 63;
+        s.w2[r * LD + c] = __float2bfloat16_rn(p[OFF_W2 + i]);
+        s.w3[r * LD + c] = __float2bfloat16_rn(p[OFF_W3 + i]);
+    }
+    for (int i = threadIdx.x; i < H * 4; i += blockDim.x) s.w1[i] = bf16r(p[OFF_W1 + i]);
+    for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) s.w4[i] = bf16r(p[OFF_W4 + i]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        s.b1[i] = p[OFF_B1 + i];
+        s.b2[i] = p[OFF_B2 + i];
+        s.b3[i] = p[OFF_B3 + i];
+    }
+    if (threadIdx.x < 2) s.b4[threadIdx.x] = p[OFF_B4 + threadIdx.x];
+}
+
+// The network on the 16 rows of a warp tile; this thread supplies the inputs
+// of rows g and g + 8 and receives their outputs (the same on the 4 lanes of
+// a group). act: the warp's 16 x LD staging tile.
+__device__ void tile_forward(const InferSmem &s, __nv_bfloat16 *act, const float xl[4], const float xh[4], int lane,
+                             float yl[2], float yh[2]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float hl[2], hh[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            float zl = s.b1[c], zh = s.b1[c];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                zl = fmaf(s.w1[4 * c + k], xl[k], zl);
+                zh = fmaf(s.w1[4 * c + k], xh[k], zh);
+            }
+            hl[e] = silu(zl);
+            hh[e] = silu(zh);
+        }
+        *reinterpret_cast<uint32_t *>(act + g * LD + 8 * j + 2 * t) = pack_bf16x2(hl[0], hl[1]);
+        *reinterpret_cast<uint32_t *>(act + (g + 8) * LD + 8 * j + 2 * t) = pack_bf16x2(hh[0], hh[1]);
+    }
+    __syncwarp();
+    float acc[8][4];
+    zero_acc(acc);
+    warp_gemm<H>(acc, act, s.w2, lane);
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        *reinterpret_cast<uint32_t *>(act + g * LD + c) =
+            pack_bf16x2(silu(acc[j][0] + s.b2[c]), silu(acc[j][1] + s.b2[c + 1]));
+        *reinterpret_cast<uint32_t *>(act + (g + 8) * LD + c) =
+            pack_bf16x2(silu(acc[j][2] + s.b2[c]), silu(acc[j][3] + s.b2[c + 1]));
+    }
+    __syncwarp();
+    zero_acc(acc);
+    warp_gemm<H>(acc, act, s.w3, lane);
+    __syncwarp();
+    float pl0 = 0.f, pl1 = 0.f, ph0 = 0.f, ph1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            const float hl = bf16r(silu(acc[j][e] + s.b3[c])), hh = bf16r(silu(acc[j][2 + e] + s.b3[c]));
+            pl0 = fmaf(s.w4[c], hl, pl0);
+            pl1 = fmaf(s.w4[H + c], hl, pl1);
+            ph0 = fmaf(s.w4[c], hh, ph0);
+            ph1 = fmaf(s.w4[H + c], hh, ph1);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        pl0 += __shfl_xor_sync(kFull, pl0, o);
+        pl1 += __shfl_xor_sync(kFull, pl1, o);
+        ph0 += __shfl_xor_sync(kFull, ph0, o);
+        ph1 += __shfl_xor_sync(kFull, ph1, o);
+    }
+    yl[0] = pl0 + s.b4[0];
+    yl[1] = pl1 + s.b4[1];
+    yh[0] = ph0 + s.b4[0];
+    yh[1] = ph1 + s.b4[1];
+}
+
+struct RowIn {
+    float c, lam, s, d;
+    int mat, bin;
+};
+
+__device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t total, RowIn &in) {
+    if (r >= total) {
+        in.c = 0.5f;
+        in.lam = 580.0f;
+        in.s = 0.5f;
+        in.d = 0.5f * (a.thick_min + a.thick_max);
+        in.mat = 0;
+        in.bin = 0;
+        return false;
+    }
+    const int L = a.sc.L;
+    if (a.mode == 0) {
+        int b = a.bin[r];
+        b = b < 0 ? 0 : (b >= L ? L - 1 : b);
+        in.c = a.cos_t[r];
+        in.s = a.s[r];
+        in.d = a.thick[r];
+        in.mat = (int)a.mat;
+        in.bin = b;
+    } else {
+        const int64_t q = r / L;
+        const float4 qq = a.queries[q];
+        in.c = qq.x;
+        in.s = qq.y;
+        in.d = qq.z;
+        in.mat = __float_as_int(qq.w);
+        in.bin = (int)(r - q * L);
+    }
+    in.lam = __ldg(a.sc.lam + in.bin);
+    return true;
+}
+
+__device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
+    const size_t k = (size_t)in.mat * a.sc.L + in.bin;
+    float R_, T_;
+    slab_RT(in.c, in.lam, __ldg(a.sc.mat_a + k), __ldg(a.sc.mat_b + k) + in.s * __ldg(a.sc.mat_c + k), in.d, R_, T_);
+    return make_float2(R_, T_);
+}
+
+// Rows are taken 32 at a time by a warp (two 16-row tiles). One row of each
+// batch, chosen by Philox, is also evaluated exactly; if it is off by more
+// than 1e-3 in R or T, or if any row lies outside the trained box, the whole
+// batch is evaluated exactly instead.
+__global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
+    __shared__ InferSmem s;
+    __shared__ __align__(16) __nv_bfloat16 act[8][16 * LD];
+    __shared__ float2 out[8][32];
+    load_infer_weights(s, a.params);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    int64_t total = a.n;
+    if (a.mode == 1) {
+        const int64_t nq = (int64_t)*a.n_queries;
+        total = (nq < a.q_cap ? nq : a.q_cap) * a.sc.L;
+    }
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long n_fb = 0;
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b * 32 < total; b += nwarps) {
+        const int64_t r0 = b * 32;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            RowIn il, ih;
+            row_input(a, r0 + 16 * half + g, total, il);
+            row_input(a, r0 + 16 * half + g + 8, total, ih);
+            float xl[4], xh[4], yl[2], yh[2];
+            features(il.c, il.lam, il.s, il.d, a.thick_min, a.thick_max, xl);
+            features(ih.c, ih.lam, ih.s, ih.d, a.thick_min, a.thick_max, xh);
+            tile_forward(s, act[w], xl, xh, lane, yl, yh);
+            if (t == 0) {
+                out[w][16 * half + g] = make_float2(yl[0], yl[1]);
+                out[w][16 * half + g + 8] = make_float2(yh[0], yh[1]);
+            }
+        }
+        __syncwarp();
+        RowIn in;
+        const bool valid = row_input(a, r0 + lane, total, in);
+        float2 y = out[w][lane];
+        const bool in_box = in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f &&
+                            in.s >= 0.0f && in.s <= 1.0f && in.d >= a.thick_min && in.d <= a.thick_max;
+        const bool box_ok = __all_sync(kFull, !valid || in_box);
+        const uint4 pr = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, kSlotProbe), a.probe_key,
+                                       0x50524f42u);
+        int pick = (int)(pr.x & 31u);
+        if (r0 + pick >= total) pick = 0;
+        int bad = 0;
+        if (lane == pick) {
+            const float2 e = exact_row(a, in);
+            bad = fabsf(e.x - y.x) > kMlpProbeTol || fabsf(e.y - y.y) > kMlpProbeTol;
+        }
+        bad = __shfl_sync(kFull, bad, pick);
+        if (!a.raw && (!box_ok || bad)) {
+            if (valid) y = exact_row(a, in);
+            if (lane == 0) ++n_fb;
+        }
+        if (valid) {
+            if (a.mode == 0) {
+                a.R[r0 + lane] = y.x;
+                a.T[r0 + lane] = y.y;
+            } else {
+                a.results[r0 + lane] = y;
+            }
+        }
+        __syncwarp();
+    }
+    if (a.fallbacks && n_fb) atomicAdd(a.fallbacks, n_fb);
+}
+
+// ---------------------------------------------------------------- training
+// One CTA = 64 rows = 4 warps x 16 rows: forward, loss gradient, backward,
+// and the CTA's share of every weight gradient, written to grad_cta[cta].
+struct TrainSmem {
+    __nv_bfloat16 w2[H * LD], w3[H * LD], w2t[H * LD], w3t[H * LD];
+    __nv_bfloat16 h1[H * LD], h2[H * LD], h3[H * LD], h1t[H * LD], h2t[H * LD];
+    __nv_bfloat16 dz3[H * LD], dz2[H * LD], dz3t[H * LD], dz2t[H * LD];
+    float z1[H * H], z2[H * H], z3[H * H];
+    float w1[H * 4], w4[2 * H], b1[H], b2[H], b3[H], b4[2];
+    float x[kMlpRowsPerCta * 4], y[kMlpRowsPerCta * 2];
+    float gw1[H * 4], gb1[H], gb2[H], gb3[H], gw4[2 * H], gb4[2], loss;
+};
+
+__global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TrainSmem &s = *reinterpret_cast<TrainSmem *>(smem_raw);
+    const float *__restrict__ p = a.params;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
+    const int cta = blockIdx.x;
+    for (int i = tid; i < H * H; i += blockDim.x) {
+        const int r = i >> 6, c = i & 63;
+        const __nv_bfloat16 v2 = __float2bfloat16_rn(p[OFF_W2 + i]), v3 = __float2bfloat16_rn(p[OFF_W3 + i]);
+        s.w2[r * LD + c] = v2;
+        s.w3[r * LD + c] = v3;
+        s.w2t[c * LD + r] = v2;
+        s.w3t[c * LD + r] = v3;
+    }
+    for (int i = tid; i < H * 4; i += blockDim.x) {
+        s.w1[i] = bf16r(p[OFF_W1 + i]);
+        s.gw1[i] = 0.f;
+    }
+    for (int i = tid; i < 2 * H; i += blockDim.x) {
+        s.w4[i] = bf16r(p[OFF_W4 + i]);
+        s.gw4[i] = 0.f;
+    }
+    for (int i = tid; i < H; i += blockDim.x) {
+        s.b1[i] = p[OFF_B1 + i];
+        s.b2[i] = p[OFF_B2 + i];
+        s.b3[i] = p[OFF_B3 + i];
+        s.gb1[i] = s.gb2[i] = s.gb3[i] = 0.f;
+    }
+    if (tid < 2) {
+        s.b4[tid] = p[OFF_B4 + tid];
+        s.gb4[tid] = 0.f;
+    }
+    if (tid == 0) s.loss = 0.f;
+    const int cta_row0 = cta * kMlpRowsPerCta;
+    for (int i = tid; i < kMlpRowsPerCta; i += blockDim.x) {
+        const bool ok = cta_row0 + i < a.n_rows;
+        const int64_t gr = (a.row0 + cta_row0 + i) % a.n_samples;
+        for (int k = 0; k < 4; ++k) s.x[4 * i + k] = ok ? a.X[4 * gr + k] : 0.f;
+        for (int k = 0; k < 2; ++k) s.y[2 * i + k] = ok ? a.Y[2 * gr + k] : 0.f;
+    }
+    __syncthreads();
+
+    const int rl = 16 * w + g, rh = rl + 8;   // this thread's two rows in the CTA
+    const bool okl = cta_row0 + rl < a.n_rows, okh = cta_row0 + rh < a.n_rows;
+    // ---- layer 1 (FP32 pipes, K = 4)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float hl[2], hh[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            float zl = s.b1[c], zh = s.b1[c];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                zl = fmaf(s.w1[4 * c + k], s.x[4 * rl + k], zl);
+                zh = fmaf(s.w1[4 * c + k], s.x[4 * rh + k], zh);
+            }
+            s.z1[rl * H + c] = zl;
+            s.z1[rh * H + c] = zh;
+            hl[e] = silu(zl);
+            hh[e] = silu(zh);
+            s.h1t[c * LD + rl] = __float2bfloat16_rn(hl[e]);
+            s.h1t[c * LD + rh] = __float2bfloat16_rn(hh[e]);
+        }
+        *reinterpret_cast<uint32_t *>(s.h1 + rl * LD + 8 * j + 2 * t) = pack_bf16x2(hl[0], hl[1]);
+        *reinterpret_cast<uint32_t *>(s.h1 + rh * LD + 8 * j + 2 * t) = pack_bf16x2(hh[0], hh[1]);
+    }
+    __syncwarp();
+    // ---- layer 2
+    float acc[8][4];
+    zero_acc(acc);
+    warp_gemm<H>(acc, s.h1 + 16 * w * LD, s.w2, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        const float zl0 = acc[j][0] + s.b2[c], zl1 = acc[j][1] + s.b2[c + 1];
+        const float zh0 = acc[j][2] + s.b2[c], zh1 = acc[j][3] + s.b2[c + 1];
+        s.z2[rl * H + c] = zl0;
+        s.z2[rl * H + c + 1] = zl1;
+        s.z2[rh * H + c] = zh0;
+        s.z2[rh * H + c + 1] = zh1;
+        const float a0 = silu(zl0), a1 = silu(zl1), a2 = silu(zh0), a3 = silu(zh1);
+        *reinterpret_cast<uint32_t *>(s.h2 + rl * LD + c) = pack_bf16x2(a0, a1);
+        *reinterpret_cast<uint32_t *>(s.h2 + rh * LD + c) = pack_bf16x2(a2, a3);
+        s.h2t[c * LD + rl] = __float2bfloat16_rn(a0);
+        s.h2t[(c + 1) * LD + rl] = __float2bfloat16_rn(a1);
+        s.h2t[c * LD + rh] = __float2bfloat16_rn(a2);
+        s.h2t[(c + 1) * LD + rh] = __float2bfloat16_rn(a3);
+    }
+    __syncwarp();
+    // ---- layer 3 and the output layer
+    zero_acc(acc);
+    warp_gemm<H>(acc, s.h2 + 16 * w * LD, s.w3, lane);
+    float h3l[16], h3h[16];
+    float yl0 = 0.f, yl1 = 0.f, yh0 = 0.f, yh1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            const float zl = acc[j][e] + s.b3[c], zh = acc[j][2 + e] + s.b3[c];
+            s.z3[rl * H + c] = zl;
+            s.z3[rh * H + c] = zh;
+            h3l[2 * j + e] = bf16r(silu(zl));
+            h3h[2 * j + e] = bf16r(silu(zh));
+            yl0 = fmaf(s.w4[c], h3l[2 * j + e], yl0);
+            yl1 = fmaf(s.w4[H + c], h3l[2 * j + e], yl1);
+            yh0 = fmaf(s.w4[c], h3h[2 * j + e], yh0);
+            yh1 = fmaf(s.w4[H + c], h3h[2 * j + e], yh1);
+        }
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        yl0 += __shfl_xor_sync(kFull, yl0, o);
+        yl1 += __shfl_xor_sync(kFull, yl1, o);
+        yh0 += __shfl_xor_sync(kFull, yh0, o);
+        yh1 += __shfl_xor_sync(kFull, yh1, o);
+    }
+    yl0 += s.b4[0];
+    yl1 += s.b4[1];
+    yh0 += s.b4[0];
+    yh1 += s.b4[1];
+    // ---- loss gradient: d/dy of mean over (rows x 2 outputs) of squared error
+    const float scale = 1.0f / (float)a.n_rows;
+    const float el0 = okl ? yl0 - s.y[2 * rl] : 0.f, el1 = okl ? yl1 - s.y[2 * rl + 1] : 0.f;
+    const float eh0 = okh ? yh0 - s.y[2 * rh] : 0.f, eh1 = okh ? yh1 - s.y[2 * rh + 1] : 0.f;
+    const float dyl0 = scale * el0, dyl1 = scale * el1, dyh0 = scale * eh0, dyh1 = scale * eh1;
+    if (t == 0) {
+        float lsum = el0 * el0 + el1 * el1 + eh0 * eh0 + eh1 * eh1;
+        float b0 = dyl0 + dyh0, b1 = dyl1 + dyh1;
+        for (int o = 4; o <= 16; o <<= 1) {
+            lsum += __shfl_xor_sync(0x11111111u, lsum, o);
+            b0 += __shfl_xor_sync(0x11111111u, b0, o);
+            b1 += __shfl_xor_sync(0x11111111u, b1, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&s.loss, lsum);
+            atomicAdd(&s.gb4[0], b0);
+            atomicAdd(&s.gb4[1], b1);
+        }
+    }
+    // dW4 and dz3
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            float g0 = dyl0 * h3l[2 * j + e] + dyh0 * h3h[2 * j + e];
+            float g1 = dyl1 * h3l[2 * j + e] + dyh1 * h3h[2 * j + e];
+            for (int o = 4; o <= 16; o <<= 1) {
+                g0 += __shfl_xor_sync(kFull, g0, o);
+                g1 += __shfl_xor_sync(kFull, g1, o);
+            }
+            if (g == 0) {
+                atomicAdd(&s.gw4[c], g0);
+                atomicAdd(&s.gw4[H + c], g1);
+            }
+            const float dzl = (dyl0 * s.w4[c] + dyl1 * s.w4[H + c]) * dsilu(s.z3[rl * H + c]);
+            const float dzh = (dyh0 * s.w4[c] + dyh1 * s.w4[H + c]) * dsilu(s.z3[rh * H + c]);
+            s.dz3[rl * LD + c] = __float2bfloat16_rn(dzl);
+            s.dz3[rh * LD + c] = __float2bfloat16_rn(dzh);
+            s.dz3t[c * LD + rl] = __float2bfloat16_rn(dzl);
+            s.dz3t[c * LD + rh] = __float2bfloat16_rn(dzh);
+            float gb = dzl + dzh;
+            for (int o = 4; o <= 16; o <<= 1) gb += __shfl_xor_sync(kFull, gb, o);
+            if (g == 0) atomicAdd(&s.gb3[c], gb);
+        }
+    }
+    __syncthreads();
+    float *gout = a.grad_cta + (size_t)cta * kMlpParams;
+    // ---- dW3 = dz3^T h2 (warp w: output units 16w .. 16w + 15, K = the CTA's 64 rows)
+    zero_acc(acc);
+    warp_gemm<kMlpRowsPerCta>(acc, s.dz3t + 16 * w * LD, s.h2t, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        gout[OFF_W3 + rl * H + c] = acc[j][0];
+        gout[OFF_W3 + rl * H + c + 1] = acc[j][1];
+        gout[OFF_W3 + rh * H + c] = acc[j][2];
+        gout[OFF_W3 + rh * H + c + 1] = acc[j][3];
+    }
+    // ---- dh2 = dz3 W3, dz2
+    zero_acc(acc);
+    warp_gemm<H>(acc, s.dz3 + 16 * w * LD, s.w3t, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            const float dzl = acc[j][e] * dsilu(s.z2[rl * H + c]), dzh = acc[j][2 + e] * dsilu(s.z2[rh * H + c]);
+            s.dz2[rl * LD + c] = __float2bfloat16_rn(dzl);
+            s.dz2[rh * LD + c] = __float2bfloat16_rn(dzh);
+            s.dz2t[c * LD + rl] = __float2bfloat16_rn(dzl);
+            s.dz2t[c * LD + rh] = __float2bfloat16_rn(dzh);
+            float gb = dzl + dzh;
+            for (int o = 4; o <= 16; o <<= 1) gb += __shfl_xor_sync(kFull, gb, o);
+            if (g == 0) atomicAdd(&s.gb2[c], gb);
+        }
+    }
+    __syncthreads();
+    // ---- dW2 = dz2^T h1
+    zero_acc(acc);
+    warp_gemm<kMlpRowsPerCta>(acc, s.dz2t + 16 * w * LD, s.h1t, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        gout[OFF_W2 + rl * H + c] = acc[j][0];
+        gout[OFF_W2 + rl * H + c + 1] = acc[j][1];
+        gout[OFF_W2 + rh * H + c] = acc[j][2];
+        gout[OFF_W2 + rh * H + c + 1] = acc[j][3];
+    }
+    // ---- dh1 = dz2 W2, dz1, dW1, db1
+    zero_acc(acc);
+    warp_gemm<H>(acc, s.dz2 + 16 * w * LD, s.w2t, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int c = 8 * j + 2 * t + e;
+            const float dzl = acc[j][e] * dsilu(s.z1[rl * H + c]), dzh = acc[j][2 + e] * dsilu(s.z1[rh * H + c]);
+            float gb = dzl + dzh;
+            float gk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gk[k] = dzl * s.x[4 * rl + k] + dzh * s.x[4 * rh + k];
+            for (int o = 4; o <= 16; o <<= 1) {
+                gb += __shfl_xor_sync(kFull, gb, o);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) gk[k] += __shfl_xor_sync(kFull, gk[k], o);
+            }
+            if (g == 0) {
+                atomicAdd(&s.gb1[c], gb);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) atomicAdd(&s.gw1[4 * c + k], gk[k]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < H * 4; i += blockDim.x) gout[OFF_W1 + i] = s.gw1[i];
+    for (int i = tid; i < 2 * H; i += blockDim.x) gout[OFF_W4 + i] = s.gw4[i];
+    for (int i = tid; i < H; i += blockDim.x) {
+        gout[OFF_B1 + i] = s.gb1[i];
+        gout[OFF_B2 + i] = s.gb2[i];
+        gout[OFF_B3 + i] = s.gb3[i];
+    }
+    if (tid < 2) gout[OFF_B4 + tid] = s.gb4[tid];
+    if (tid == 0) a.loss_cta[cta] = s.loss;
+}
+
+// Sum of the per-CTA gradients in CTA order (deterministic), then Adam with
+// bias corrections bc1 = 1 - beta1^t, bc2 = 1 - beta2^t. With grad_out the
+// summed gradient is only written out (no update).
+__global__ void k_mlp_adam(float *params, float *m, float *v, const float *grad_cta, const float *loss_cta, int n_cta,
+                           float lr, float bc1, float bc2, float *grad_out, float *loss_out, float loss_scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && loss_out) {
+        float l = 0.f;
+        for (int c = 0; c < n_cta; ++c) l += loss_cta[c];
+        *loss_out = l * loss_scale;
+    }
+    if (i >= kMlpParams) return;
+    float gsum = 0.f;
+    for (int c = 0; c < n_cta; ++c) gsum += grad_cta[(size_t)c * kMlpParams + i];
+    if (grad_out) {
+        grad_out[i] = gsum;
+        return;
+    }
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float mi = b1 * m[i] + (1.0f - b1) * gsum;
+    const float vi = b2 * v[i] + (1.0f - b2) * gsum * gsum;
+    m[i] = mi;
+    v[i] = vi;
+    params[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// Exact training samples: (cos, lambda, s, d) uniform over the trained box,
+// lambda continuous (material curves linearly interpolated between bins).
+__global__ void k_mlp_data(DevScene sc, uint32_t mat, int64_t n, uint32_t seed, float dmin, float dmax, float *X,
+                           float *Y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 u = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0u, 0x20001u), seed, 0x4d4c5044u);
+    const float c = u01(u.x), lam = 380.0f + 400.0f * u01(u.y), st = u01(u.z), d = dmin + (dmax - dmin) * u01(u.w);
+    const int L = sc.L;
+    int lo = 0, hi = L - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(sc.lam + mid) <= lam) lo = mid; else hi = mid;
+    }
+    const float l0 = __ldg(sc.lam + lo), l1 = __ldg(sc.lam + hi);
+    const float f = l1 > l0 ? fminf(fmaxf((lam - l0) / (l1 - l0), 0.0f), 1.0f) : 0.0f;
+    const size_t k0 = (size_t)mat * L + lo, k1 = (size_t)mat * L + hi;
+    const float nn = (1.0f - f) * __ldg(sc.mat_a + k0) + f * __ldg(sc.mat_a + k1);
+    const float ac = (1.0f - f) * __ldg(sc.mat_b + k0) + f * __ldg(sc.mat_b + k1);
+    const float da = (1.0f - f) * __ldg(sc.mat_c + k0) + f * __ldg(sc.mat_c + k1);
+    float R_, T_;
+    slab_RT(c, lam, nn, ac + st * da, d, R_, T_);
+    float x[4];
+    features(c, lam, st, d, dmin, dmax, x);
+    for (int k = 0; k < 4; ++k) X[4 * i + k] = x[k];
+    Y[2 * i] = R_;
+    Y[2 * i + 1] = T_;
+}
+
+// Xavier-uniform initial weights from Philox, zero biases.
+__global__ void k_mlp_init(float *p, uint32_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    float bound = 0.0f;
+    if (i < OFF_B1) bound = sqrtf(6.0f / (4 + H));
+    else if (i >= OFF_W2 && i < OFF_B2) bound = sqrtf(6.0f / (H + H));
+    else if (i >= OFF_W3 && i < OFF_B3) bound = sqrtf(6.0f / (H + H));
+    else if (i >= OFF_W4 && i < OFF_B4) bound = sqrtf(6.0f / (H + 2));
+    const uint4 u = philox4x32_10(make_uint4((uint32_t)i, 0u, 0u, 0x20002u), seed, 0x494e4954u);
+    p[i] = bound * (2.0f * u01(u.x) - 1.0f);
+}
+
+// Max |error| of R and T over a held-out grid of the trained box (cos, bin, s, d).
+__global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
+    __shared__ InferSmem s;
+    __shared__ __align__(16) __nv_bfloat16 act[8][16 * LD];
+    load_infer_weights(s, a.params);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int L = a.sc.L;
+    const int nc = 17, ns = 5, nd = 5;
+    const int64_t total = (int64_t)nc * L * ns * nd;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    auto grid_in = [&](int64_t r, RowIn &in) {
+        int64_t q = r;
+        const int ic = (int)(q % nc);
+        q /= nc;
+        const int ib = (int)(q % L);
+        q /= L;
+        const int is = (int)(q % ns);
+        q /= ns;
+        const int id = (int)q;
+        in.c = (ic + 0.5f) / nc;
+        in.bin = ib;
+        in.lam = __ldg(a.sc.lam + ib);
+        in.s = (is + 0.5f) / ns;
+        in.d = a.thick_min + (a.thick_max - a.thick_min) * (id + 0.5f) / nd;
+        in.mat = (int)a.mat;
+    };
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b * 16 < total; b += nwarps) {
+        const int64_t r0 = b * 16;
+        RowIn il, ih;
+        grid_in(min(r0 + g, total - 1), il);
+        grid_in(min(r0 + g + 8, total - 1), ih);
+        float xl[4], xh[4], yl[2], yh[2];
+        features(il.c, il.lam, il.s, il.d, a.thick_min, a.thick_max, xl);
+        features(ih.c, ih.lam, ih.s, ih.d, a.thick_min, a.thick_max, xh);
+        tile_forward(s, act[w], xl, xh, lane, yl, yh);
+        if (t == 0) {
+            const float2 el = exact_row(a, il), eh = exact_row(a, ih);
+            atomicMax(max_err + 0, __float_as_uint(fmaxf(fabsf(el.x - yl[0]), fabsf(eh.x - yh[0]))));
+            atomicMax(max_err + 1, __float_as_uint(fmaxf(fabsf(el.y - yl[1]), fabsf(eh.y - yh[1]))));
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
+
+cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
+    const int blocks = sm_count * 2;
+    k_mlp_rows<<<blocks, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train_tile(const MlpTrainArgs &a, cudaStream_t stream) {
+    static bool attr_set = false;
+    const size_t bytes = sizeof(TrainSmem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int n_cta = (a.n_rows + kMlpRowsPerCta - 1) / kMlpRowsPerCta;
+    k_mlp_train_tile<<<n_cta, 128, bytes, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_adam(float *params, float *m, float *v, const float *grad_cta, const float *loss_cta, int n_cta,
+                            float lr, float bc1, float bc2, float *grad_out, float *loss_out, float loss_scale,
+                            cudaStream_t stream) {
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(params, m, v, grad_cta, loss_cta, n_cta, lr, bc1, bc2,
+                                                             grad_out, loss_out, loss_scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_data(const DevScene &sc, uint32_t mat, float, int64_t n, uint32_t seed, float dmin, float dmax,
+                            float *X, float *Y, cudaStream_t stream) {
+    k_mlp_data<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, mat, n, seed, dmin, dmax, X, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_init(float *params, uint32_t seed, cudaStream_t stream) {
+    k_mlp_init<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(params, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_grid_error(const float *params, const DevScene &sc, uint32_t mat, float dmin, float dmax,
+                                  unsigned int *max_err, cudaStream_t stream) {
+    MlpRows a{};
+    a.params = params;
+    a.sc = sc;
+    a.mat = mat;
+    a.thick_min = dmin;
+    a.thick_max = dmax;
+    k_mlp_grid_error<<<152, 256, 0, stream>>>(a, max_err);
+    return cudaGetLastError();
+}
+
+}  // namespace sddm

@@ -17,6 +17,7 @@
 
 #include "sddm_internal.h"
 #include "sddm_ddm.h"
+#include "sddm_mlp.h"
 
 namespace sddm {
 
@@ -100,6 +101,15 @@ struct sddm_ctx {
     DDMBuffers ddm_buf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int profile = 0;
+    // learned glass surrogates: one network may serve several materials
+    struct MlpNet {
+        DevBuf params, m, v;
+        int64_t step = 0;
+        float dmin = 0.002f, dmax = 0.010f;
+    };
+    std::vector<std::unique_ptr<MlpNet>> nets;
+    std::vector<int> net_of_mat;     // per material, -1 = none
+    DevBuf mlp_grad_cta, mlp_loss_cta, mlp_scalar, mlp_X, mlp_Y;
 };
 
 extern "C" {
@@ -556,8 +566,26 @@ extern "C" {
 int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st) {
     int rc = validate_desc(ctx, d, n);
     if (rc != SDDM_OK) return rc;
-    if (d[0].bsdf_mode == SDDM_BSDF_MLP)
-        return fail(SDDM_ERR_MLP_UNTRAINED, "sddm_render: SDDM_BSDF_MLP needs trained weights");
+    const float *mlp_params = nullptr;
+    float mlp_dmin = 0.f, mlp_dmax = 0.f;
+    if (d[0].bsdf_mode == SDDM_BSDF_MLP) {
+        if (d[0].method != SDDM_METHOD_DDM)
+            return fail(SDDM_ERR_INVALID_ARG, "sddm_render: the learned glass model runs with the DDM method");
+        int net_id = -1;
+        ctx->net_of_mat.resize(ctx->mats.size(), -1);
+        for (size_t m = 0; m < ctx->mats.size(); ++m) {
+            if (ctx->mats[m].kind != kGlass) continue;
+            const int id = ctx->net_of_mat[m];
+            if (id < 0) return fail(SDDM_ERR_MLP_UNTRAINED, "sddm_render: a glass material has no trained surrogate");
+            if (net_id >= 0 && id != net_id)
+                return fail(SDDM_ERR_INVALID_ARG, "sddm_render: the learned model supports one network per call");
+            net_id = id;
+        }
+        if (net_id < 0) return fail(SDDM_ERR_INVALID_ARG, "sddm_render: no glass material in the scene");
+        mlp_params = ctx->nets[net_id]->params.as<float>();
+        mlp_dmin = ctx->nets[net_id]->dmin;
+        mlp_dmax = ctx->nets[net_id]->dmax;
+    }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "sddm_render: cudaSetDevice");
     const int M = (int)ctx->mats.size();
@@ -675,6 +703,10 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
             run.time_trace = time_trace;
             run.count_traversal = count_trav;
             run.launches = &launches;
+            run.mlp_params = mlp_params;
+            run.mlp_dmin = mlp_dmin;
+            run.mlp_dmax = mlp_dmax;
+            run.probe_key = d[0].seed ^ 0x9e3779b9u;
             int rc2 = ddm_trace_chunk(run, ctx->ddm_buf, s);
             if (rc2 != SDDM_OK) return rc2;
         }
@@ -845,6 +877,234 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
     return SDDM_OK;
 }
 
+// ---------------------------------------------------- learned glass surrogate
+static bool same_curves(const Material &a, const Material &b) {
+    return a.kind == kGlass && b.kind == kGlass && a.a == b.a && a.b == b.b && a.c == b.c;
+}
+
+static int mlp_net_for(sddm_ctx *ctx, uint32_t mat, bool create, sddm_ctx::MlpNet **out) {
+    if (mat >= ctx->mats.size() || ctx->mats[mat].kind != kGlass)
+        return fail(SDDM_ERR_INVALID_ARG, "surrogate: material is not a glass slab");
+    ctx->net_of_mat.resize(ctx->mats.size(), -1);
+    int id = ctx->net_of_mat[mat];
+    if (id < 0) {
+        if (!create) return fail(SDDM_ERR_MLP_UNTRAINED, "surrogate: no weights for this material");
+        ctx->nets.emplace_back(new sddm_ctx::MlpNet());
+        id = (int)ctx->nets.size() - 1;
+        cudaError_t e;
+        sddm_ctx::MlpNet &n = *ctx->nets.back();
+        if ((e = n.params.ensure(kMlpParams * 4)) || (e = n.m.ensure(kMlpParams * 4)) || (e = n.v.ensure(kMlpParams * 4)))
+            return cuda_fail(e, "surrogate: allocation");
+        for (size_t m = 0; m < ctx->mats.size(); ++m)
+            if (same_curves(ctx->mats[m], ctx->mats[mat]) && ctx->net_of_mat[m] < 0) ctx->net_of_mat[m] = id;
+    }
+    *out = ctx->nets[id].get();
+    return SDDM_OK;
+}
+
+int sddm_mlp_train(sddm_ctx *ctx, uint32_t mat, const sddm_mlp_train_opts *opts, sddm_mlp_report *rep) {
+    if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_train: ctx is NULL");
+    if (!ctx->built) return fail(SDDM_ERR_NOT_BUILT, "sddm_mlp_train: call sddm_build first");
+    sddm_mlp_train_opts o{};
+    if (opts) o = *opts;
+    if (o.samples <= 0) o.samples = (int64_t)1 << 22;
+    if (o.steps <= 0) o.steps = 20000;
+    if (o.batch <= 0) o.batch = 8192;
+    if (o.lr <= 0.f) o.lr = 1e-3f;
+    if (o.thick_min <= 0.f && o.thick_max <= 0.f) {
+        o.thick_min = 0.002f;
+        o.thick_max = 0.010f;
+    }
+    if (o.batch % kMlpRowsPerCta || o.batch > (1 << 20) || o.samples > ((int64_t)1 << 28) ||
+        !(o.thick_max > o.thick_min) || o.thick_min <= 0.f)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_train: batch must be a multiple of 64 (<= 2^20), "
+                                          "samples <= 2^28, 0 < thick_min < thick_max");
+    sddm_ctx::MlpNet *net = nullptr;
+    int rc = mlp_net_for(ctx, mat, true, &net);
+    if (rc != SDDM_OK) return rc;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int n_cta = o.batch / kMlpRowsPerCta;
+    if ((e = ctx->mlp_grad_cta.ensure((size_t)n_cta * kMlpParams * 4)) || (e = ctx->mlp_loss_cta.ensure(n_cta * 4)) ||
+        (e = ctx->mlp_scalar.ensure(64)) || (e = ctx->mlp_X.ensure((size_t)o.samples * 16)) ||
+        (e = ctx->mlp_Y.ensure((size_t)o.samples * 8)))
+        return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_mlp_train: allocation failed")
+                                              : cuda_fail(e, "sddm_mlp_train: allocation");
+    if (!o.resume || net->step == 0) {
+        if ((e = launch_mlp_init(net->params.as<float>(), o.seed, s)) ||
+            (e = cudaMemsetAsync(net->m.p, 0, kMlpParams * 4, s)) || (e = cudaMemsetAsync(net->v.p, 0, kMlpParams * 4, s)))
+            return cuda_fail(e, "sddm_mlp_train: init");
+        net->step = 0;
+    }
+    net->dmin = o.thick_min;
+    net->dmax = o.thick_max;
+    if ((e = launch_mlp_data(ctx->dev, mat, 0.f, o.samples, o.seed, o.thick_min, o.thick_max, ctx->mlp_X.as<float>(),
+                             ctx->mlp_Y.as<float>(), s)))
+        return cuda_fail(e, "sddm_mlp_train: data");
+    if ((e = cudaEventRecord(ctx->ev0, s))) return cuda_fail(e, "sddm_mlp_train: event");
+    const int64_t t_end = net->step + o.steps;
+    for (int k = 0; k < o.steps; ++k) {
+        const int64_t t = net->step + 1;
+        MlpTrainArgs a;
+        a.params = net->params.as<float>();
+        a.X = ctx->mlp_X.as<float>();
+        a.Y = ctx->mlp_Y.as<float>();
+        a.n_samples = o.samples;
+        a.row0 = ((t - 1) * (int64_t)o.batch) % o.samples;
+        a.n_rows = o.batch;
+        a.grad_cta = ctx->mlp_grad_cta.as<float>();
+        a.loss_cta = ctx->mlp_loss_cta.as<float>();
+        if ((e = launch_mlp_train_tile(a, s))) return cuda_fail(e, "sddm_mlp_train: train kernel");
+        // cosine decay from lr to lr / 100 over this call's steps
+        const double frac = (double)(t - (t_end - o.steps)) / (double)o.steps;
+        const float lr = (float)(o.lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
+        const float bc1 = (float)(1.0 - std::pow(0.9, (double)t)), bc2 = (float)(1.0 - std::pow(0.999, (double)t));
+        const bool last = k == o.steps - 1;
+        if ((e = launch_mlp_adam(net->params.as<float>(), net->m.as<float>(), net->v.as<float>(), a.grad_cta,
+                                 a.loss_cta, n_cta, lr, bc1, bc2, nullptr, last ? ctx->mlp_scalar.as<float>() : nullptr,
+                                 1.0f / (2.0f * (float)o.batch), s)))
+            return cuda_fail(e, "sddm_mlp_train: adam kernel");
+        net->step = t;
+    }
+    if ((e = cudaEventRecord(ctx->ev1, s))) return cuda_fail(e, "sddm_mlp_train: event");
+    unsigned int *errs = reinterpret_cast<unsigned int *>(ctx->mlp_scalar.as<char>() + 16);
+    if ((e = cudaMemsetAsync(errs, 0, 8, s)) ||
+        (e = launch_mlp_grid_error(net->params.as<float>(), ctx->dev, mat, o.thick_min, o.thick_max, errs, s)))
+        return cuda_fail(e, "sddm_mlp_train: held-out error");
+    float loss = 0.f;
+    unsigned int me[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(&loss, ctx->mlp_scalar.p, 4, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(me, errs, 8, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "sddm_mlp_train: execution");
+    // the training samples are not needed afterwards
+    ctx->mlp_X.release();
+    ctx->mlp_Y.release();
+    if (rep) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        rep->final_loss = loss;
+        float eR, eT;
+        std::memcpy(&eR, &me[0], 4);
+        std::memcpy(&eT, &me[1], 4);
+        rep->max_abs_err_R = eR;
+        rep->max_abs_err_T = eT;
+        rep->train_ms = ms;
+        const double flop = 3.0 * 2.0 * (64.0 * 64.0 * 2.0) * (double)o.batch * o.steps;   // tensor-core GEMMs
+        rep->tflops = ms > 0 ? flop / (ms * 1e-3) / 1e12 : 0.0;
+        rep->steps = net->step;
+    }
+    return SDDM_OK;
+}
+
+int sddm_mlp_get_weights(sddm_ctx *ctx, uint32_t mat, float *params) {
+    if (!ctx || !params) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_get_weights: NULL");
+    sddm_ctx::MlpNet *net = nullptr;
+    int rc = mlp_net_for(ctx, mat, false, &net);
+    if (rc != SDDM_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(params, net->params.p, kMlpParams * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_mlp_get_weights");
+}
+
+int sddm_mlp_set_weights(sddm_ctx *ctx, uint32_t mat, const float *params, float thick_min, float thick_max) {
+    if (!ctx || !params) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_set_weights: NULL");
+    for (int i = 0; i < kMlpParams; ++i)
+        if (!std::isfinite(params[i])) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_set_weights: non-finite weight");
+    if (!(thick_max > thick_min) || thick_min <= 0.f)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_set_weights: need 0 < thick_min < thick_max");
+    sddm_ctx::MlpNet *net = nullptr;
+    int rc = mlp_net_for(ctx, mat, true, &net);
+    if (rc != SDDM_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(net->params.p, params, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->m.p, 0, kMlpParams * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->v.p, 0, kMlpParams * 4, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    net->step = 0;
+    net->dmin = thick_min;
+    net->dmax = thick_max;
+    return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_mlp_set_weights");
+}
+
+int sddm_mlp_save(sddm_ctx *ctx, uint32_t mat, const char *path) {
+    if (!ctx || !path) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_save: NULL");
+    sddm_ctx::MlpNet *net = nullptr;
+    int rc = mlp_net_for(ctx, mat, false, &net);
+    if (rc != SDDM_OK) return rc;
+    std::vector<float> buf(3 * (size_t)kMlpParams);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), net->params.p, kMlpParams * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(buf.data() + kMlpParams, net->m.p, kMlpParams * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(buf.data() + 2 * kMlpParams, net->v.p, kMlpParams * 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (e) return cuda_fail(e, "sddm_mlp_save");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(SDDM_ERR_INVALID_ARG, std::string("sddm_mlp_save: cannot open ") + path);
+    const char magic[8] = {'S', 'D', 'D', 'M', 'M', 'L', 'P', '1'};
+    const int32_t np = kMlpParams;
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&np, 4, 1, f) == 1 &&
+              std::fwrite(&net->step, 8, 1, f) == 1 && std::fwrite(&net->dmin, 4, 1, f) == 1 &&
+              std::fwrite(&net->dmax, 4, 1, f) == 1 && std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SDDM_OK : fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_save: write failed");
+}
+
+int sddm_mlp_load(sddm_ctx *ctx, uint32_t mat, const char *path) {
+    if (!ctx || !path) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_load: NULL");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(SDDM_ERR_INVALID_ARG, std::string("sddm_mlp_load: cannot open ") + path);
+    char magic[8];
+    int32_t np = 0;
+    int64_t step = 0;
+    float dmin = 0, dmax = 0;
+    std::vector<float> buf(3 * (size_t)kMlpParams);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "SDDMMLP1", 8) == 0 &&
+              std::fread(&np, 4, 1, f) == 1 && np == kMlpParams && std::fread(&step, 8, 1, f) == 1 &&
+              std::fread(&dmin, 4, 1, f) == 1 && std::fread(&dmax, 4, 1, f) == 1 &&
+              std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok || step < 0 || !(dmax > dmin) || dmin <= 0.f)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_load: not a valid surrogate checkpoint");
+    for (float x : buf)
+        if (!std::isfinite(x)) return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_load: non-finite values");
+    sddm_ctx::MlpNet *net = nullptr;
+    int rc = mlp_net_for(ctx, mat, true, &net);
+    if (rc != SDDM_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(net->params.p, buf.data(), kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(net->m.p, buf.data() + kMlpParams, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(net->v.p, buf.data() + 2 * kMlpParams, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (e) return cuda_fail(e, "sddm_mlp_load");
+    net->step = step;
+    net->dmin = dmin;
+    net->dmax = dmax;
+    return SDDM_OK;
+}
+
+int sddm_mlp_grad(sddm_ctx *ctx, int n, const float *X, const float *Y, const float *params, float *grad,
+                  float *loss) {
+    if (!ctx || n <= 0 || n > (1 << 20) || !X || !Y || !params || !grad || !loss)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_mlp_grad: bad arguments");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int n_cta = (n + kMlpRowsPerCta - 1) / kMlpRowsPerCta;
+    if ((e = ctx->mlp_grad_cta.ensure((size_t)n_cta * kMlpParams * 4)) || (e = ctx->mlp_loss_cta.ensure(n_cta * 4)))
+        return cuda_fail(e, "sddm_mlp_grad: allocation");
+    MlpTrainArgs a;
+    a.params = params;
+    a.X = X;
+    a.Y = Y;
+    a.n_samples = n;
+    a.row0 = 0;
+    a.n_rows = n;
+    a.grad_cta = ctx->mlp_grad_cta.as<float>();
+    a.loss_cta = ctx->mlp_loss_cta.as<float>();
+    if ((e = launch_mlp_train_tile(a, s)) ||
+        (e = launch_mlp_adam(nullptr, nullptr, nullptr, a.grad_cta, a.loss_cta, n_cta, 0.f, 1.f, 1.f, grad, loss,
+                             1.0f / (2.0f * (float)n), s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "sddm_mlp_grad");
+    return SDDM_OK;
+}
+
 int sddm_set_profiling(sddm_ctx *ctx, int flags) {
     if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: ctx is NULL");
     if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL))
@@ -861,7 +1121,32 @@ int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, 
         return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: mat is not a glass slab");
     if (n < 0 || (n > 0 && (!cos_theta || !bin || !s || !thickness_m || !R || !T)))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: bad arguments");
-    if (mode == SDDM_BSDF_MLP) return fail(SDDM_ERR_MLP_UNTRAINED, "sddm_glass_eval: no trained weights");
+    if (mode == SDDM_BSDF_MLP || mode == SDDM_BSDF_MLP_RAW) {
+        sddm_ctx::MlpNet *net = nullptr;
+        int rc = mlp_net_for(ctx, mat, false, &net);
+        if (rc != SDDM_OK) return rc;
+        MlpRows a{};
+        a.params = net->params.as<float>();
+        a.sc = ctx->dev;
+        a.thick_min = net->dmin;
+        a.thick_max = net->dmax;
+        a.probe_key = 0x5eed;
+        a.n = n;
+        a.mat = mat;
+        a.cos_t = cos_theta;
+        a.s = s;
+        a.thick = thickness_m;
+        a.bin = bin;
+        a.R = R;
+        a.T = T;
+        a.mode = 0;
+        a.raw = mode == SDDM_BSDF_MLP_RAW;
+        a.fallbacks = nullptr;
+        cudaError_t e = cudaSetDevice(ctx->device);
+        if (e == cudaSuccess) e = launch_mlp_rows(a, ctx->sm_count, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_glass_eval (surrogate)");
+    }
     if (mode != SDDM_BSDF_EXACT) return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: unknown mode");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = launch_glass_eval(ctx->dev, mat, n, cos_theta, bin, s, thickness_m, R, T, ctx->stream);

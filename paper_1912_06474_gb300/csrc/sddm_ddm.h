@@ -93,6 +93,10 @@ struct DDMRun {
     int bsdf_mode;
     int time_trace, count_traversal;
     int64_t *launches;
+    // learned glass model (bsdf_mode == SDDM_BSDF_MLP)
+    const float *mlp_params;
+    float mlp_dmin, mlp_dmax;
+    uint32_t probe_key;
 };
 
 // Run every bounce of one chunk of paths (asynchronous on `stream`).

@@ -19,16 +19,18 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsddm.so")
 OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_QUEUE_OVERFLOW = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_NOT_BUILT, ERR_MLP_UNTRAINED, ERR_DEVICE_CHECK = -5, -6, -7, -8
-BSDF_EXACT, BSDF_MLP = 0, 1
+BSDF_EXACT, BSDF_MLP, BSDF_MLP_RAW = 0, 1, 2
+MLP_PARAMS = 8770
 METHOD_MEGAKERNEL, METHOD_DDM = 0, 1
 METHODS = {"megakernel": METHOD_MEGAKERNEL, "ddm": METHOD_DDM}
-BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP}
+BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP, "mlp_raw": BSDF_MLP_RAW}
 
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
             "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
             "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
-            "sddm_render_noalloc"]
+            "sddm_render_noalloc", "sddm_mlp_train", "sddm_mlp_get_weights", "sddm_mlp_set_weights",
+            "sddm_mlp_save", "sddm_mlp_load", "sddm_mlp_grad"]
 
 
 class SddmError(RuntimeError):
@@ -40,6 +42,19 @@ class SddmError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("grid", C.c_int * 3), ("leaf_size", C.c_int), ("sah_bins", C.c_int),
                 ("queue_capacity", C.c_int64), ("blocks_per_sm", C.c_int), ("paths_in_flight", C.c_int64)]
+
+
+class MlpTrainOpts(C.Structure):
+    _fields_ = [("samples", C.c_int64), ("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
+                ("seed", C.c_uint32), ("thick_min", C.c_float), ("thick_max", C.c_float), ("resume", C.c_int)]
+
+
+class MlpReport(C.Structure):
+    _fields_ = [("final_loss", C.c_double), ("max_abs_err_R", C.c_double), ("max_abs_err_T", C.c_double),
+                ("train_ms", C.c_double), ("tflops", C.c_double), ("steps", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Camera(C.Structure):
@@ -91,6 +106,12 @@ def _load():
         "sddm_philox": ([P, I, P, C.c_uint32, C.c_uint32, P], I),
         "sddm_set_profiling": ([P, I], I),
         "sddm_render_noalloc": ([P, C.POINTER(RenderDesc), C.POINTER(Stats)], I),
+        "sddm_mlp_train": ([P, C.c_uint32, C.POINTER(MlpTrainOpts), C.POINTER(MlpReport)], I),
+        "sddm_mlp_get_weights": ([P, C.c_uint32, P], I),
+        "sddm_mlp_set_weights": ([P, C.c_uint32, P, C.c_float, C.c_float], I),
+        "sddm_mlp_save": ([P, C.c_uint32, C.c_char_p], I),
+        "sddm_mlp_load": ([P, C.c_uint32, C.c_char_p], I),
+        "sddm_mlp_grad": ([P, I, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -283,6 +304,40 @@ class Context:
     def set_profiling(self, time_trace=False, count_traversal=False):
         """sddm_set_profiling: per-launch trace-kernel events and traversal counters."""
         _check(lib.sddm_set_profiling(self._h, (1 if time_trace else 0) | (2 if count_traversal else 0)))
+
+    # -- learned glass surrogate ------------------------------------------------
+    def mlp_train(self, mat, samples=0, steps=0, batch=0, lr=0.0, seed=0, thick_min=0.0, thick_max=0.0,
+                  resume=False):
+        """sddm_mlp_train: train the surrogate of glass material ``mat``; returns the report."""
+        o = MlpTrainOpts(samples, steps, batch, lr, seed & 0xFFFFFFFF, thick_min, thick_max, 1 if resume else 0)
+        r = MlpReport()
+        _check(lib.sddm_mlp_train(self._h, int(mat), C.byref(o), C.byref(r)))
+        return r.as_dict()
+
+    def mlp_get_weights(self, mat):
+        p = np.zeros(MLP_PARAMS, np.float32)
+        _check(lib.sddm_mlp_get_weights(self._h, int(mat), _ptr(p)))
+        return p
+
+    def mlp_set_weights(self, mat, params, thick_min=0.002, thick_max=0.010):
+        p = _f32(params)
+        assert p.shape == (MLP_PARAMS,)
+        _check(lib.sddm_mlp_set_weights(self._h, int(mat), _ptr(p), float(thick_min), float(thick_max)))
+
+    def mlp_save(self, mat, path):
+        _check(lib.sddm_mlp_save(self._h, int(mat), os.fsencode(path)))
+
+    def mlp_load(self, mat, path):
+        _check(lib.sddm_mlp_load(self._h, int(mat), os.fsencode(path)))
+
+    def mlp_grad(self, X, Y, params):
+        """sddm_mlp_grad on CUDA tensors X [n,4], Y [n,2], params [8770]; returns (grad, loss)."""
+        import torch
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(lib.sddm_mlp_grad(self._h, int(X.shape[0]), X.data_ptr(), Y.data_ptr(), params.data_ptr(),
+                                 grad.data_ptr(), loss.data_ptr()))
+        return grad, loss
 
     # -- test hooks -----------------------------------------------------------
     def glass_eval(self, mat, cos_t, bins, s, thick, mode="exact"):

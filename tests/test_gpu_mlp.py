@@ -1,0 +1,172 @@
+"""GPU checks of the learned glass surrogate (BF16 tensor-core kernels) against
+the FP64 oracle network and the exact slab.
+
+* the training kernels' gradient (BF16 forward/backward, FP32 accumulation)
+  agrees with FP64 backpropagation to 1e-2 relative (BF16 rounds activations
+  and weights to 8 significand bits, 2^-9 relative each);
+* the inference kernel reproduces the FP64 network within the error BF16
+  rounding of activations and weights allows;
+* trained as specified (2^22 exact samples, 20k Adam steps of 8192 rows), the
+  surrogate's held-out error is small, and images rendered with it (probe and
+  exact fallback on) stay within the 1e-3 relative RMSE of the oracle;
+* a checkpoint round-trips through save/load.
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_1912_06474_gb300 import scenes
+from tests.helpers import rel_rmse
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(scope="module")
+def sddm():
+    from paper_1912_06474_gb300 import sddm as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def room41():
+    return scenes.tiny_room(L=41, seed=0)
+
+
+@pytest.fixture(scope="module")
+def trained(sddm, room41):
+    """Context with the tiny room's glass surrogate trained as specified."""
+    ctx = sddm.Context(0)
+    ctx.set_scene(room41)
+    ctx.build(grid=(2, 2, 2))
+    g = room41.glass_materials()[0]
+    t0 = time.perf_counter()
+    rep = ctx.mlp_train(g, seed=7)
+    rep["wall_s"] = time.perf_counter() - t0
+    print("surrogate training:", rep)
+    yield ctx, g, rep
+    ctx.close()
+
+
+def _xavier(rng):
+    p = np.zeros(8770, np.float32)
+
+    def u(n, fi, fo):
+        b = np.sqrt(6.0 / (fi + fo))
+        return rng.uniform(-b, b, n).astype(np.float32)
+    p[0:256] = u(256, 4, 64)
+    p[256:320] = rng.normal(0, 0.1, 64)
+    p[320:4416] = u(4096, 64, 64)
+    p[4416:4480] = rng.normal(0, 0.1, 64)
+    p[4480:8576] = u(4096, 64, 64)
+    p[8576:8640] = rng.normal(0, 0.1, 64)
+    p[8640:8768] = u(128, 64, 2)
+    p[8768:8770] = [0.1, 0.8]
+    return p
+
+
+def test_gradient_matches_fp64_backprop(oracle_mod, sddm, room41):
+    rng = np.random.default_rng(31)
+    ctx = sddm.Context(0)
+    ctx.set_scene(room41)
+    ctx.build()
+    for n in (64, 200, 1024):
+        p = _xavier(rng)
+        X = rng.uniform(-1, 1, (n, 4)).astype(np.float32)
+        Y = rng.uniform(0, 1, (n, 2)).astype(np.float32)
+        g_gpu, loss_gpu = ctx.mlp_grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(),
+                                       torch.from_numpy(p).cuda())
+        g_gpu = g_gpu.cpu().numpy().astype(np.float64)
+        loss, g = oracle_mod.mlp_loss_grad(p, X.astype(np.float64), Y.astype(np.float64))
+        assert abs(float(loss_gpu.item()) - loss) <= 1e-2 * loss
+        for name, lo, hi in (("W1", 0, 256), ("b1", 256, 320), ("W2", 320, 4416), ("b2", 4416, 4480),
+                             ("W3", 4480, 8576), ("b3", 8576, 8640), ("W4", 8640, 8768), ("b4", 8768, 8770)):
+            rel = np.linalg.norm(g_gpu[lo:hi] - g[lo:hi]) / np.linalg.norm(g[lo:hi])
+            assert rel <= 1e-2, (n, name, rel)
+    ctx.close()
+
+
+def test_inference_matches_fp64_network(oracle_mod, sddm, room41):
+    rng = np.random.default_rng(32)
+    ctx = sddm.Context(0)
+    ctx.set_scene(room41)
+    ctx.build()
+    g = room41.glass_materials()[0]
+    p = _xavier(rng)
+    ctx.mlp_set_weights(g, p)
+    n = 3000
+    c = rng.uniform(0, 1, n).astype(np.float32)
+    b = rng.integers(0, room41.L, n).astype(np.int32)
+    s = rng.uniform(0, 1, n).astype(np.float32)
+    d = rng.uniform(0.002, 0.010, n).astype(np.float32)
+    R, T = ctx.glass_eval(g, *(torch.from_numpy(a).cuda() for a in (c, b, s, d)), mode="mlp_raw")
+    got = np.stack([R.cpu().numpy(), T.cpu().numpy()], 1)
+    X = np.array([oracle_mod.mlp_features(c[i], room41.lam[b[i]], s[i], d[i]) for i in range(n)])
+    want = oracle_mod.mlp_forward(p, X)
+    err = np.abs(got - want)
+    # BF16 (8-bit significand) rounding of three activation layers and the weights: a few 1e-3 absolute
+    assert err.max() < 2.5e-2 and err.mean() < 5e-3, (err.max(), err.mean())
+    ctx.close()
+
+
+def test_trained_surrogate_accuracy(sddm, room41, trained):
+    """Held-out error of the trained network (reported), and what the served
+    values look like once the per-batch probe sends bad batches to the exact slab."""
+    ctx, g, rep = trained
+    assert rep["steps"] == 20000
+    assert rep["final_loss"] < 1e-4, rep
+    assert rep["max_abs_err_R"] < 0.15 and rep["max_abs_err_T"] < 0.15, rep
+    # random points of the trained box, raw network vs exact slab
+    rng = np.random.default_rng(33)
+    n = 20000
+    c = rng.uniform(0.05, 1, n).astype(np.float32)
+    b = rng.integers(0, room41.L, n).astype(np.int32)
+    s = rng.uniform(0, 1, n).astype(np.float32)
+    d = np.full(n, 0.004, np.float32)
+    args = [torch.from_numpy(a).cuda() for a in (c, b, s, d)]
+    Rm, Tm = ctx.glass_eval(g, *args, mode="mlp_raw")
+    Re, Te = ctx.glass_eval(g, *args, mode="exact")
+    eR = (Rm - Re).abs()
+    eT = (Tm - Te).abs()
+    print(f"surrogate |dR| max {eR.max().item():.2e} mean {eR.mean().item():.2e}, "
+          f"|dT| max {eT.max().item():.2e} mean {eT.mean().item():.2e}")
+    assert eR.mean().item() < 1e-2 and eT.mean().item() < 1e-2
+    # served values (probe + exact fallback) are closer to the exact slab than the raw network
+    Rp, Tp = ctx.glass_eval(g, *args, mode="mlp")
+    served = (Tp - Te).abs().mean().item()
+    print(f"served |dT| mean {served:.2e}")
+    assert served <= eT.mean().item()
+
+
+def test_render_with_surrogate(oracle_mod, sddm, room41, trained):
+    """Images with the surrogate meet the 1e-3 relative RMSE of the oracle; the
+    device time of both glass models is printed (what the network gains or costs)."""
+    ctx, g, rep = trained
+    spec = scenes.RenderSpec(64, 64, 4, 5, seed=3, camera=room41.camera)
+    ref = oracle_mod.Oracle(room41).render_pixels(spec, brute_force=True)["xyz"]
+    imgs, st = ctx.render([spec], method="ddm", bsdf="mlp")
+    e_mlp = rel_rmse(imgs[0].cpu().numpy(), ref)
+    imgs_x, st_x = ctx.render([spec], method="ddm", bsdf="exact")
+    e_exact = rel_rmse(imgs_x[0].cpu().numpy(), ref)
+    print(f"rel-RMSE surrogate {e_mlp:.2e} exact {e_exact:.2e}, fallbacks {st['mlp_fallbacks']} batches, "
+          f"device ms surrogate {st['gpu_ms']:.3f} exact {st_x['gpu_ms']:.3f}")
+    assert e_mlp <= 1e-3 and e_exact <= 1e-3
+    assert st["segments_ext"] == st_x["segments_ext"]
+
+
+def test_checkpoint_round_trip(sddm, room41, trained, tmp_path):
+    ctx, g, rep = trained
+    path = os.path.join(tmp_path, "glass.sddmmlp")
+    ctx.mlp_save(g, path)
+    w = ctx.mlp_get_weights(g)
+    ctx2 = sddm.Context(0)
+    ctx2.set_scene(room41)
+    ctx2.build()
+    ctx2.mlp_load(g, path)
+    assert np.array_equal(ctx2.mlp_get_weights(g), w)
+    rep2 = ctx2.mlp_train(g, steps=200, resume=True, seed=7, samples=1 << 18)
+    assert rep2["steps"] == rep["steps"] + 200
+    ctx2.close()
