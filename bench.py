@@ -217,10 +217,22 @@ def run(args):
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    # the same steps replayed as a CUDA graph (the library's default launch path)
+    ctx.set_profiling()
+    for _ in range(3):
+        ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
+    gms, gsegs = 0.0, 0
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        st = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
+        ev[k][1].record(stream)
+        gsegs += st["segments_ext"] + st["segments_shadow"]
+    torch.cuda.synchronize()
+    gms = sum(a.elapsed_time(b) for a, b in ev)
     # end to end through the host-buffer entry point
     host = torch.empty((spec.height, spec.width, 3), dtype=torch.float32).pin_memory()
     e2e_ms, e2e_segs = 0.0, 0
-    ctx.set_profiling()
     for k in range(max(1, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
@@ -274,6 +286,7 @@ def run(args):
                      "trace_launches_per_step": trace_launches // args.steps,
                      "nodes_per_visit": round(cst["node_visits"] / max(visits, 1), 2),
                      "tris_per_visit": round(cst["tri_tests"] / max(visits, 1), 2)},
+        "value_graph_replay": round(gsegs / (gms / 1e3) / 1e6, 3) if gms > 0 else None,
         "segments_per_step": segs // (args.steps * world), "build_s": round(build_s, 3), "clocks": clk,
         "mlp_fallback_batches_per_step": st.get("mlp_fallbacks", 0) if args.bsdf == "mlp" else None,
     }

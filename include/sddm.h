@@ -112,7 +112,8 @@ typedef struct {
 /* Profiling switches (sddm_set_profiling), off by default. */
 enum {
     SDDM_PROFILE_TIME_TRACE = 1,        /* CUDA events around every trace-kernel launch */
-    SDDM_PROFILE_COUNT_TRAVERSAL = 2    /* count nodes, triangle tests and ray visits */
+    SDDM_PROFILE_COUNT_TRAVERSAL = 2,   /* count nodes, triangle tests and ray visits */
+    SDDM_PROFILE_EAGER = 4              /* launch every kernel from the host (no CUDA graph replay) */
 };
 
 /* ---------------------------------------------------------------- context */
@@ -268,7 +269,10 @@ int sddm_mlp_grad(sddm_ctx *ctx, int n, const float *X, const float *Y, const fl
 
 /* Enable the SDDM_PROFILE_* measurements of later sddm_render calls
  * (0 = off). Counting uses a separately compiled trace kernel, so the timed
- * kernel is never the counting one within a call. */
+ * kernel is never the counting one within a call. By default the launch
+ * sequence of a render is captured into a CUDA graph the second time the same
+ * render shapes are seen (same sizes, depth, method, build) and replayed from
+ * then on; any profiling flag, or SDDM_PROFILE_EAGER, launches eagerly. */
 int sddm_set_profiling(sddm_ctx *ctx, int flags);
 
 /* ---------------------------------------------------------- test hooks */

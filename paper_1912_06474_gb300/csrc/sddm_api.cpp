@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <thread>
@@ -110,6 +111,25 @@ struct sddm_ctx {
     std::vector<std::unique_ptr<MlpNet>> nets;
     std::vector<int> net_of_mat;     // per material, -1 = none
     DevBuf mlp_grad_cta, mlp_loss_cta, mlp_scalar, mlp_X, mlp_Y;
+    // CUDA graphs of the render launch sequence, keyed by everything that is
+    // baked into kernel parameters (sizes, buffer addresses, build)
+    int64_t build_id = 0;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t hand0 = nullptr, hand1 = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec;
+        int64_t launches;   // kernels in the captured sequence
+        int events_used;    // trace-timing event records captured with it
+    };
+    std::map<std::string, Graph> graphs;
+    std::map<std::string, int> seen;
+    bool graphs_enabled = true;
+    ~sddm_ctx() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+        if (gstream) cudaStreamDestroy(gstream);
+        if (hand0) cudaEventDestroy(hand0);
+        if (hand1) cudaEventDestroy(hand1);
+    }
 };
 
 extern "C" {
@@ -136,8 +156,11 @@ int sddm_create(sddm_ctx **out, int device, void *stream) {
     c->device = device;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     c->sm_count = prop.multiProcessorCount;
-    if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess)
-        return cuda_fail(e, "sddm_create: cudaEventCreate");
+    if ((e = cudaEventCreate(&c->ev0)) != cudaSuccess || (e = cudaEventCreate(&c->ev1)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->hand0, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->hand1, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "sddm_create: events and graph stream");
     *out = c.release();
     return SDDM_OK;
 }
@@ -455,6 +478,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     g.root = ctx->d_cell_root.as<int>();
     ctx->opts = o;
     ctx->built = true;
+    ++ctx->build_id;
     return SDDM_OK;
 }
 
@@ -643,88 +667,142 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
     int64_t launches = 0;
     const int time_trace = (ctx->profile & SDDM_PROFILE_TIME_TRACE) != 0;
     const int count_trav = (ctx->profile & SDDM_PROFILE_COUNT_TRAVERSAL) != 0;
-    int64_t path0 = 0, pix0 = 0;
-    int rr = 0;   // render of pix0
-    while (path0 < paths) {
-        // extend the chunk pixel-row by pixel-row within renders
-        int64_t path1 = path0, pix1 = pix0;
-        int r = rr;
-        while (r < n) {
-            const RenderInfo &ri = info[r];
-            int64_t render_pix_end = ri.pixel_begin + (int64_t)ri.width * ri.height;
-            int64_t room = (cap - (path1 - path0)) / ri.spp;
-            if (room <= 0) break;
-            int64_t take = std::min(room, render_pix_end - pix1);
-            pix1 += take;
-            path1 += take * ri.spp;
-            if (pix1 == render_pix_end) ++r; else break;
-        }
-        const int64_t np = path1 - path0;
-        if ((e = ctx->d_samples.ensure((size_t)np * 3 * sizeof(float))) ||
-            (any_aov && (e = ctx->d_first.ensure((size_t)np * sizeof(int32_t)))))
-            return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render: scratch allocation failed")
-                                                  : cuda_fail(e, "sddm_render: scratch");
-        if (d[0].method == SDDM_METHOD_MEGAKERNEL) {
-            MegaArgs a;
-            a.sc = ctx->dev;
-            a.rb = rb;
-            a.path_begin = path0;
-            a.path_count = np;
-            a.sample_xyz = ctx->d_samples.as<float>();
-            a.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
-            a.counters = ctx->d_counters.as<unsigned long long>();
-            a.error_flag = ctx->d_err.as<int>();
-            a.count_traversal = count_trav;
-            cudaEvent_t t0 = nullptr, t1 = nullptr;
-            if (time_trace) {
-                if ((e = ctx->ddm_buf.event_pair(t0, t1)) || (e = cudaEventRecord(t0, s)))
-                    return cuda_fail(e, "sddm_render: events");
+    // Every kernel and memset of the call, on stream `ls` (eager, or captured into a graph).
+    auto launch_all = [&](cudaStream_t ls) -> int {
+        cudaStream_t s = ls;
+        int64_t path0 = 0, pix0 = 0;
+        int rr = 0;   // render of pix0
+        while (path0 < paths) {
+            // extend the chunk pixel-row by pixel-row within renders
+            int64_t path1 = path0, pix1 = pix0;
+            int r = rr;
+            while (r < n) {
+                const RenderInfo &ri = info[r];
+                int64_t render_pix_end = ri.pixel_begin + (int64_t)ri.width * ri.height;
+                int64_t room = (cap - (path1 - path0)) / ri.spp;
+                if (room <= 0) break;
+                int64_t take = std::min(room, render_pix_end - pix1);
+                pix1 += take;
+                path1 += take * ri.spp;
+                if (pix1 == render_pix_end) ++r; else break;
             }
-            if ((e = launch_megakernel(a, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: megakernel launch");
-            if (time_trace && (e = cudaEventRecord(t1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
+            const int64_t np = path1 - path0;
+            if ((e = ctx->d_samples.ensure((size_t)np * 3 * sizeof(float))) ||
+                (any_aov && (e = ctx->d_first.ensure((size_t)np * sizeof(int32_t)))))
+                return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render: scratch allocation failed")
+                                                      : cuda_fail(e, "sddm_render: scratch");
+            if (d[0].method == SDDM_METHOD_MEGAKERNEL) {
+                MegaArgs a;
+                a.sc = ctx->dev;
+                a.rb = rb;
+                a.path_begin = path0;
+                a.path_count = np;
+                a.sample_xyz = ctx->d_samples.as<float>();
+                a.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+                a.counters = ctx->d_counters.as<unsigned long long>();
+                a.error_flag = ctx->d_err.as<int>();
+                a.count_traversal = count_trav;
+                cudaEvent_t t0 = nullptr, t1 = nullptr;
+                if (time_trace) {
+                    if ((e = ctx->ddm_buf.event_pair(t0, t1)) || (e = cudaEventRecord(t0, s)))
+                        return cuda_fail(e, "sddm_render: events");
+                }
+                if ((e = launch_megakernel(a, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: megakernel launch");
+                if (time_trace && (e = cudaEventRecord(t1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
+                launches += 1;
+            } else {
+                DDMRun run;
+                run.sc = ctx->dev;
+                run.g = ctx->ddm;
+                run.rb = rb;
+                run.path_begin = path0;
+                run.path_count = np;
+                run.max_depth = 1;
+                for (int q = 0; q < n; ++q) run.max_depth = std::max(run.max_depth, d[q].max_depth);
+                run.sample_xyz = ctx->d_samples.as<float>();
+                run.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+                run.counters = ctx->d_counters.as<unsigned long long>();
+                run.error_flag = ctx->d_err.as<int>();
+                run.sm_count = ctx->sm_count;
+                run.blocks_per_sm = ctx->opts.blocks_per_sm;
+                run.queue_capacity = ctx->opts.queue_capacity;
+                run.bsdf_mode = d[0].bsdf_mode;
+                run.time_trace = time_trace;
+                run.count_traversal = count_trav;
+                run.launches = &launches;
+                run.mlp_params = mlp_params;
+                run.mlp_dmin = mlp_dmin;
+                run.mlp_dmax = mlp_dmax;
+                run.probe_key = d[0].seed ^ 0x9e3779b9u;
+                int rc2 = ddm_trace_chunk(run, ctx->ddm_buf, s);
+                if (rc2 != SDDM_OK) return rc2;
+            }
+            ReduceArgs ra;
+            ra.rb = rb;
+            ra.path_begin = path0;
+            ra.sample_xyz = ctx->d_samples.as<float>();
+            ra.xyz_out = ctx->d_out_tab.as<float *>();
+            ra.aov_xyz = ctx->d_aov_xyz_tab.as<float *>();
+            ra.aov_prim = ctx->d_aov_prim_tab.as<int32_t *>();
+            ra.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
+            if ((e = launch_reduce_pixels(ra, pix0, pix1 - pix0, s)) != cudaSuccess)
+                return cuda_fail(e, "sddm_render: reduce launch");
             launches += 1;
-        } else {
-            DDMRun run;
-            run.sc = ctx->dev;
-            run.g = ctx->ddm;
-            run.rb = rb;
-            run.path_begin = path0;
-            run.path_count = np;
-            run.max_depth = 1;
-            for (int q = 0; q < n; ++q) run.max_depth = std::max(run.max_depth, d[q].max_depth);
-            run.sample_xyz = ctx->d_samples.as<float>();
-            run.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
-            run.counters = ctx->d_counters.as<unsigned long long>();
-            run.error_flag = ctx->d_err.as<int>();
-            run.sm_count = ctx->sm_count;
-            run.blocks_per_sm = ctx->opts.blocks_per_sm;
-            run.queue_capacity = ctx->opts.queue_capacity;
-            run.bsdf_mode = d[0].bsdf_mode;
-            run.time_trace = time_trace;
-            run.count_traversal = count_trav;
-            run.launches = &launches;
-            run.mlp_params = mlp_params;
-            run.mlp_dmin = mlp_dmin;
-            run.mlp_dmax = mlp_dmax;
-            run.probe_key = d[0].seed ^ 0x9e3779b9u;
-            int rc2 = ddm_trace_chunk(run, ctx->ddm_buf, s);
-            if (rc2 != SDDM_OK) return rc2;
+            path0 = path1;
+            pix0 = pix1;
+            rr = r;
+            while (rr < n && pix0 >= info[rr].pixel_begin + (int64_t)info[rr].width * info[rr].height) ++rr;
         }
-        ReduceArgs ra;
-        ra.rb = rb;
-        ra.path_begin = path0;
-        ra.sample_xyz = ctx->d_samples.as<float>();
-        ra.xyz_out = ctx->d_out_tab.as<float *>();
-        ra.aov_xyz = ctx->d_aov_xyz_tab.as<float *>();
-        ra.aov_prim = ctx->d_aov_prim_tab.as<int32_t *>();
-        ra.first_prim = any_aov ? ctx->d_first.as<int32_t>() : nullptr;
-        if ((e = launch_reduce_pixels(ra, pix0, pix1 - pix0, s)) != cudaSuccess)
-            return cuda_fail(e, "sddm_render: reduce launch");
-        launches += 1;
-        path0 = path1;
-        pix0 = pix1;
-        rr = r;
-        while (rr < n && pix0 >= info[rr].pixel_begin + (int64_t)info[rr].width * info[rr].height) ++rr;
+        return SDDM_OK;
+    };
+    const bool graphable = ctx->graphs_enabled && !count_trav && !time_trace;
+    std::string key;
+    if (graphable) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "%lld|%d|%d|%d|%d|%lld|%d|%u|%d|%p|%p|%p|%p|%p|%p", (long long)ctx->build_id,
+                      n, d[0].method, d[0].bsdf_mode, (int)any_aov, (long long)ctx->opts.paths_in_flight,
+                      ctx->opts.blocks_per_sm, d[0].seed, time_trace, ctx->d_samples.p, ctx->d_first.p,
+                      ctx->ddm_buf.mem, ctx->d_info.p, (const void *)mlp_params, ctx->d_counters.p);
+        key = buf;
+        for (int r = 0; r < n; ++r) {
+            std::snprintf(buf, sizeof buf, "|%d,%d,%d,%d", d[r].width, d[r].height, d[r].spp, d[r].max_depth);
+            key += buf;
+        }
+    }
+    auto it = graphable ? ctx->graphs.find(key) : ctx->graphs.end();
+    if (graphable && (it != ctx->graphs.end() || ctx->seen[key] > 0)) {
+        if ((e = cudaEventRecord(ctx->hand0, s)) || (e = cudaStreamWaitEvent(ctx->gstream, ctx->hand0, 0)))
+            return cuda_fail(e, "sddm_render: stream hand-off");
+        if (it == ctx->graphs.end()) {
+            if (ctx->graphs.size() >= 8) {
+                for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+                ctx->graphs.clear();
+            }
+            cudaGraph_t graph = nullptr;
+            if ((e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal)))
+                return cuda_fail(e, "sddm_render: begin capture");
+            int rc2 = launch_all(ctx->gstream);
+            cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
+            if (rc2 != SDDM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc2;
+            }
+            if (ce) return cuda_fail(ce, "sddm_render: end capture");
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce) return cuda_fail(ce, "sddm_render: graph instantiate");
+            it = ctx->graphs.emplace(key, sddm_ctx::Graph{exec, launches, ctx->ddm_buf.events_used}).first;
+        }
+        launches = it->second.launches;
+        ctx->ddm_buf.events_used = it->second.events_used;
+        if ((e = cudaGraphLaunch(it->second.exec, ctx->gstream)) || (e = cudaEventRecord(ctx->hand1, ctx->gstream)) ||
+            (e = cudaStreamWaitEvent(s, ctx->hand1, 0)))
+            return cuda_fail(e, "sddm_render: graph launch");
+    } else {
+        int rc2 = launch_all(s);
+        if (rc2 != SDDM_OK) return rc2;
+        if (graphable) ctx->seen[key] = 1;
     }
     if ((e = cudaEventRecord(ctx->ev1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: event");
     unsigned long long cnt[8];
@@ -1107,9 +1185,10 @@ int sddm_mlp_grad(sddm_ctx *ctx, int n, const float *X, const float *Y, const fl
 
 int sddm_set_profiling(sddm_ctx *ctx, int flags) {
     if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: ctx is NULL");
-    if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL))
+    if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL | SDDM_PROFILE_EAGER))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: unknown flag");
     ctx->profile = flags;
+    ctx->graphs_enabled = flags == 0;   // events inside a replayed graph give no elapsed times
     return SDDM_OK;
 }
 

@@ -301,9 +301,11 @@ class Context:
                     queue_capacity=best.queue_capacity, blocks_per_sm=best.blocks_per_sm,
                     paths_in_flight=best.paths_in_flight)
 
-    def set_profiling(self, time_trace=False, count_traversal=False):
-        """sddm_set_profiling: per-launch trace-kernel events and traversal counters."""
-        _check(lib.sddm_set_profiling(self._h, (1 if time_trace else 0) | (2 if count_traversal else 0)))
+    def set_profiling(self, time_trace=False, count_traversal=False, eager=False):
+        """sddm_set_profiling: per-launch trace-kernel events, traversal counters,
+        or eager launches (all three disable CUDA graph replay)."""
+        _check(lib.sddm_set_profiling(self._h, (1 if time_trace else 0) | (2 if count_traversal else 0)
+                                      | (4 if eager else 0)))
 
     # -- learned glass surrogate ------------------------------------------------
     def mlp_train(self, mat, samples=0, steps=0, batch=0, lr=0.0, seed=0, thick_min=0.0, thick_max=0.0,

@@ -206,3 +206,29 @@ def test_invalid_inputs_fail_cleanly(sddm, tiny16):
     imgs, st = ctx.render([spec])
     assert torch.isfinite(imgs[0]).all()
     ctx.close()
+
+
+def test_graph_replay_matches_eager(sddm, tiny16):
+    """From the third call with the same shapes the launch sequence is a replayed
+    CUDA graph; the per-call tables (camera, coloration state) still apply."""
+    import copy
+    ctx = sddm.Context(0)
+    ctx.set_scene(tiny16)
+    ctx.build(grid=(2, 2, 2))
+    g = tiny16.glass_materials()[0]
+    spec = scenes.RenderSpec(48, 32, 3, 4, seed=9, camera=tiny16.camera, glass_s={g: 0.2})
+    outs = [ctx.render([spec], method="ddm")[0][0].cpu().numpy() for _ in range(4)]
+    ctx.set_profiling(eager=True)
+    eager = ctx.render([spec], method="ddm")[0][0].cpu().numpy()
+    for o in outs:
+        assert np.array_equal(o, eager)
+    spec2 = copy.deepcopy(spec)
+    spec2.camera = scenes.Camera((0.7, 1.8, 1.4), (2.5, 2.2, 1.2), vfov_deg=55.0)
+    spec2.glass_s = {g: 0.9}
+    eager2 = ctx.render([spec2], method="ddm")[0][0].cpu().numpy()
+    ctx.set_profiling()
+    for _ in range(3):
+        replay2 = ctx.render([spec2], method="ddm")[0][0].cpu().numpy()
+    assert np.array_equal(replay2, eager2)
+    assert not np.array_equal(eager2, eager)
+    ctx.close()
