@@ -265,32 +265,24 @@ def quad_mesh(p0, p1, p2, p3):
 def uv_sphere(center, radius, n_lat, n_lon):
     """UV sphere with 2*n_lon*(n_lat-1) triangles, outward CCW."""
     cx, cy, cz = center
-    verts = [[cx, cy, cz + radius]]
-    for i in range(1, n_lat):
-        th = math.pi * i / n_lat
-        for j in range(n_lon):
-            ph = 2.0 * math.pi * j / n_lon
-            verts.append([cx + radius * math.sin(th) * math.cos(ph),
-                          cy + radius * math.sin(th) * math.sin(ph),
-                          cz + radius * math.cos(th)])
-    verts.append([cx, cy, cz - radius])
-    V = np.array(verts, dtype=np.float64)
-    south = len(verts) - 1
+    th = math.pi * np.arange(1, n_lat) / n_lat
+    ph = 2.0 * math.pi * np.arange(n_lon) / n_lon
+    st, ct = np.sin(th)[:, None], np.cos(th)[:, None]
+    ring = np.stack([cx + radius * st * np.cos(ph)[None, :], cy + radius * st * np.sin(ph)[None, :],
+                     np.broadcast_to(cz + radius * ct, (n_lat - 1, n_lon))], -1).reshape(-1, 3)
+    V = np.concatenate([[[cx, cy, cz + radius]], ring, [[cx, cy, cz - radius]]]).astype(np.float64)
+    south = len(V) - 1
+    j = np.arange(n_lon)
+    jn = (j + 1) % n_lon
 
-    def ring(i, j):
-        return 1 + (i - 1) * n_lon + (j % n_lon)
-    F = []
-    for j in range(n_lon):
-        F.append([0, ring(1, j), ring(1, j + 1)])
-    for i in range(1, n_lat - 1):
-        for j in range(n_lon):
-            a, b = ring(i, j), ring(i, j + 1)
-            c, d = ring(i + 1, j), ring(i + 1, j + 1)
-            F.append([a, c, d])
-            F.append([a, d, b])
-    for j in range(n_lon):
-        F.append([south, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)])
-    return V, np.array(F, dtype=np.int64)
+    def idx(i, jj):
+        return 1 + (i - 1) * n_lon + jj
+    top = np.stack([np.zeros(n_lon, np.int64), idx(1, j), idx(1, jn)], 1)
+    i = np.arange(1, n_lat - 1)[:, None]
+    a, b, c, d = idx(i, j[None]), idx(i, jn[None]), idx(i + 1, j[None]), idx(i + 1, jn[None])
+    mid = np.stack([np.stack([a, c, d], -1), np.stack([a, d, b], -1)], 2).reshape(-1, 3)
+    bot = np.stack([np.full(n_lon, south, np.int64), idx(n_lat - 1, jn), idx(n_lat - 1, j)], 1)
+    return V, np.concatenate([top, mid, bot]).astype(np.int64)
 
 
 def extrusion_mesh(rng, center, radius, height, n_sides, n_rings):
@@ -298,28 +290,21 @@ def extrusion_mesh(rng, center, radius, height, n_sides, n_rings):
     cx, cy, z0 = center
     ang = np.sort(rng.uniform(0, 2 * math.pi, n_sides))
     rad = radius * rng.uniform(0.5, 1.0, n_sides)
-    ring_xy = np.stack([cx + rad * np.cos(ang), cy + rad * np.sin(ang)], 1)
-    verts = []
-    for r in range(n_rings + 1):
-        z = z0 + height * r / n_rings
-        for k in range(n_sides):
-            verts.append([ring_xy[k, 0], ring_xy[k, 1], z])
-    bot = len(verts)
-    verts.append([cx, cy, z0])
-    top = len(verts)
-    verts.append([cx, cy, z0 + height])
-    F = []
-    for r in range(n_rings):
-        for k in range(n_sides):
-            a = r * n_sides + k
-            b = r * n_sides + (k + 1) % n_sides
-            c, d = a + n_sides, b + n_sides
-            F.append([a, b, d])
-            F.append([a, d, c])
-    for k in range(n_sides):
-        F.append([bot, (k + 1) % n_sides, k])
-        F.append([top, n_rings * n_sides + k, n_rings * n_sides + (k + 1) % n_sides])
-    return np.array(verts, dtype=np.float64), np.array(F, dtype=np.int64)
+    rx, ry = cx + rad * np.cos(ang), cy + rad * np.sin(ang)
+    z = z0 + height * np.arange(n_rings + 1) / n_rings
+    V = np.stack([np.broadcast_to(rx, (n_rings + 1, n_sides)), np.broadcast_to(ry, (n_rings + 1, n_sides)),
+                  np.broadcast_to(z[:, None], (n_rings + 1, n_sides))], -1).reshape(-1, 3)
+    bot, top = len(V), len(V) + 1
+    V = np.concatenate([V, [[cx, cy, z0], [cx, cy, z0 + height]]]).astype(np.float64)
+    k = np.arange(n_sides)
+    kn = (k + 1) % n_sides
+    r = np.arange(n_rings)[:, None]
+    a, b = r * n_sides + k[None], r * n_sides + kn[None]
+    c, d = a + n_sides, b + n_sides
+    side = np.stack([np.stack([a, b, d], -1), np.stack([a, d, c], -1)], 2).reshape(-1, 3)
+    caps = np.concatenate([np.stack([np.full(n_sides, bot), kn, k], 1),
+                           np.stack([np.full(n_sides, top), n_rings * n_sides + k, n_rings * n_sides + kn], 1)])
+    return V, np.concatenate([side, caps]).astype(np.int64)
 
 
 def _spectral_base(L):
@@ -435,7 +420,8 @@ def facade_room(L: int = 81, seed: int = 0, target_tris: int = 5_000_000,
                 n_panes: int = 8, light_scale: float = 10.0) -> Scene:
     """12x8x3 m room, seeded furniture meshes (5k-50k triangles each) up to
     ``target_tris`` triangles, 8 electrochromic panes on the x = 12 facade,
-    each with its own coloration state s ~ U[0, 1] and its own sun quad."""
+    each with its own coloration state s ~ U[0, 1] and its own sun quad, and
+    four ceiling lamps."""
     rng = np.random.default_rng(seed)
     lam, w, cmf = _spectral_base(L)
     mats: List[Material] = [
@@ -459,6 +445,8 @@ def facade_room(L: int = 81, seed: int = 0, target_tris: int = 5_000_000,
         glass_ids.append(len(mats) - 1)
     light_id = len(mats)
     mats.append(Material(EMITTER, Le=planck_normalised(lam, 5800.0, light_scale), name="sun"))
+    lamp_id = len(mats)
+    mats.append(Material(EMITTER, Le=planck_normalised(lam, 3000.0, 0.5 * light_scale), name="lamp"))
 
     mb = _MeshBuilder()
     V, F = box_mesh((0, 0, 0), (12, 8, 3), inward=True)
@@ -470,34 +458,40 @@ def facade_room(L: int = 81, seed: int = 0, target_tris: int = 5_000_000,
         mb.add(*box_mesh((11.9, yc - hw, 0.8), (11.906, yc + hw, 2.4)), glass_ids[i])
         mb.add(*quad_mesh((11.99, yc - hw + 0.05, 0.9), (11.99, yc - hw + 0.05, 2.3),
                           (11.99, yc + hw - 0.05, 2.3), (11.99, yc + hw - 0.05, 0.9)), light_id)
+    # four ceiling lamps
+    for lx in (4.0, 8.0):
+        for ly in (2.5, 5.5):
+            mb.add(*quad_mesh((lx - 0.4, ly - 0.4, 2.99), (lx - 0.4, ly + 0.4, 2.99), (lx + 0.4, ly + 0.4, 2.99),
+                              (lx + 0.4, ly - 0.4, 2.99)), lamp_id)
+    # furniture: finely tessellated objects, knee to chest height, x >= 3 m (the cameras stand nearer)
     n_now = sum(len(f) for f in mb.F)
     while n_now < target_tris:
         budget = int(rng.integers(5_000, 50_001))
         budget = min(budget, max(target_tris - n_now, 12))
         kind = int(rng.integers(3))
-        cx, cy = rng.uniform(0.5, 10.5), rng.uniform(1.0, 7.0)
-        if kind == 0 or budget < 200:        # cluster of boxes
+        cx, cy = rng.uniform(3.0, 10.5), rng.uniform(0.8, 7.2)
+        if kind == 0 or budget < 200:        # cluster of small boxes
             nb = max(1, budget // 12)
             for _ in range(nb):
-                s3 = rng.uniform(0.02, 0.3, 3)
-                p = (cx + rng.uniform(-0.8, 0.8), cy + rng.uniform(-0.8, 0.8), rng.uniform(0, 1.5))
+                s3 = rng.uniform(0.02, 0.15, 3)
+                p = (cx + rng.uniform(-0.4, 0.4), cy + rng.uniform(-0.4, 0.4), rng.uniform(0, 1.0))
                 mb.add(*box_mesh(p, (p[0] + s3[0], p[1] + s3[1], p[2] + s3[2])),
                        diffuse_ids[int(rng.integers(len(diffuse_ids)))])
             n_now += nb * 12
         elif kind == 1:                      # sphere
             n_lon = max(8, int(math.sqrt(budget / 2.0) * 1.4))
             n_lat = max(4, budget // (2 * n_lon) + 1)
-            r = rng.uniform(0.15, 0.7)
+            r = rng.uniform(0.1, 0.35)
             mat = metal_ids[int(rng.integers(len(metal_ids)))] if rng.uniform() < 0.3 else \
                 diffuse_ids[int(rng.integers(len(diffuse_ids)))]
-            V_, F_ = uv_sphere((cx, cy, rng.uniform(r, 2.9 - r)), r, n_lat, n_lon)
+            V_, F_ = uv_sphere((cx, cy, rng.uniform(r, 1.2)), r, n_lat, n_lon)
             mb.add(V_, F_, mat)
             n_now += len(F_)
         else:                                # extrusion
             n_sides = int(rng.integers(12, 64))
             n_rings = max(1, budget // (2 * n_sides))
-            V_, F_ = extrusion_mesh(rng, (cx, cy, 0.0), rng.uniform(0.2, 0.9),
-                                    rng.uniform(0.3, 2.5), n_sides, n_rings)
+            V_, F_ = extrusion_mesh(rng, (cx, cy, 0.0), rng.uniform(0.1, 0.4), rng.uniform(0.3, 1.4),
+                                    n_sides, n_rings)
             mb.add(V_, F_, diffuse_ids[int(rng.integers(len(diffuse_ids)))])
             n_now += len(F_)
     Vv, Ff, M, O = mb.arrays()
@@ -565,7 +559,7 @@ def facade_renders(scene: Scene, n_renders=16, width=1920, height=1080, spp=64, 
     rng = np.random.default_rng(seed + 1)
     out = []
     for r in range(n_renders):
-        pos = (rng.uniform(0.4, 3.0), rng.uniform(1.0, 7.0), rng.uniform(1.2, 2.0))
+        pos = (rng.uniform(0.4, 2.5), rng.uniform(1.0, 7.0), rng.uniform(1.2, 2.0))
         look = (11.0, rng.uniform(2.0, 6.0), rng.uniform(1.0, 1.8))
         out.append(RenderSpec(width, height, spp, max_depth, seed=seed, render_id=r,
                               camera=Camera(pos=pos, look=look, vfov_deg=75.0)))

@@ -1,0 +1,45 @@
+"""The large electrochromic facade room on the GPU: 5M triangles of seeded
+furniture meshes, 8 panes with their own coloration state, 81 bins at 5 nm,
+depth 8, traced by domain decomposition over 8 x 8 x 4 subdomains (whose BVH
+working set exceeds the 129 MB L2), checked on pixel subsets against the FP64
+oracle, and timed against the global-BVH megakernel.
+"""
+import time
+
+import pytest
+
+from paper_1912_06474_gb300 import scenes
+from tests.helpers import rel_rmse
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+def test_facade_room(oracle_mod):
+    from paper_1912_06474_gb300 import sddm
+    sc = scenes.facade_room(L=81, seed=0)
+    assert sc.n_tris >= 5_000_000 and len(sc.glass_materials()) == 8
+    ctx = sddm.Context(0)
+    ctx.set_scene(sc)
+    t0 = time.perf_counter()
+    ctx.build(grid=(8, 8, 4))
+    build_s = time.perf_counter() - t0
+    specs = scenes.facade_renders(sc, n_renders=2, width=480, height=270, spp=4, max_depth=8)
+    imgs, st = ctx.render(specs, method="ddm")
+    orc = oracle_mod.Oracle(sc)
+    for r, sp in enumerate(specs):
+        pix = scenes.pixel_subset(sp.width, sp.height, 768, seed=r)
+        ref = orc.render_pixels(sp, pix)["xyz"]
+        e = rel_rmse(imgs[r].cpu().numpy().reshape(-1, 3)[pix], ref)
+        print(f"facade render {r}: rel-RMSE {e:.2e}")
+        assert e <= 1e-3
+    big = scenes.facade_renders(sc, n_renders=1, width=1920, height=1080, spp=4, max_depth=8)
+    rates = {}
+    for method in ("ddm", "megakernel"):
+        ctx.render(big, method=method)
+        _, st = ctx.render(big, method=method)
+        rates[method] = (st["segments_ext"] + st["segments_shadow"]) / (st["gpu_ms"] * 1e3)
+    print(f"facade build {build_s:.1f} s; 1920x1080x4 spp, depth 8, L 81: DDM 8x8x4 {rates['ddm']:.0f} "
+          f"Mseg/s, megakernel {rates['megakernel']:.0f} Mseg/s")
+    ctx.close()
