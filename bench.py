@@ -261,14 +261,20 @@ def run(args):
     peak, peak_kind = _peaks()
     achieved = bytes_step / trace_s / 1e9 if trace_s > 0 else None
     traffic = None
-    try:
+    try:   # DRAM bytes per trace launch from an ncu capture, only while the kernel sources are unchanged
+        import hashlib
         with open(os.path.join(ROOT, "profiles", "trace_traffic.json")) as f:
             tt = json.load(f)
         ent = tt.get(f"{args.method}:{cfg['workload']}")
         if ent and ent.get("valid", False):
-            traffic = ent["dram_bytes_per_launch"]
+            m = hashlib.sha256()
+            for src in ent["sources"]:
+                with open(os.path.join(ROOT, src), "rb") as f:
+                    m.update(f.read())
+            if m.hexdigest()[:16] == ent["source_sha256_16"]:
+                traffic = ent["dram_bytes_per_launch"]
     except Exception:
-        pass
+        traffic = None
     h2d = 0   # render tables: a few hundred bytes, counted below from the descriptor layout
     h2d = 128 * 1 + 4 * len(scene.materials) + 3 * 8
     d2h = spec.width * spec.height * 3 * 4 + 64 + 16
