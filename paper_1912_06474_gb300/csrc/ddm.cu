@@ -62,8 +62,8 @@ struct KArgs {
     int32_t *first_prim;
     unsigned long long *counters;
     int *err;
-    // learned glass model: queries gathered per bounce, results [query][L] (R, T)
-    int use_mlp;
+    // glass queries gathered per bounce and evaluated (exact or learned) before shading
+    int use_queries;
     float4 *queries;
     unsigned long long *n_queries;
     int64_t q_cap;
@@ -290,10 +290,11 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
 // Persistent warps whose lanes are refilled one by one: a lane that finishes
 // its ray (hit, occlusion, or exit from the cell) takes the next ray of the
 // cell-sorted queue while the other lanes carry on, so a warp is not held by
-// its slowest ray. Traversal is a resumable state machine run for at most
-// kTraceSteps node or leaf visits between refills.
+// its slowest ray. Traversal is a resumable state machine; each round runs the
+// warp through interior nodes until every lane stands at a leaf (at most
+// kTraceSteps steps), then through the leaves, then refills.
 #ifndef SDDM_TRACE_STEPS
-#define SDDM_TRACE_STEPS 32
+#define SDDM_TRACE_STEPS 64   // interior steps per round at most
 #endif
 constexpr int kTraceSteps = SDDM_TRACE_STEPS;
 // Resident 128-thread blocks per SM the trace kernel is compiled for (register budget).
@@ -370,87 +371,85 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
         }
         if (__ballot_sync(full, idx >= 0) == 0) break;
 
-        // 2. a bounded number of traversal steps
+        // 2. one traversal round, while-while: an interior phase in which every
+        //    lane descends until it stands at a leaf (or its stack runs out),
+        //    then a leaf phase in which the lanes at a leaf test its triangles.
         bool fin = false;
-        if (idx >= 0) {
-            const bool shadow = (rfl & kRayShadow) != 0;
-            for (int step = 0; step < kTraceSteps; ++step) {
-                bool pop = false;
-                if (node >= 0) {
-                    if (COUNT) ++tc.nodes;
-                    const float4 n0 = __ldg(g.nodes + 4 * node + 0), n1 = __ldg(g.nodes + 4 * node + 1),
-                                 n2 = __ldg(g.nodes + 4 * node + 2), n3 = __ldg(g.nodes + 4 * node + 3);
-                    float ta, tb;
-                    bool ha, hb;
-                    child_boxes(ray, n0, n1, n2, tmin, tw, ta, tb, ha, hb);
-                    const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
-                    if (ha && hb) {
-                        const bool a_first = shadow || ta <= tb;
-                        if (sp < kStackSize) {
-                            stack[sp++] = a_first ? cb : ca;
-                        } else {
-                            atomicCAS(a.err, 0, 5);   // deeper than the builder allows
-                        }
-                        node = a_first ? ca : cb;
-                    } else if (ha) {
-                        node = ca;
-                    } else if (hb) {
-                        node = cb;
+        const bool live = idx >= 0;
+        const bool shadow = (rfl & kRayShadow) != 0;
+        for (int it = 0; it < kTraceSteps; ++it) {
+            const bool act = live && !fin && node >= 0;
+            if (!__any_sync(full, act)) break;
+            if (act) {
+                if (COUNT) ++tc.nodes;
+                const float4 n0 = __ldg(g.nodes + 4 * node + 0), n1 = __ldg(g.nodes + 4 * node + 1),
+                             n2 = __ldg(g.nodes + 4 * node + 2), n3 = __ldg(g.nodes + 4 * node + 3);
+                float ta, tb;
+                bool ha, hb;
+                child_boxes(ray, n0, n1, n2, tmin, tw, ta, tb, ha, hb);
+                const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+                if (ha && hb) {
+                    const bool a_first = shadow || ta <= tb;
+                    if (sp < kStackSize) {
+                        stack[sp++] = a_first ? cb : ca;
                     } else {
-                        pop = true;
+                        atomicCAS(a.err, 0, 5);   // deeper than the builder allows
                     }
+                    node = a_first ? ca : cb;
+                } else if (ha) {
+                    node = ca;
+                } else if (hb) {
+                    node = cb;
+                } else if (sp == 0) {
+                    fin = true;
                 } else {
-                    const int v = ~node;
-                    const int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
-                    for (int i = 0; i < count; ++i) {
-                        const float4 *tp = g.tris + 3 * (first + i);
-                        const float4 ta4 = __ldg(tp), tb4 = __ldg(tp + 1), tc4 = __ldg(tp + 2);
-                        const int id = __float_as_int(ta4.w);
-                        if (shadow) {
-                            if (id == excl) continue;
-                            if (COUNT) ++tc.tris;
-                            const V3 e1 = xyz(tb4), e2 = xyz(tc4);
-                            const float t = mt_intersect(ray, xyz(ta4), e1, e2);
-                            if (!(t > tmin && t <= tw)) continue;
-                            if (!(__float_as_uint(tc4.w) & kTriGlass)) {
-                                occ = true;
-                                break;
-                            }
-                            if (dot(ray.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
-                            const int ob = __float_as_int(tb4.w);
-                            bool seen = false;
-                            for (int k = 0; k < cr.n; ++k) seen |= cr.obj[k] == ob;
-                            if (seen) continue;
-                            if (cr.n >= kMaxCross) {
-                                occ = true;
-                                break;
-                            }
-                            cr.obj[cr.n] = ob;
-                            cr.tri[cr.n] = id;
-                            ++cr.n;
-                        } else {
-                            if (id == ep || (eo >= 0 && __float_as_int(tb4.w) == eo)) continue;
-                            if (COUNT) ++tc.tris;
-                            const float t = mt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
-                            if (t > tmin && (t < tw || (t == tw && (best < 0 || id < best)))) {
-                                tw = t;
-                                best = id;
-                            }
-                        }
-                    }
-                    if (occ) {
-                        fin = true;
-                        break;
-                    }
-                    pop = true;
-                }
-                if (pop) {
-                    if (sp == 0) {
-                        fin = true;
-                        break;
-                    }
                     node = stack[--sp];
                 }
+            }
+        }
+        if (live && !fin && node < 0) {
+            const int v = ~node;
+            const int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
+            for (int i = 0; i < count; ++i) {
+                const float4 *tp = g.tris + 3 * (first + i);
+                const float4 ta4 = __ldg(tp), tb4 = __ldg(tp + 1), tc4 = __ldg(tp + 2);
+                const int id = __float_as_int(ta4.w);
+                if (shadow) {
+                    if (id == excl) continue;
+                    if (COUNT) ++tc.tris;
+                    const V3 e1 = xyz(tb4), e2 = xyz(tc4);
+                    const float t = mt_intersect(ray, xyz(ta4), e1, e2);
+                    if (!(t > tmin && t <= tw)) continue;
+                    if (!(__float_as_uint(tc4.w) & kTriGlass)) {
+                        occ = true;
+                        break;
+                    }
+                    if (dot(ray.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
+                    const int ob = __float_as_int(tb4.w);
+                    bool seen = false;
+                    for (int k = 0; k < cr.n; ++k) seen |= cr.obj[k] == ob;
+                    if (seen) continue;
+                    if (cr.n >= kMaxCross) {
+                        occ = true;
+                        break;
+                    }
+                    cr.obj[cr.n] = ob;
+                    cr.tri[cr.n] = id;
+                    ++cr.n;
+                } else {
+                    if (id == ep || (eo >= 0 && __float_as_int(tb4.w) == eo)) continue;
+                    if (COUNT) ++tc.tris;
+                    const float t = mt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
+                    if (t > tmin && (t < tw || (t == tw && (best < 0 || id < best)))) {
+                        tw = t;
+                        best = id;
+                    }
+                }
+            }
+            if (occ || sp == 0) {
+                fin = true;
+            } else {
+                node = stack[--sp];
             }
         }
 
@@ -574,28 +573,24 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_shade(KArgs a) {
+// Spectral half of shading: resolve the previous vertex's shadow ray, apply its
+// weight, add this vertex's emission, per bin, with compensated sums.
+__global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
     const int L = sc.L;
     const int b = a.b;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long n_ext = 0, n_sh = 0, n_glass = 0;
+    unsigned long long n_glass = 0;
     const PathState &ps = a.ps;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
         const int64_t q = base + lane;
-        bool want_e = false, want_s = false;
-        int cell_e = 0, cell_s = 0;
-        float4 e0 = make_float4(0, 0, 0, 0), e1 = e0, s0 = e0, s1 = e0;
-        int4 e2 = make_int4(0, 0, 0, 0), s2 = e2;
         int fl = q < np ? ps.flags[q] : 0;
         if (fl & (kFlExt | kFlShadow)) {
             const int64_t gp = a.path_begin + q;
             const int r = find_render(a.rb, gp);
             const RenderInfo &ri = a.rb.info[r];
-            const int64_t local = gp - ri.path_begin;
-            const uint32_t p = (uint32_t)(local / ri.spp), j = (uint32_t)(local % ri.spp);
 
             // (1) shadow ray of the previous vertex
             bool resolve = false;
@@ -631,24 +626,20 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
                 pw = ps.pend_w[q];
             }
             // (3) the hit of this vertex
-            bool has_hit = false, emit = false;
+            bool emit = false;
             int prim = -1, mat = 0, kind = 0;
-            V3 x = v3(0, 0, 0), d = x, ng = x, ns = x;
+            V3 d = v3(0, 0, 0), ng = d;
             float cd = 0.f;
             if ((fl & kFlExt) && b <= ri.max_depth) {
                 const float4 h0 = ps.hit0[q], h1 = ps.hit1[q];
                 prim = __float_as_int(h0.w);
-                if (b == 1 && a.first_prim) a.first_prim[q] = prim;
                 if (prim >= 0) {
-                    has_hit = true;
-                    x = xyz(h0);
                     d = xyz(h1);
                     const float4 tn = __ldg(sc.tri_n + prim);
                     ng = xyz(tn);
                     mat = __float_as_int(tn.w);
                     kind = __ldg(sc.mat_kind + mat);
                     cd = dot(d, ng);
-                    ns = cd < 0.0f ? ng : (-1.0f) * ng;
                     emit = (kind == kEmitter || kind == kDiffuseEmitter) && cd < 0.0f &&
                            (!ri.nee || b == 1 || (fl & kFlPrevSpec));
                 }
@@ -667,13 +658,13 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
             for (int k = 0; k < ncr; ++k) {
                 cst[k] = st_of(a.rb, r, cmat[k], sc.n_mat);
                 cth[k] = __ldg(sc.mat_thick + cmat[k]);
-                cq[k] = a.use_mlp ? a.cross_query[k * np + q] : -1;
+                cq[k] = a.use_queries ? a.cross_query[k * np + q] : -1;
             }
-            const int pq = (a.use_mlp && pend && pkind == kGlass) ? a.pend_query[q] : -1;
+            const int pq = (a.use_queries && pend && pkind == kGlass) ? a.pend_query[q] : -1;
             const bool need_T = resolve || pend || emit;
             if (need_T) {
                 Kahan NX, NY, NZ, EX, EY, EZ;
-#pragma unroll 2
+#pragma unroll 4
                 for (int i = 0; i < L; ++i) {
                     float t = ps.T[(size_t)i * np + q];
                     const float wx = __ldg(sc.wcmf + 3 * i), wy = __ldg(sc.wcmf + 3 * i + 1),
@@ -738,6 +729,57 @@ __global__ void __launch_bounds__(256) k_shade(KArgs a) {
                 ps.acc[3 * np + q] = acc.x.c;
                 ps.acc[4 * np + q] = acc.y.c;
                 ps.acc[5 * np + q] = acc.z.c;
+            }
+        }
+    }
+    warp_count(a.counters + 2, n_glass);
+}
+
+// Continuation half of shading: next-event sample toward the lights and the
+// next direction at this vertex, appended to the ray staging area.
+__global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t np = a.ps.np;
+    const DevScene &sc = a.sc;
+    const int L = sc.L;
+    const int b = a.b;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long n_ext = 0, n_sh = 0, n_glass = 0;
+    const PathState &ps = a.ps;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
+        const int64_t q = base + lane;
+        bool want_e = false, want_s = false;
+        int cell_e = 0, cell_s = 0;
+        float4 e0 = make_float4(0, 0, 0, 0), e1 = e0, s0 = e0, s1 = e0;
+        int4 e2 = make_int4(0, 0, 0, 0), s2 = e2;
+        int fl = q < np ? ps.flags[q] : 0;
+        if (fl & (kFlExt | kFlShadow)) {
+            const int64_t gp = a.path_begin + q;
+            const int r = find_render(a.rb, gp);
+            const RenderInfo &ri = a.rb.info[r];
+            const int64_t local = gp - ri.path_begin;
+            const uint32_t p = (uint32_t)(local / ri.spp), j = (uint32_t)(local % ri.spp);
+
+            // (3) the hit of this vertex
+            bool has_hit = false;
+            int prim = -1, mat = 0, kind = 0;
+            V3 x = v3(0, 0, 0), d = x, ng = x, ns = x;
+            float cd = 0.f;
+            if ((fl & kFlExt) && b <= ri.max_depth) {
+                const float4 h0 = ps.hit0[q], h1 = ps.hit1[q];
+                prim = __float_as_int(h0.w);
+                if (b == 1 && a.first_prim) a.first_prim[q] = prim;
+                if (prim >= 0) {
+                    has_hit = true;
+                    x = xyz(h0);
+                    d = xyz(h1);
+                    const float4 tn = __ldg(sc.tri_n + prim);
+                    ng = xyz(tn);
+                    mat = __float_as_int(tn.w);
+                    kind = __ldg(sc.mat_kind + mat);
+                    cd = dot(d, ng);
+                    ns = cd < 0.0f ? ng : (-1.0f) * ng;
+                }
             }
             // (4) continue the path from this vertex
             int nfl = fl & kFlPrevSpec;
@@ -887,10 +929,13 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
                  oCc = take(4 * kMaxCross * np), oH0 = take(16 * np), oH1 = take(16 * np), oIn = take(48 * cap),
                  oSt = take(48 * cap), oCtl = take(32 + 8 * (size_t)nc), oFill = take(8 * (size_t)nc),
                  oOff = take(4 * (2 * (size_t)nc + 1));
+    // glass evaluations of each bounce go through a query list, evaluated by the
+    // exact slab or the learned model in a dense pass before shading
     const bool use_mlp = run.bsdf_mode == SDDM_BSDF_MLP;
-    const int64_t q_cap = use_mlp ? 2 * np : 0;
-    const size_t oQ = take(16 * (size_t)q_cap + 16), oNq = take(16), oPq = take(use_mlp ? 4 * np : 4),
-                 oCq = take(use_mlp ? 4 * kMaxCross * np : 4), oRes = take(8 * (size_t)q_cap * L + 16);
+    const bool use_queries = true;
+    const int64_t q_cap = use_queries ? 2 * np : 0;
+    const size_t oQ = take(16 * (size_t)q_cap + 16), oNq = take(16), oPq = take(use_queries ? 4 * np : 4),
+                 oCq = take(use_queries ? 4 * kMaxCross * np : 4), oRes = take(8 * (size_t)q_cap * L + 16);
     if (off > buf.bytes) {
         if (buf.mem) cudaFree(buf.mem);
         buf.mem = nullptr;
@@ -937,7 +982,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     Q.cnt = (int *)(m + oCtl + 32);
     Q.fill = (int *)(m + oFill);
     Q.off = (int *)(m + oOff);
-    a.use_mlp = use_mlp;
+    a.use_queries = use_queries;
     a.queries = (float4 *)(m + oQ);
     a.n_queries = (unsigned long long *)(m + oNq);
     a.q_cap = q_cap;
@@ -945,7 +990,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     a.cross_query = (int *)(m + oCq);
     a.glass_res = (const float2 *)(m + oRes);
     MlpRows mr{};
-    if (use_mlp) {
+    if (use_queries) {
         mr.params = run.mlp_params;
         mr.sc = run.sc;
         mr.thick_min = run.mlp_dmin;
@@ -997,16 +1042,21 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
             *run.launches += 2;
         }
         a.b = b;
-        if (use_mlp && b >= 2) {
+        if (use_queries && b >= 2) {
             DDM_CHECK(cudaMemsetAsync(a.n_queries, 0, 8, s));
             k_glass_gather<<<path_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
-            DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s));
+            if (use_mlp)
+                DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s));
+            else
+                DDM_CHECK(launch_slab_rows(mr, run.sm_count, s));
             *run.launches += 2;
         }
-        k_shade<<<path_blocks, 256, 0, s>>>(a);
+        k_shade_spectral<<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
-        *run.launches += 1;
+        k_shade_continue<<<path_blocks, 256, 0, s>>>(a);
+        DDM_CHECK(cudaGetLastError());
+        *run.launches += 2;
     }
     k_finalize<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(a);
     DDM_CHECK(cudaGetLastError());

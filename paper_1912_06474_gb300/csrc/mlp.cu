@@ -281,6 +281,28 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
     if (a.fallbacks && n_fb) atomicAdd(a.fallbacks, n_fb);
 }
 
+// The exact slab for the same query rows, one thread per (query, bin): the
+// glass evaluations of a bounce as one dense, divergence-free pass.
+__global__ void __launch_bounds__(256) k_slab_rows(MlpRows a) {
+    int64_t total = a.n;
+    if (a.mode == 1) {
+        const int64_t nq = (int64_t)*a.n_queries;
+        total = (nq < a.q_cap ? nq : a.q_cap) * a.sc.L;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
+        RowIn in;
+        row_input(a, r, total, in);
+        const float2 y = exact_row(a, in);
+        if (a.mode == 0) {
+            a.R[r] = y.x;
+            a.T[r] = y.y;
+        } else {
+            a.results[r] = y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- training
 // One CTA = 64 rows = 4 warps x 16 rows: forward, loss gradient, backward,
 // and the CTA's share of every weight gradient, written to grad_cta[cta].
@@ -662,6 +684,11 @@ size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
     const int blocks = sm_count * 2;
     k_mlp_rows<<<blocks, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
+    k_slab_rows<<<sm_count * 8, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,8 @@ struct MlpRows {
     unsigned long long *fallbacks;    // 32-row batches that fell back to the exact slab
 };
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream);
+// The exact slab over the same rows (no network).
+cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream);
 
 // Training.
 struct MlpTrainArgs {
