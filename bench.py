@@ -6,18 +6,26 @@ synthetic hotel room -- 6x4x3 m, ~200.5k triangles (40 boxes, 100 spheres of
 2000 triangles, 20 of them metallic), two photochromic panes at s = 0.5 lit by
 suns behind them, a ceiling lamp -- at 512x512 px, 16 spp, max depth 5, 41
 wavelength bins, traced by domain decomposition over a 4x4x2 grid of
-subdomains (or by the plain global-BVH megakernel with --method megakernel).
+subdomains with the glass evaluated by the learned surrogate (probe and exact
+fallback on); --method megakernel / --bsdf exact select the other variants.
 
 value   = (extension + shadow segments of all ranks) / (max over ranks of the
           summed device time of the K timed steps), inputs resident in HBM,
-          L2 flushed between steps.
+          L2 flushed between steps, launched the library's default way (the
+          render's launch sequence replayed as a CUDA graph).
+value_eager = the same steps launched eagerly with CUDA events around every
+          trace launch (these events give the roofline's kernel time).
+arms    = the same metric for the other variants on the same workload: DDM
+          with the exact slab and the plain global-BVH megakernel with the
+          exact slab (the comparison the metric names).
 e2e     = the same metric through sddm_render_host: result image copied back
           to pinned host memory inside the timed region.
 roofline: the trace kernel (k_trace_wave for DDM, k_megakernel for the plain
           path): algorithmic bytes = ray-record reads and writes + BVH node
           (64 B) and triangle (48 B) fetches counted per ray, divided by the
-          kernel's own device time (CUDA events around each launch on the
-          library's stream), against the measured HBM copy bandwidth.
+          kernel's own device time, against the measured HBM copy bandwidth.
+image_rel_rmse_vs_oracle: the timed image against the FP64 oracle on the
+          pixel sample the CPU-baseline leg renders (validity: <= 1e-3).
 --impl reference times the FP64 CPU oracle on a bounded pixel sample of the
 same workload (there is no reference implementation to install).
 """
@@ -107,6 +115,20 @@ def _dist():
     return world, rank, local
 
 
+def reduce_over_ranks(max_vals, sum_vals, device="cpu"):
+    """Max over ranks of the timings and sum over ranks of the work counts
+    (the whole-job figures of a replicated run). A no-op on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(max_vals), list(sum_vals)
+    t = torch.tensor(list(max_vals), dtype=torch.float64, device=device)
+    n = torch.tensor(list(sum_vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in n.tolist()]
+
+
 def workload(method, width=512, height=512, spp=16, bsdf="exact"):
     from paper_1912_06474_gb300 import scenes
     scene = scenes.hotel_room(L=41, seed=0)
@@ -119,14 +141,18 @@ def workload(method, width=512, height=512, spp=16, bsdf="exact"):
     return scene, spec, grid, cfg
 
 
-def cpu_baseline(seconds_target=10.0, n_threads=0):
-    """The FP64 oracle, as it stands, on a seeded pixel sample of the same workload."""
+def cpu_baseline(seconds_target=10.0, n_threads=0, width=512, height=512, spp=16):
+    """The FP64 oracle, as it stands, on a seeded pixel sample of the same
+    workload. Returns the timing and the sampled pixels with their XYZ."""
+    import numpy as np
+
     import oracle
     from paper_1912_06474_gb300 import scenes
-    scene, spec, _, _ = workload("ddm")
+    scene, spec, _, _ = workload("ddm", width, height, spp)
     orc = oracle.Oracle(scene)
     n_pix, done_pix, segs, t_total = 512, 0, 0, 0.0
     seed = 0
+    pix_all, xyz_all = [], []
     while t_total < seconds_target and done_pix < spec.width * spec.height:
         pix = scenes.pixel_subset(spec.width, spec.height, n_pix, seed=seed)
         t0 = time.perf_counter()
@@ -134,24 +160,28 @@ def cpu_baseline(seconds_target=10.0, n_threads=0):
         dt = time.perf_counter() - t0
         t_total += dt
         segs += sum(r["segments"])
-        done_pix += n_pix
+        done_pix += len(pix)
+        pix_all.append(np.asarray(pix))
+        xyz_all.append(np.asarray(r["xyz"]))
         seed += 1
         n_pix = min(n_pix * 2, 8192)
     cores = n_threads if n_threads > 0 else (os.cpu_count() or 1)
-    return {"value": segs / t_total / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done_pix} seeded pixels x 16 spp of the hotel-room workload ({segs} segments, "
+    info = {"value": segs / t_total / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done_pix} seeded pixels x {spec.spp} spp of the hotel-room workload ({segs} segments, "
                       f"{t_total:.1f} s wall)"}
+    return info, np.concatenate(pix_all), np.concatenate(xyz_all)
 
 
 def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    _, _, _, cfg = workload(args.method, args.width, args.height, args.spp)
-    times, vals = [], []
+    _, _, _, cfg = workload("ddm", args.width, args.height, args.spp, args.bsdf)
+    vals = []
     base = None
     for k in range(args.warmup + args.steps):
-        b = cpu_baseline(seconds_target=min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+        b, _, _ = cpu_baseline(seconds_target=min(20.0, 60.0 / max(1, args.steps + args.warmup)),
+                               width=args.width, height=args.height, spp=args.spp)
         if k >= args.warmup:
             vals.append(b["value"])
             base = b
@@ -163,6 +193,26 @@ def run_reference(args):
                              "sample": base["sample"]},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timed_steps(ctx, spec, out, method, bsdf, steps, flush, stream):
+    """K renders, each bracketed by CUDA events on the library's stream, L2
+    flushed before each. Returns (device ms per step, stats per step)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sts = []
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sts.append(ctx.render_into([spec], [out], method=method, bsdf=bsdf))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], sts
+
+
+def _segs(st):
+    return st["segments_ext"] + st["segments_shadow"]
 
 
 def run(args):
@@ -184,7 +234,7 @@ def run(args):
     t0 = time.perf_counter()
     ctx.build(grid=grid, blocks_per_sm=args.blocks_per_sm, paths_in_flight=args.paths_in_flight)
     build_s = time.perf_counter() - t0
-    train = None
+    cfg["build_s"] = round(build_s, 3)
     if args.bsdf == "mlp":   # the surrogate is trained once, before and outside the timed steps
         train = ctx.mlp_train(scene.glass_materials()[0], seed=7)
         cfg["surrogate_training"] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in train.items()}
@@ -194,7 +244,9 @@ def run(args):
     # traversal counts of this exact workload (separately compiled counting kernel, untimed)
     ctx.set_profiling(count_traversal=True)
     cst = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
-    ctx.set_profiling(time_trace=True)
+    # the library's default launch path: the render's launch sequence captured
+    # once as a CUDA graph and replayed
+    ctx.set_profiling()
     for _ in range(args.warmup):
         ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
     torch.cuda.synchronize()
@@ -202,34 +254,21 @@ def run(args):
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    segs, trace_ms, trace_launches, launches = 0, 0.0, 0, 0
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        st = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
-        ev[k][1].record(stream)
-        segs += st["segments_ext"] + st["segments_shadow"]
-        trace_ms += st["trace_ms"]
-        trace_launches += st["trace_launches"]
-        launches += st["kernel_launches"]
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms, sts = _timed_steps(ctx, spec, out, args.method, args.bsdf, args.steps, flush, stream)
+    segs = sum(_segs(s) for s in sts)
+    launches = sum(s["kernel_launches"] for s in sts)
+    fallbacks = sum(s.get("mlp_fallbacks", 0) for s in sts)
     total_ms = sum(step_ms)
-    # the same steps replayed as a CUDA graph (the library's default launch path)
-    ctx.set_profiling()
+    image = out.clone()
+    # the same steps launched eagerly with CUDA events around every trace launch:
+    # the trace kernel's own device time for the roofline
+    ctx.set_profiling(time_trace=True)
     for _ in range(3):
         ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
-    gms, gsegs = 0.0, 0
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        st = ctx.render_into([spec], [out], method=args.method, bsdf=args.bsdf)
-        ev[k][1].record(stream)
-        gsegs += st["segments_ext"] + st["segments_shadow"]
-    torch.cuda.synchronize()
-    gms = sum(a.elapsed_time(b) for a, b in ev)
+    eager_ms, ests = _timed_steps(ctx, spec, out, args.method, args.bsdf, args.steps, flush, stream)
+    trace_ms = sum(s["trace_ms"] for s in ests)
+    trace_launches = sum(s["trace_launches"] for s in ests)
+    ctx.set_profiling()
     # end to end through the host-buffer entry point
     host = torch.empty((spec.height, spec.width, 3), dtype=torch.float32).pin_memory()
     e2e_ms, e2e_segs = 0.0, 0
@@ -239,16 +278,36 @@ def run(args):
         t0 = time.perf_counter()
         st = ctx.render_host([spec], [host], method=args.method, bsdf=args.bsdf)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_segs += st["segments_ext"] + st["segments_shadow"]
+        e2e_segs += _segs(st)
+    # the other arms of the comparison on the same workload and timing rules
+    arms = {}
+    if not args.single_arm:
+        other = [("ddm", "exact")] if (args.method, args.bsdf) != ("ddm", "exact") else [("ddm", "mlp")]
+        other.append(("megakernel", "exact"))
+        for method, bsdf in other:
+            if method == "ddm":
+                actx = ctx
+                if bsdf == "mlp" and args.bsdf != "mlp":
+                    ctx.mlp_train(scene.glass_materials()[0], seed=7)
+            else:
+                actx = sddm.Context(local, stream)
+                actx.set_scene(scene)
+                actx.build(grid=(1, 1, 1))
+            for _ in range(args.warmup):
+                actx.render_into([spec], [out], method=method, bsdf=bsdf)
+            ms, asts = _timed_steps(actx, spec, out, method, bsdf, args.steps, flush, stream)
+            arms[f"{method}_{bsdf}"] = [sum(ms), sum(_segs(s) for s in asts)]
+            if actx is not ctx:
+                actx.close()
     clk = clocks.stop()
 
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        n = torch.tensor([segs, e2e_segs], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(n)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
-        segs, e2e_segs = int(n[0]), int(n[1])
+    keys = sorted(arms)
+    mx, sm = reduce_over_ranks([total_ms, e2e_ms, sum(eager_ms), trace_ms] + [arms[k][0] for k in keys],
+                               [segs, e2e_segs, sum(_segs(s) for s in ests)] + [arms[k][1] for k in keys],
+                               device="cuda")
+    total_ms, e2e_ms, eager_total, trace_ms = mx[:4]
+    segs, e2e_segs, eager_segs = sm[:3]
+    arm_vals = {k: round(sm[3 + i] / (mx[4 + i] / 1e3) / 1e6, 3) for i, k in enumerate(keys)}
     if rank != 0:
         return
     value = segs / (total_ms / 1e3) / 1e6
@@ -256,7 +315,10 @@ def run(args):
     # algorithmic bytes of the trace kernel per step, from the counting run
     visits, crossings = cst["ray_visits"], cst["crossings"]
     n_ext = cst["segments_ext"]
-    bytes_step = (48 * visits + 48 * crossings + 32 * n_ext + 64 * cst["node_visits"] + 48 * cst["tri_tests"])
+    if args.method == "ddm":
+        bytes_step = (48 * visits + 48 * crossings + 32 * n_ext + 64 * cst["node_visits"] + 48 * cst["tri_tests"])
+    else:   # megakernel: per segment a 16 B hit record, node and triangle fetches
+        bytes_step = 16 * n_ext + 64 * cst["node_visits"] + 48 * cst["tri_tests"]
     trace_s = trace_ms / 1e3 / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_step / trace_s / 1e9 if trace_s > 0 else None
@@ -275,7 +337,8 @@ def run(args):
                 traffic = ent["dram_bytes_per_launch"]
     except Exception:
         traffic = None
-    h2d = 0   # render tables: a few hundred bytes, counted below from the descriptor layout
+    # host->device per step: the render descriptor, the per-material state table
+    # and the stats block; device->host: the XYZ image, counters and error word
     h2d = 128 * 1 + 4 * len(scene.materials) + 3 * 8
     d2h = spec.width * spec.height * 3 * 4 + 64 + 16
     line = {
@@ -292,12 +355,16 @@ def run(args):
                      "trace_launches_per_step": trace_launches // args.steps,
                      "nodes_per_visit": round(cst["node_visits"] / max(visits, 1), 2),
                      "tris_per_visit": round(cst["tri_tests"] / max(visits, 1), 2)},
-        "value_graph_replay": round(gsegs / (gms / 1e3) / 1e6, 3) if gms > 0 else None,
-        "segments_per_step": segs // (args.steps * world), "build_s": round(build_s, 3), "clocks": clk,
-        "mlp_fallback_batches_per_step": st.get("mlp_fallbacks", 0) if args.bsdf == "mlp" else None,
+        "value_eager": round(eager_segs / (eager_total / 1e3) / 1e6, 3),
+        "arms": arm_vals,
+        "segments_per_step": segs // (args.steps * world), "clocks": clk,
+        "mlp_fallback_batches_per_step": fallbacks // args.steps if args.bsdf == "mlp" else None,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        info, pix, ref = cpu_baseline(width=args.width, height=args.height, spp=args.spp)
+        line["cpu_baseline"] = info
+        got = image.cpu().numpy().reshape(-1, 3)[pix].astype(np.float64)
+        line["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     print(json.dumps(line), flush=True)
 
 
@@ -308,16 +375,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sddm", choices=["sddm", "reference"])
     ap.add_argument("--method", default="ddm", choices=["ddm", "megakernel"])
-    ap.add_argument("--bsdf", default="exact", choices=["exact", "mlp"])
+    ap.add_argument("--bsdf", default="mlp", choices=["exact", "mlp"])
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--paths-in-flight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-arm", action="store_true", help="time only the selected method and glass model")
     ap.add_argument("--width", type=int, default=512)
     ap.add_argument("--height", type=int, default=512)
     ap.add_argument("--spp", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.method == "megakernel":
+        args.bsdf = "exact"   # the surrogate is served by the DDM path's dense query pass only
     if args.impl == "reference":
         run_reference(args)
     else:
