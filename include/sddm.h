@@ -208,18 +208,24 @@ int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats
  * streams or threads) race on it. Output: d->xyz_out, DEVICE, as sddm_render. */
 int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st);
 
-/* Pick grid, queue capacity and blocks per SM for these renders by timing
- * short pilot renders (<= 1 spp) of candidate settings (Sec. 5 load
- * balancing, done here by measurement). Writes the best options to *best and
- * leaves the context built with them. */
+/* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}), the
+ * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per
+ * chunk ({2^21, 2^22, 2^23}; the ray queues are sized from it, two rays per
+ * path, so they cannot overflow) for these renders, by timing short pilot
+ * renders (1 spp, at most 512 x 512) of each candidate (Sec. 5 load
+ * balancing, settled here by measurement). Writes the best options to *best
+ * and leaves the context built with them. */
 int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_opts *best);
 
 /* ------------------------------------------------- learned glass surrogate
  * A small network stands in for the exact slab R, T of a glass material (the
  * paper evaluates glass "by the Fresnel definition", Sec. 6): inputs
- * (cos theta, lambda, s, thickness) mapped to [-1, 1] over the trained box
- * cos in [0,1], lambda in [380,780] nm, s in [0,1], thickness in
- * [thick_min, thick_max]; 3 hidden layers of 64 SiLU units; outputs (R, T).
+ * (cos theta, lambda, s, thickness), each mapped to [-1, 1]: 2 cos - 1,
+ * (lambda - 380)/200 - 1, 2 s - 1, and the thickness d through the normal-
+ * incidence internal transmittance 2 exp(-alpha(lambda, s) d) - 1 with the
+ * material's alpha = alpha_clear + s dalpha; the trained box is cos in [0,1],
+ * lambda in [380,780] nm, s in [0,1], d in [thick_min, thick_max]; 3 hidden
+ * layers of 64 SiLU units; outputs (R, T).
  * Weights and activations are BF16 with FP32 accumulation and FP32 master
  * weights; parameters in this order (8770 floats): W1[64][4], b1[64],
  * W2[64][64], b2[64], W3[64][64], b3[64], W4[2][64], b4[2]. */
@@ -229,7 +235,7 @@ typedef struct {
     int64_t samples;          /* exact training samples drawn once (0 = 2^22) */
     int steps;                /* Adam steps (0 = 20000) */
     int batch;                /* rows per step, multiple of 64 (0 = 8192) */
-    float lr;                 /* peak learning rate, cosine decay to lr/100 (0 = 1e-3) */
+    float lr;                 /* peak learning rate, cosine decay to lr/100 (0 = 3e-3) */
     uint32_t seed;            /* Philox key of the samples and the initial weights */
     float thick_min, thick_max; /* trained thickness range, m (0, 0 = 0.002, 0.010) */
     int resume;               /* 1: continue from the current weights and Adam state */

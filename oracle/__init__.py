@@ -99,7 +99,7 @@ def _load():
         lib.orc_num_lights.argtypes = [P]
         lib.orc_num_lights.restype = C.c_int
         lib.orc_mlp_n_params.restype = C.c_int
-        lib.orc_mlp_features.argtypes = [C.c_double] * 4 + [P]
+        lib.orc_mlp_features.argtypes = [C.c_double] * 5 + [P]
         lib.orc_mlp_forward.argtypes = [P, P, P]
         lib.orc_mlp_forward_d.argtypes = [P, P, P]
         lib.orc_mlp_loss_grad.argtypes = [P, C.c_int, P, P, P]
@@ -163,9 +163,11 @@ def cosine_dir(ns, u0, u1):
 MLP_PARAMS = 8770
 
 
-def mlp_features(c, lam_nm, s, d):
+def mlp_features(c, lam_nm, s, d, alpha):
+    """Network inputs of one row: cos, wavelength (nm), coloration state,
+    thickness (m) and the absorption coefficient alpha(lambda, s) (1/m)."""
     x = np.zeros(4)
-    _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), _ptr(x))
+    _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), float(alpha), _ptr(x))
     return x
 
 

@@ -70,6 +70,7 @@ struct KArgs {
     int *pend_query;      // [np]
     int *cross_query;     // [kMaxCross][np]
     const float2 *glass_res;
+    int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
 };
 
 // ---------------------------------------------------------------- grid
@@ -515,44 +516,99 @@ __device__ __forceinline__ float st_of(const RenderBatch &rb, int r, int m, int 
     return __ldg(rb.state_s + (size_t)r * n_mat + m);
 }
 
-// Glass evaluations the next shading pass needs (the pending glass weight of
+// Glass evaluations of this bounce (the weight of a glass vertex pending from
 // the last vertex, the slabs an unoccluded shadow ray crossed), compacted into
-// a query list for the learned model; a query index of -1 (list full) makes
-// the shading pass use the exact slab.
+// a query list in path-slot order, so that the list and everything computed
+// from it are the same on every run. Block i owns the contiguous slot range
+// [i*chunk, (i+1)*chunk): a count pass stores each block's total, the gather
+// pass offsets each block by the totals of the blocks before it. A query index
+// of -1 (list full) makes the shading pass use the exact slab.
+__device__ __forceinline__ int glass_query_count(const KArgs &a, int64_t q, int &pm) {
+    const PathState &ps = a.ps;
+    const int fl = q < ps.np ? ps.flags[q] : 0;
+    int n = 0;
+    pm = 0;
+    if (fl & (kFlExt | kFlShadow)) {
+        if (fl & kFlPend) {
+            pm = ps.pend_mat[q];
+            n = __ldg(a.sc.mat_kind + pm) == kGlass;
+        }
+        if (fl & kFlShadow) {
+            const int st = ps.sh_status[q];
+            if ((st & 3) == kShadowClear) n += st >> 4;
+        }
+    }
+    return n;
+}
+
+__device__ __forceinline__ int64_t glass_chunk(int64_t np) {
+    const int64_t per = (np + gridDim.x - 1) / gridDim.x;
+    return (per + 255) & ~(int64_t)255;
+}
+
+// Block-wide exclusive scan of one int per thread (256 threads); returns the
+// thread's exclusive prefix and the block total in *total.
+__device__ __forceinline__ int block_scan256(int v, int *s_w, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < 8; ++k) {
+        const int t = s_w[k];
+        before += k < w ? t : 0;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(256) k_glass_count(KArgs a) {
+    __shared__ int s_w[8];
+    const int64_t np = a.ps.np, chunk = glass_chunk(np);
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
+    int sum = 0;
+    for (int64_t q = lo + threadIdx.x; q < hi; q += 256) {
+        int pm;
+        sum += glass_query_count(a, q, pm);
+    }
+    int total;
+    block_scan256(sum, s_w, &total);
+    if (threadIdx.x == 0) a.block_cnt[blockIdx.x] = total;
+}
+
 __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t np = a.ps.np;
+    __shared__ int s_w[8];
     const PathState &ps = a.ps;
     const DevScene &sc = a.sc;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-        const int64_t q = base + lane;
-        int fl = q < np ? ps.flags[q] : 0;
-        int n_pend = 0, n_cr = 0, pm = 0;
-        if (fl & (kFlExt | kFlShadow)) {
-            if (fl & kFlPend) {
-                pm = ps.pend_mat[q];
-                n_pend = __ldg(sc.mat_kind + pm) == kGlass;
-            }
-            if (fl & kFlShadow) {
-                const int st = ps.sh_status[q];
-                if ((st & 3) == kShadowClear) n_cr = st >> 4;
-            }
-        }
-        const int cnt = n_pend + n_cr;
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned long long wb = 0;
-        if (lane == 31 && warp_total > 0) wb = atomicAdd(a.n_queries, (unsigned long long)warp_total);
-        wb = __shfl_sync(0xffffffffu, wb, 31);
+    const int64_t np = ps.np, chunk = glass_chunk(np);
+    const int64_t lo = (int64_t)blockIdx.x * chunk, hi = lo + chunk < np ? lo + chunk : np;
+    // this block's offset: the totals of the blocks before it
+    int part = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += 256) part += a.block_cnt[k];
+    int before_all;
+    block_scan256(part, s_w, &before_all);
+    int64_t base = before_all;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        *a.n_queries = (unsigned long long)(base + a.block_cnt[blockIdx.x]);
+    for (int64_t t0 = lo; t0 < hi; t0 += 256) {
+        const int64_t q = t0 + threadIdx.x;
+        int pm = 0;
+        const int cnt = q < hi ? glass_query_count(a, q, pm) : 0;
+        int tile_total;
+        const int excl = block_scan256(cnt, s_w, &tile_total);
         if (cnt > 0) {
+            const int fl = ps.flags[q];
+            const int n_pend = (fl & kFlPend) && __ldg(sc.mat_kind + pm) == kGlass;
+            const int n_cr = cnt - n_pend;
             const int64_t gp = a.path_begin + q;
             const int r = find_render(a.rb, gp);
-            int64_t idx = (int64_t)wb + incl - cnt;
+            int64_t idx = base + excl;
             if (n_pend) {
                 const int my = idx < a.q_cap ? (int)idx : -1;
                 if (my >= 0)
@@ -570,6 +626,7 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
                 a.cross_query[k * np + q] = my;
             }
         }
+        base += tile_total;
     }
 }
 
@@ -934,8 +991,11 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     const bool use_mlp = run.bsdf_mode == SDDM_BSDF_MLP;
     const bool use_queries = true;
     const int64_t q_cap = use_queries ? 2 * np : 0;
+    const int sm = std::max(1, run.sm_count);
+    const unsigned path_blocks = (unsigned)std::min<int64_t>((np + 255) / 256, (int64_t)sm * 16);
     const size_t oQ = take(16 * (size_t)q_cap + 16), oNq = take(16), oPq = take(use_queries ? 4 * np : 4),
-                 oCq = take(use_queries ? 4 * kMaxCross * np : 4), oRes = take(8 * (size_t)q_cap * L + 16);
+                 oCq = take(use_queries ? 4 * kMaxCross * np : 4), oRes = take(8 * (size_t)q_cap * L + 16),
+                 oBc = take(4 * (size_t)path_blocks + 16);
     if (off > buf.bytes) {
         if (buf.mem) cudaFree(buf.mem);
         buf.mem = nullptr;
@@ -989,6 +1049,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     a.pend_query = (int *)(m + oPq);
     a.cross_query = (int *)(m + oCq);
     a.glass_res = (const float2 *)(m + oRes);
+    a.block_cnt = (int *)(m + oBc);
     MlpRows mr{};
     if (use_queries) {
         mr.params = run.mlp_params;
@@ -1005,10 +1066,8 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
         mr.fallbacks = run.counters + 4;
     }
 
-    const int sm = std::max(1, run.sm_count);
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
     const int scatter_blocks = sm * 4;
-    const unsigned path_blocks = (unsigned)std::min<int64_t>((np + 255) / 256, (int64_t)sm * 16);
     const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
     const size_t ctl_bytes = 32 + 8 * (size_t)nc;
     cudaError_t e;
@@ -1043,9 +1102,11 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
         }
         a.b = b;
         if (use_queries && b >= 2) {
-            DDM_CHECK(cudaMemsetAsync(a.n_queries, 0, 8, s));
+            k_glass_count<<<path_blocks, 256, 0, s>>>(a);
+            DDM_CHECK(cudaGetLastError());
             k_glass_gather<<<path_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
+            *run.launches += 1;
             if (use_mlp)
                 DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s));
             else

@@ -73,11 +73,16 @@ __device__ __forceinline__ void zero_acc(float acc[8][4]) {
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
 }
 
-__device__ __forceinline__ void features(float c, float lam, float s, float d, float dmin, float dmax, float x[4]) {
+// Network inputs from (cos, lambda, s, thickness): cos and s mapped to [-1, 1],
+// lambda over 380-780 nm to [-1, 1], and the thickness through the slab's
+// internal transmittance at normal incidence, exp(-alpha(lambda, s) d) mapped
+// to [-1, 1] (alpha = alpha_clear + s dalpha, the material's absorption law).
+// Angle, Fresnel and the multiple reflections are left to the network.
+__device__ __forceinline__ void features(float c, float lam, float s, float alpha_d, float x[4]) {
     x[0] = 2.0f * c - 1.0f;
     x[1] = (lam - 380.0f) * (1.0f / 200.0f) - 1.0f;
     x[2] = 2.0f * s - 1.0f;
-    x[3] = 2.0f * (d - dmin) / (dmax - dmin) - 1.0f;
+    x[3] = 2.0f * expf(-alpha_d) - 1.0f;
 }
 
 // ------------------------------------------------------------- inference
@@ -174,6 +179,12 @@ struct RowIn {
     int mat, bin;
 };
 
+// alpha(lambda, s) * d of a row: the absorption law at the row's bin.
+__device__ __forceinline__ float row_alpha_d(const DevScene &sc, const RowIn &in) {
+    const size_t k = (size_t)in.mat * sc.L + in.bin;
+    return (__ldg(sc.mat_b + k) + in.s * __ldg(sc.mat_c + k)) * in.d;
+}
+
 __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t total, RowIn &in) {
     if (r >= total) {
         in.c = 0.5f;
@@ -224,40 +235,59 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
     load_infer_weights(s, a.params);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    int64_t total = a.n;
+    // A batch is 32 rows of one query's bins (renderer queries: a batch never
+    // mixes two glass evaluations, so its probe speaks for rows that share
+    // angle, state and thickness) or 32 consecutive explicit rows.
+    const int L = a.sc.L;
+    int64_t total = a.n, n_batches = (a.n + 31) / 32;
+    int nb = 1;
     if (a.mode == 1) {
-        const int64_t nq = (int64_t)*a.n_queries;
-        total = (nq < a.q_cap ? nq : a.q_cap) * a.sc.L;
+        const int64_t nq0 = (int64_t)*a.n_queries;
+        const int64_t nq = nq0 < a.q_cap ? nq0 : a.q_cap;
+        total = nq * L;
+        nb = (L + 31) / 32;
+        n_batches = nq * nb;
     }
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long n_fb = 0;
-    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b * 32 < total; b += nwarps) {
-        const int64_t r0 = b * 32;
+    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b < n_batches; b += nwarps) {
+        int64_t r0;
+        int nvalid;
+        if (a.mode == 1) {
+            const int64_t qi = b / nb;
+            const int j = (int)(b - qi * nb);
+            r0 = qi * L + 32 * j;
+            nvalid = L - 32 * j < 32 ? L - 32 * j : 32;
+        } else {
+            r0 = b * 32;
+            nvalid = total - r0 < 32 ? (int)(total - r0) : 32;
+        }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
+            if (half == 1 && nvalid <= 16) break;   // warp-uniform: no valid row in the second tile
             RowIn il, ih;
-            row_input(a, r0 + 16 * half + g, total, il);
-            row_input(a, r0 + 16 * half + g + 8, total, ih);
+            const int kl = 16 * half + g, kh = kl + 8;
+            row_input(a, kl < nvalid ? r0 + kl : total, total, il);
+            row_input(a, kh < nvalid ? r0 + kh : total, total, ih);
             float xl[4], xh[4], yl[2], yh[2];
-            features(il.c, il.lam, il.s, il.d, a.thick_min, a.thick_max, xl);
-            features(ih.c, ih.lam, ih.s, ih.d, a.thick_min, a.thick_max, xh);
+            features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
+            features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
             tile_forward(s, act[w], xl, xh, lane, yl, yh);
             if (t == 0) {
-                out[w][16 * half + g] = make_float2(yl[0], yl[1]);
-                out[w][16 * half + g + 8] = make_float2(yh[0], yh[1]);
+                out[w][kl] = make_float2(yl[0], yl[1]);
+                out[w][kh] = make_float2(yh[0], yh[1]);
             }
         }
         __syncwarp();
         RowIn in;
-        const bool valid = row_input(a, r0 + lane, total, in);
+        const bool valid = row_input(a, lane < nvalid ? r0 + lane : total, total, in);
         float2 y = out[w][lane];
         const bool in_box = in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f &&
                             in.s >= 0.0f && in.s <= 1.0f && in.d >= a.thick_min && in.d <= a.thick_max;
         const bool box_ok = __all_sync(kFull, !valid || in_box);
         const uint4 pr = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, kSlotProbe), a.probe_key,
                                        0x50524f42u);
-        int pick = (int)(pr.x & 31u);
-        if (r0 + pick >= total) pick = 0;
+        const int pick = (int)(pr.x % (uint32_t)nvalid);
         int bad = 0;
         if (lane == pick) {
             const float2 e = exact_row(a, in);
@@ -313,7 +343,9 @@ struct TrainSmem {
     float z1[H * H], z2[H * H], z3[H * H];
     float w1[H * 4], w4[2 * H], b1[H], b2[H], b3[H], b4[2];
     float x[kMlpRowsPerCta * 4], y[kMlpRowsPerCta * 2];
-    float gw1[H * 4], gb1[H], gb2[H], gb3[H], gw4[2 * H], gb4[2], loss;
+    // per-warp partial sums of the small gradients, added in warp order at the
+    // end (no float atomics: the same rows give the same gradient bits)
+    float gw1[4][H * 4], gb1[4][H], gb2[4][H], gb3[4][H], gw4[4][2 * H], gb4[4][2], loss[4];
 };
 
 __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
@@ -332,23 +364,16 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
     }
     for (int i = tid; i < H * 4; i += blockDim.x) {
         s.w1[i] = bf16r(p[OFF_W1 + i]);
-        s.gw1[i] = 0.f;
     }
     for (int i = tid; i < 2 * H; i += blockDim.x) {
         s.w4[i] = bf16r(p[OFF_W4 + i]);
-        s.gw4[i] = 0.f;
     }
     for (int i = tid; i < H; i += blockDim.x) {
         s.b1[i] = p[OFF_B1 + i];
         s.b2[i] = p[OFF_B2 + i];
         s.b3[i] = p[OFF_B3 + i];
-        s.gb1[i] = s.gb2[i] = s.gb3[i] = 0.f;
     }
-    if (tid < 2) {
-        s.b4[tid] = p[OFF_B4 + tid];
-        s.gb4[tid] = 0.f;
-    }
-    if (tid == 0) s.loss = 0.f;
+    if (tid < 2) s.b4[tid] = p[OFF_B4 + tid];
     const int cta_row0 = cta * kMlpRowsPerCta;
     for (int i = tid; i < kMlpRowsPerCta; i += blockDim.x) {
         const bool ok = cta_row0 + i < a.n_rows;
@@ -452,9 +477,9 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
             b1 += __shfl_xor_sync(0x11111111u, b1, o);
         }
         if (lane == 0) {
-            atomicAdd(&s.loss, lsum);
-            atomicAdd(&s.gb4[0], b0);
-            atomicAdd(&s.gb4[1], b1);
+            s.loss[w] = lsum;
+            s.gb4[w][0] = b0;
+            s.gb4[w][1] = b1;
         }
     }
     // dW4 and dz3
@@ -470,8 +495,8 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
                 g1 += __shfl_xor_sync(kFull, g1, o);
             }
             if (g == 0) {
-                atomicAdd(&s.gw4[c], g0);
-                atomicAdd(&s.gw4[H + c], g1);
+                s.gw4[w][c] = g0;
+                s.gw4[w][H + c] = g1;
             }
             const float dzl = (dyl0 * s.w4[c] + dyl1 * s.w4[H + c]) * dsilu(s.z3[rl * H + c]);
             const float dzh = (dyh0 * s.w4[c] + dyh1 * s.w4[H + c]) * dsilu(s.z3[rh * H + c]);
@@ -481,7 +506,7 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
             s.dz3t[c * LD + rh] = __float2bfloat16_rn(dzh);
             float gb = dzl + dzh;
             for (int o = 4; o <= 16; o <<= 1) gb += __shfl_xor_sync(kFull, gb, o);
-            if (g == 0) atomicAdd(&s.gb3[c], gb);
+            if (g == 0) s.gb3[w][c] = gb;
         }
     }
     __syncthreads();
@@ -512,7 +537,7 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
             s.dz2t[c * LD + rh] = __float2bfloat16_rn(dzh);
             float gb = dzl + dzh;
             for (int o = 4; o <= 16; o <<= 1) gb += __shfl_xor_sync(kFull, gb, o);
-            if (g == 0) atomicAdd(&s.gb2[c], gb);
+            if (g == 0) s.gb2[w][c] = gb;
         }
     }
     __syncthreads();
@@ -546,22 +571,24 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
                 for (int k = 0; k < 4; ++k) gk[k] += __shfl_xor_sync(kFull, gk[k], o);
             }
             if (g == 0) {
-                atomicAdd(&s.gb1[c], gb);
+                s.gb1[w][c] = gb;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) atomicAdd(&s.gw1[4 * c + k], gk[k]);
+                for (int k = 0; k < 4; ++k) s.gw1[w][4 * c + k] = gk[k];
             }
         }
     }
     __syncthreads();
-    for (int i = tid; i < H * 4; i += blockDim.x) gout[OFF_W1 + i] = s.gw1[i];
-    for (int i = tid; i < 2 * H; i += blockDim.x) gout[OFF_W4 + i] = s.gw4[i];
+    for (int i = tid; i < H * 4; i += blockDim.x)
+        gout[OFF_W1 + i] = ((s.gw1[0][i] + s.gw1[1][i]) + s.gw1[2][i]) + s.gw1[3][i];
+    for (int i = tid; i < 2 * H; i += blockDim.x)
+        gout[OFF_W4 + i] = ((s.gw4[0][i] + s.gw4[1][i]) + s.gw4[2][i]) + s.gw4[3][i];
     for (int i = tid; i < H; i += blockDim.x) {
-        gout[OFF_B1 + i] = s.gb1[i];
-        gout[OFF_B2 + i] = s.gb2[i];
-        gout[OFF_B3 + i] = s.gb3[i];
+        gout[OFF_B1 + i] = ((s.gb1[0][i] + s.gb1[1][i]) + s.gb1[2][i]) + s.gb1[3][i];
+        gout[OFF_B2 + i] = ((s.gb2[0][i] + s.gb2[1][i]) + s.gb2[2][i]) + s.gb2[3][i];
+        gout[OFF_B3 + i] = ((s.gb3[0][i] + s.gb3[1][i]) + s.gb3[2][i]) + s.gb3[3][i];
     }
-    if (tid < 2) gout[OFF_B4 + tid] = s.gb4[tid];
-    if (tid == 0) a.loss_cta[cta] = s.loss;
+    if (tid < 2) gout[OFF_B4 + tid] = ((s.gb4[0][tid] + s.gb4[1][tid]) + s.gb4[2][tid]) + s.gb4[3][tid];
+    if (tid == 0) a.loss_cta[cta] = ((s.loss[0] + s.loss[1]) + s.loss[2]) + s.loss[3];
 }
 
 // Sum of the per-CTA gradients in CTA order (deterministic), then Adam with
@@ -613,7 +640,7 @@ __global__ void k_mlp_data(DevScene sc, uint32_t mat, int64_t n, uint32_t seed, 
     float R_, T_;
     slab_RT(c, lam, nn, ac + st * da, d, R_, T_);
     float x[4];
-    features(c, lam, st, d, dmin, dmax, x);
+    features(c, lam, st, (ac + st * da) * d, x);
     for (int k = 0; k < 4; ++k) X[4 * i + k] = x[k];
     Y[2 * i] = R_;
     Y[2 * i + 1] = T_;
@@ -665,8 +692,8 @@ __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
         grid_in(min(r0 + g, total - 1), il);
         grid_in(min(r0 + g + 8, total - 1), ih);
         float xl[4], xh[4], yl[2], yh[2];
-        features(il.c, il.lam, il.s, il.d, a.thick_min, a.thick_max, xl);
-        features(ih.c, ih.lam, ih.s, ih.d, a.thick_min, a.thick_max, xh);
+        features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
+        features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
         tile_forward(s, act[w], xl, xh, lane, yl, yh);
         if (t == 0) {
             const float2 el = exact_row(a, il), eh = exact_row(a, ih);

@@ -948,6 +948,24 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
             }
         }
     }
+    // second stage: paths in flight per chunk (memory per chunk against the
+    // per-chunk launch overhead) for the chosen grid and blocks per SM
+    if (rc == SDDM_OK && (rc = sddm_build(ctx, &chosen)) == SDDM_OK) {
+        const int64_t pif_list[] = {(int64_t)1 << 21, (int64_t)1 << 22, (int64_t)1 << 23};
+        sddm_build_opts stage = chosen;
+        for (int64_t pif : pif_list) {
+            ctx->opts.paths_in_flight = pif;
+            sddm_stats st{};
+            if ((rc = sddm_render(ctx, pilot.data(), n, &st)) != SDDM_OK) break;
+            if ((rc = sddm_render(ctx, pilot.data(), n, &st)) != SDDM_OK) break;
+            double rate = (double)(st.segments_ext + st.segments_shadow) / std::max(st.gpu_ms, 1e-6);
+            if (rate > best_rate) {
+                best_rate = rate;
+                stage = ctx->opts;
+            }
+        }
+        chosen = stage;
+    }
     for (void *q : bufs) cudaFree(q);
     if (rc != SDDM_OK) return rc;
     if ((rc = sddm_build(ctx, &chosen)) != SDDM_OK) return rc;
@@ -988,7 +1006,7 @@ int sddm_mlp_train(sddm_ctx *ctx, uint32_t mat, const sddm_mlp_train_opts *opts,
     if (o.samples <= 0) o.samples = (int64_t)1 << 22;
     if (o.steps <= 0) o.steps = 20000;
     if (o.batch <= 0) o.batch = 8192;
-    if (o.lr <= 0.f) o.lr = 1e-3f;
+    if (o.lr <= 0.f) o.lr = 3e-3f;
     if (o.thick_min <= 0.f && o.thick_max <= 0.f) {
         o.thick_min = 0.002f;
         o.thick_max = 0.010f;

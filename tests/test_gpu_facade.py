@@ -43,3 +43,36 @@ def test_facade_room(oracle_mod):
     print(f"facade build {build_s:.1f} s; 1920x1080x4 spp, depth 8, L 81: DDM 8x8x4 {rates['ddm']:.0f} "
           f"Mseg/s, megakernel {rates['megakernel']:.0f} Mseg/s")
     ctx.close()
+
+
+def test_facade_full_configuration_batched_surrogate(oracle_mod):
+    """The facade workload at its full size, in one call: 16 renders of
+    1920x1080 px at 64 spp, depth 8, 81 bins, DDM over 8x8x4 subdomains, the
+    glass of all 8 panes (one set of curves, each pane its own s) served by one
+    trained surrogate with probe and exact fallback. Checked on a seeded pixel
+    subset of every render against the FP64 oracle."""
+    from paper_1912_06474_gb300 import sddm
+    sc = scenes.facade_room(L=81, seed=0)
+    ctx = sddm.Context(0)
+    ctx.set_scene(sc)
+    ctx.build(grid=(8, 8, 4))
+    rep = ctx.mlp_train(sc.glass_materials()[0], seed=7)
+    specs = scenes.facade_renders(sc)   # 16 x 1920x1080 x 64 spp, depth 8
+    assert len(specs) == 16 and specs[0].n_paths == 1920 * 1080 * 64
+    t0 = time.perf_counter()
+    imgs, st = ctx.render(specs, method="ddm", bsdf="mlp")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    seg = st["segments_ext"] + st["segments_shadow"]
+    print(f"facade full: surrogate loss {rep['final_loss']:.2e}; {st['paths']} paths, {seg} segments, "
+          f"{st['gpu_ms']:.0f} ms device ({seg / (st['gpu_ms'] * 1e3):.0f} Mseg/s), {wall:.1f} s wall, "
+          f"{st['mlp_fallbacks']} fallback batches of {st['glass_queries']} glass queries")
+    orc = oracle_mod.Oracle(sc)
+    errs = []
+    for r, sp in enumerate(specs):
+        pix = scenes.pixel_subset(sp.width, sp.height, 128, seed=100 + r)
+        ref = orc.render_pixels(sp, pix)["xyz"]
+        errs.append(rel_rmse(imgs[r].cpu().numpy().reshape(-1, 3)[pix], ref))
+    print("per-render rel-RMSE max %.2e mean %.2e" % (max(errs), sum(errs) / len(errs)))
+    assert max(errs) <= 1e-3
+    ctx.close()

@@ -104,7 +104,10 @@ def test_inference_matches_fp64_network(oracle_mod, sddm, room41):
     d = rng.uniform(0.002, 0.010, n).astype(np.float32)
     R, T = ctx.glass_eval(g, *(torch.from_numpy(a).cuda() for a in (c, b, s, d)), mode="mlp_raw")
     got = np.stack([R.cpu().numpy(), T.cpu().numpy()], 1)
-    X = np.array([oracle_mod.mlp_features(c[i], room41.lam[b[i]], s[i], d[i]) for i in range(n)])
+    gm = room41.materials[g]
+    ac, da = np.asarray(gm.alpha_clear, np.float32), np.asarray(gm.dalpha, np.float32)
+    X = np.array([oracle_mod.mlp_features(c[i], room41.lam[b[i]], s[i], d[i], ac[b[i]] + s[i] * da[b[i]])
+                  for i in range(n)])
     want = oracle_mod.mlp_forward(p, X)
     err = np.abs(got - want)
     # BF16 (8-bit significand) rounding of three activation layers and the weights: a few 1e-3 absolute

@@ -33,9 +33,28 @@ def test_backprop_matches_central_differences(oracle_mod):
 
 
 def test_feature_map_box_corners(oracle_mod):
-    assert np.allclose(oracle_mod.mlp_features(1.0, 780.0, 1.0, 0.010), [1, 1, 1, 1], atol=1e-12)
-    assert np.allclose(oracle_mod.mlp_features(0.0, 380.0, 0.0, 0.002), [-1, -1, -1, -1], atol=1e-12)
-    assert np.allclose(oracle_mod.mlp_features(0.5, 580.0, 0.5, 0.006), [0, 0, 0, 0], atol=1e-12)
+    # no absorption: transmittance 1; opaque (alpha d = 100): transmittance ~ 0;
+    # alpha d = ln 2: transmittance 1/2, the middle of the range
+    assert np.allclose(oracle_mod.mlp_features(1.0, 780.0, 1.0, 0.010, 0.0), [1, 1, 1, 1], atol=1e-12)
+    assert np.allclose(oracle_mod.mlp_features(0.0, 380.0, 0.0, 0.002, 5e4), [-1, -1, -1, -1], atol=1e-12)
+    assert np.allclose(oracle_mod.mlp_features(0.5, 580.0, 0.5, 0.006, np.log(2.0) / 0.006), [0, 0, 0, 0],
+                       atol=1e-12)
+
+
+def test_feature_transmittance_is_beer_lambert(oracle_mod):
+    """x3 is 2 T_int - 1 with T_int the internal transmittance of the slab at
+    normal incidence: halving the thickness takes its square root, and for a
+    material law alpha = alpha_clear + s dalpha it falls with s as
+    exp(-s dalpha d)."""
+    for ad in (0.05, 0.7, 3.0):
+        t_full = (oracle_mod.mlp_features(0.3, 500.0, 0.2, 0.008, ad / 0.008)[3] + 1) / 2
+        t_half = (oracle_mod.mlp_features(0.3, 500.0, 0.2, 0.004, ad / 0.008)[3] + 1) / 2
+        assert abs(t_half - np.sqrt(t_full)) <= 1e-12
+    ac, da, d = 20.0, 400.0, 0.004
+    t0 = (oracle_mod.mlp_features(0.5, 600.0, 0.0, d, ac)[3] + 1) / 2
+    for s in (0.25, 0.5, 1.0):
+        ts = (oracle_mod.mlp_features(0.5, 600.0, s, d, ac + s * da)[3] + 1) / 2
+        assert abs(ts / t0 - np.exp(-s * da * d)) <= 1e-12
 
 
 def test_constant_networks(oracle_mod):
