@@ -63,5 +63,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))
+    # --force: rebuild; --ptxas: print register/spill use; -DNAME=VALUE: compile-time
+    # kernel options (e.g. -DSDDM_TRACE_MIN_BLOCKS=10 -DSDDM_TRACE_SPEC=1)
+    extra = (["-Xptxas", "-v"] if "--ptxas" in sys.argv else []) + [a for a in sys.argv[1:] if a.startswith("-D")]
+    print(build(force="--force" in sys.argv or any(a.startswith("-D") for a in sys.argv[1:]), verbose=True,
+                extra=extra))

@@ -126,48 +126,117 @@ __device__ __forceinline__ float cell_exit(const DDMScene &g, int cell, V3 o, V3
     return t;
 }
 
-// Warp-aggregated append of rays to the staging area. All 32 lanes call it.
-__device__ __forceinline__ void stage_push(const Queues &Q, bool want, int cell, float4 r0, float4 r1, int4 r2,
-                                           int *err) {
-    const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, want);
-    if (m == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(Q.ctl + 0, (unsigned long long)__popc(m));
-    base = __shfl_sync(full, base, leader);
-    if (want) {
-        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
-        if (slot < (unsigned long long)Q.cap) {
-            float4 *dst = Q.stage + 3 * slot;
-            dst[0] = r0;
-            dst[1] = r1;
-            dst[2] = make_float4(__int_as_float(r2.x), __int_as_float(r2.y), __int_as_float(r2.z),
-                                 __int_as_float(r2.w));
-        } else {
-            atomicCAS(err, 0, 1);
-        }
-        const int bin = 2 * cell + (r2.z & kRayShadow);   // sort key: cell, then ray kind
-        const unsigned peers = __match_any_sync(m, bin);
-        if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + bin, __popc(peers));
+// Block-aggregated append of up to two rays per thread (an extension ray e
+// and a shadow ray s): one global atomic per block and call on the staging
+// cursor instead of one per warp and ray, so that thousands of warps do not
+// serialise on one counter. All threads of the block call it together.
+struct PushSmem {
+    int warp_off[32];
+    unsigned long long base;
+};
+
+__device__ __forceinline__ void put_ray(const Queues &Q, unsigned long long slot, float4 r0, float4 r1, int4 r2,
+                                        int *err) {
+    if (slot < (unsigned long long)Q.cap) {
+        float4 *dst = Q.stage + 3 * slot;
+        dst[0] = r0;
+        dst[1] = r1;
+        dst[2] = make_float4(__int_as_float(r2.x), __int_as_float(r2.y), __int_as_float(r2.z), __int_as_float(r2.w));
+    } else {
+        atomicCAS(err, 0, 1);
     }
 }
 
-__device__ __forceinline__ void warp_count(unsigned long long *ctr, unsigned long long v) {
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(ctr, v);
+__device__ __forceinline__ void block_stage_push2(const Queues &Q, PushSmem &sm, int *bins, bool we, int ce, float4 e0,
+                                                  float4 e1, int4 e2, bool ws, int cs, float4 s0, float4 s1, int4 s2,
+                                                  int *err) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned me = __ballot_sync(full, we), ms = __ballot_sync(full, ws);
+    if (lane == 0) sm.warp_off[w] = __popc(me) + __popc(ms);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const int c = sm.warp_off[k];
+            sm.warp_off[k] = tot;
+            tot += c;
+        }
+        sm.base = tot ? atomicAdd(Q.ctl + 0, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long base = sm.base + (unsigned long long)sm.warp_off[w];
+    __syncthreads();   // the next call rewrites warp_off and base
+    if (we) {
+        put_ray(Q, base + __popc(me & lt), e0, e1, e2, err);
+        const int bin = 2 * ce + (e2.z & kRayShadow);
+        const unsigned peers = __match_any_sync(me, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
+    }
+    if (ws) {
+        put_ray(Q, base + __popc(me) + __popc(ms & lt), s0, s1, s2, err);
+        const int bin = 2 * cs + (s2.z & kRayShadow);
+        const unsigned peers = __match_any_sync(ms, bin);
+        if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
+    }
+}
+
+// Per-block (cell, kind) ray counts in shared memory (2 * n_cells ints of
+// dynamic shared memory), added to the global counts once per block.
+__device__ __forceinline__ int *block_bins_init(int n_bins) {
+    extern __shared__ int s_bins[];
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x) s_bins[i] = 0;
+    __syncthreads();
+    return s_bins;
+}
+
+__device__ __forceinline__ void block_bins_flush(const Queues &Q, const int *bins, int n_bins) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_bins; i += blockDim.x)
+        if (bins[i]) atomicAdd(Q.cnt + i, bins[i]);
+}
+
+// Block-wide sums of up to three statistics counters, one atomic per counter
+// and block. All threads of the block call it.
+__device__ __forceinline__ void block_count3(unsigned long long *c0, unsigned long long v0, unsigned long long *c1,
+                                             unsigned long long v1, unsigned long long *c2, unsigned long long v2) {
+    __shared__ unsigned long long s_red[32][3];
+    for (int off = 16; off > 0; off >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, off);
+        v1 += __shfl_down_sync(0xffffffffu, v1, off);
+        v2 += __shfl_down_sync(0xffffffffu, v2, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_red[w][0] = v0;
+        s_red[w][1] = v1;
+        s_red[w][2] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t0 = 0, t1 = 0, t2 = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t0 += s_red[k][0];
+            t1 += s_red[k][1];
+            t2 += s_red[k][2];
+        }
+        if (c0 && t0) atomicAdd(c0, t0);
+        if (c1 && t1) atomicAdd(c1, t1);
+        if (c2 && t2) atomicAdd(c2, t2);
+    }
 }
 
 // --------------------------------------------------------- camera rays
 __global__ void __launch_bounds__(256) k_camera(KArgs a) {
-    const int lane = threadIdx.x & 31;
     const int64_t np = a.ps.np;
     const int L = a.sc.L;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long n_ext = 0;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-        const int64_t q = base + lane;
+    __shared__ PushSmem psm;
+    int *bins = block_bins_init(2 * a.g.n_cells);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
+        const int64_t q = base + threadIdx.x;
         bool want = false;
         int cell = 0;
         float4 r0 = make_float4(0, 0, 0, 0), r1 = r0;
@@ -200,9 +269,10 @@ __global__ void __launch_bounds__(256) k_camera(KArgs a) {
                 a.ps.hit1[q] = make_float4(d.x, d.y, d.z, 0.f);
             }
         }
-        stage_push(a.Q, want, cell, r0, r1, r2, a.err);
+        block_stage_push2(a.Q, psm, bins, want, cell, r0, r1, r2, false, 0, r0, r1, r2, a.err);
     }
-    warp_count(a.counters + 0, n_ext);
+    block_bins_flush(a.Q, bins, 2 * a.g.n_cells);
+    block_count3(a.counters + 0, n_ext, nullptr, 0, nullptr, 0);
 }
 
 // ------------------------------------------------------ sort by cell
@@ -298,6 +368,26 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
 #define SDDM_TRACE_STEPS 64   // interior steps per round at most
 #endif
 constexpr int kTraceSteps = SDDM_TRACE_STEPS;
+// Queue slots a warp reserves per refill atomic (>= 32, so one run always covers a refill).
+constexpr int kRefillChunk = 32;
+// Rays a warp buffers in shared memory before appending them to the staging area.
+constexpr int kPushBuf = 32;
+
+// Append a warp's buffered rays to the staging area: one atomic, then the
+// warp copies the 3 * n float4 words with consecutive lanes on consecutive words.
+__device__ __forceinline__ void flush_push_buf(const Queues &Q, const float4 *buf, int n, int lane, int *err) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(Q.ctl + 0, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    if (base + (unsigned long long)n > (unsigned long long)Q.cap) {
+        if (lane == 0) atomicCAS(err, 0, 1);
+        return;
+    }
+    float4 *dst = Q.stage + 3 * base;
+    for (int k = lane; k < 3 * n; k += 32) dst[k] = buf[k];
+    __syncwarp();
+}
 // Resident 128-thread blocks per SM the trace kernel is compiled for (register budget).
 #ifndef SDDM_TRACE_MIN_BLOCKS
 #define SDDM_TRACE_MIN_BLOCKS 8
@@ -316,8 +406,15 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
     unsigned long long n_cross = 0, n_vis = 0;
     TravCount tc;
 
+    __shared__ float4 s_push[128 / 32][3 * kPushBuf];   // per-warp hand-off buffers
+    float4 *pbuf = s_push[threadIdx.x >> 5];
+    int nbuf = 0;              // rays in the warp's buffer (uniform)
     int idx = -1;              // queue index of this lane's ray, -1 = none
     bool exhausted = false;    // no ray left for this lane
+    __shared__ unsigned long long s_run[128 / 32][2];    // per warp: reserved run [begin, end) of queue slots
+    unsigned long long *run = s_run[threadIdx.x >> 5];
+    if (lane == 0) run[0] = run[1] = 0;
+    __syncwarp();
     Ray ray;
     float t_cur = 0.f, t_max = 0.f, t_exit = 0.f, tmin = 0.f, tw = 0.f;
     int q = 0, excl = -1, rfl = 0, next = -1, node = 0, sp = 0, best = -1, ep = -1, eo = -1, n_prev = 0;
@@ -327,16 +424,34 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
     int stack[kStackSize];
 
     for (;;) {
-        // 1. idle lanes take the next rays of the queue
+        // 1. idle lanes take the next rays of the queue, from a run of
+        //    kRefillChunk queue slots the warp reserves at a time (one atomic
+        //    per run instead of one per refill)
         const bool need = idx < 0 && !exhausted;
         const unsigned m = __ballot_sync(full, need);
         if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(Q.ctl + 1, (unsigned long long)__popc(m));
-            base = __shfl_sync(full, base, leader);
+            const unsigned want = __popc(m);
+            const unsigned long long cbeg = run[0], cend = run[1];
+            const unsigned long long avail = cend - cbeg;
+            unsigned long long nb = 0;
+            if (avail < want) {
+                if (lane == 0) nb = atomicAdd(Q.ctl + 1, (unsigned long long)kRefillChunk);
+                nb = __shfl_sync(full, nb, 0);
+            }
+            const unsigned rank = __popc(m & lt_mask);
+            const unsigned long long mine = rank < avail ? cbeg + rank : nb + (rank - avail);
+            __syncwarp();
+            if (lane == 0) {
+                if (avail >= want) {
+                    run[0] = cbeg + want;
+                } else {
+                    run[0] = nb + (want - avail);
+                    run[1] = nb + kRefillChunk;
+                }
+            }
+            __syncwarp();
             if (need) {
-                const unsigned long long my = base + __popc(m & lt_mask);
+                const unsigned long long my = mine;
                 if (my < (unsigned long long)total) {
                     idx = (int)my;
                     const float4 *src = Q.in + 3 * (size_t)idx;
@@ -501,13 +616,34 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
             atomicCAS(a.err, 0, 4);
             want = false;
         }
-        stage_push(Q, want, next, o0, o1, o2, a.err);
+        // hand-off: append to the warp's buffer, flushing it to the staging
+        // area (one atomic, coalesced stores) when the new rays do not fit
+        const unsigned mw = __ballot_sync(full, want);
+        if (mw) {
+            const int n = __popc(mw);
+            if (nbuf + n > kPushBuf) {
+                flush_push_buf(Q, pbuf, nbuf, lane, a.err);
+                nbuf = 0;
+            }
+            if (want) {
+                float4 *slot = pbuf + 3 * (nbuf + __popc(mw & lt_mask));
+                slot[0] = o0;
+                slot[1] = o1;
+                slot[2] = make_float4(__int_as_float(o2.x), __int_as_float(o2.y), __int_as_float(o2.z),
+                                      __int_as_float(o2.w));
+                const int bin = 2 * next + (o2.z & kRayShadow);
+                const unsigned peers = __match_any_sync(mw, bin);
+                if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + bin, __popc(peers));
+            }
+            nbuf += n;
+            __syncwarp();
+        }
     }
-    warp_count(a.counters + 3, n_cross);
+    if (nbuf > 0) flush_push_buf(Q, pbuf, nbuf, lane, a.err);
+    block_count3(a.counters + 3, n_cross, nullptr, 0, nullptr, 0);
     if (COUNT) {
-        warp_count(a.counters + 5, tc.nodes);
-        warp_count(a.counters + 6, tc.tris);
-        warp_count(a.counters + 7, n_vis);
+        __syncthreads();
+        block_count3(a.counters + 5, tc.nodes, a.counters + 6, tc.tris, a.counters + 7, n_vis);
     }
 }
 
@@ -633,7 +769,6 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
 // Spectral half of shading: resolve the previous vertex's shadow ray, apply its
 // weight, add this vertex's emission, per bin, with compensated sums.
 __global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
-    const int lane = threadIdx.x & 31;
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
     const int L = sc.L;
@@ -641,8 +776,8 @@ __global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long n_glass = 0;
     const PathState &ps = a.ps;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-        const int64_t q = base + lane;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
+        const int64_t q = base + threadIdx.x;
         int fl = q < np ? ps.flags[q] : 0;
         if (fl & (kFlExt | kFlShadow)) {
             const int64_t gp = a.path_begin + q;
@@ -789,13 +924,12 @@ __global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
             }
         }
     }
-    warp_count(a.counters + 2, n_glass);
+    block_count3(a.counters + 2, n_glass, nullptr, 0, nullptr, 0);
 }
 
 // Continuation half of shading: next-event sample toward the lights and the
 // next direction at this vertex, appended to the ray staging area.
 __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
-    const int lane = threadIdx.x & 31;
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
     const int L = sc.L;
@@ -803,8 +937,10 @@ __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long n_ext = 0, n_sh = 0, n_glass = 0;
     const PathState &ps = a.ps;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < np; base += stride) {
-        const int64_t q = base + lane;
+    __shared__ PushSmem psm;
+    int *bins = block_bins_init(2 * a.g.n_cells);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
+        const int64_t q = base + threadIdx.x;
         bool want_e = false, want_s = false;
         int cell_e = 0, cell_s = 0;
         float4 e0 = make_float4(0, 0, 0, 0), e1 = e0, s0 = e0, s1 = e0;
@@ -937,12 +1073,10 @@ __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
             }
             ps.flags[q] = nfl;
         }
-        stage_push(a.Q, want_e, cell_e, e0, e1, e2, a.err);
-        stage_push(a.Q, want_s, cell_s, s0, s1, s2, a.err);
+        block_stage_push2(a.Q, psm, bins, want_e, cell_e, e0, e1, e2, want_s, cell_s, s0, s1, s2, a.err);
     }
-    warp_count(a.counters + 0, n_ext);
-    warp_count(a.counters + 1, n_sh);
-    warp_count(a.counters + 2, n_glass);
+    block_bins_flush(a.Q, bins, 2 * a.g.n_cells);
+    block_count3(a.counters + 0, n_ext, a.counters + 1, n_sh, a.counters + 2, n_glass);
 }
 
 __global__ void k_finalize(KArgs a) {
@@ -1078,7 +1212,8 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
     a.b = 0;
     a.last_wave = 0;
-    k_camera<<<path_blocks, 256, 0, s>>>(a);
+    const size_t bins_smem = sizeof(int) * 2 * (size_t)nc;
+    k_camera<<<path_blocks, 256, bins_smem, s>>>(a);
     DDM_CHECK(cudaGetLastError());
     for (int b = 1; b <= run.max_depth + 1; ++b) {
         for (int w = 0; w < waves; ++w) {
@@ -1115,7 +1250,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
         }
         k_shade_spectral<<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
-        k_shade_continue<<<path_blocks, 256, 0, s>>>(a);
+        k_shade_continue<<<path_blocks, 256, bins_smem, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         *run.launches += 2;
     }
