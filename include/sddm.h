@@ -225,7 +225,8 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
  * incidence internal transmittance 2 exp(-alpha(lambda, s) d) - 1 with the
  * material's alpha = alpha_clear + s dalpha; the trained box is cos in [0,1],
  * lambda in [380,780] nm, s in [0,1], d in [thick_min, thick_max]; 3 hidden
- * layers of 64 SiLU units; outputs (R, T).
+ * layers of 64 SiLU units; 2 outputs y, served as R = max(exp(y0) - 1e-3, 0),
+ * T = max(exp(y1) - 1e-3, 0) (trained on log(R + 1e-3), log(T + 1e-3)).
  * Weights and activations are BF16 with FP32 accumulation and FP32 master
  * weights; parameters in this order (8770 floats): W1[64][4], b1[64],
  * W2[64][64], b2[64], W3[64][64], b3[64], W4[2][64], b4[2]. */
@@ -242,7 +243,7 @@ typedef struct {
 } sddm_mlp_train_opts;
 
 typedef struct {
-    double final_loss;        /* mean squared error of the last batch */
+    double final_loss;        /* mean squared error of the last batch, in the network's log(. + 1e-3) outputs */
     double max_abs_err_R;     /* on a held-out grid of the trained box, vs the exact slab */
     double max_abs_err_T;
     double train_ms;          /* device time of the training steps */

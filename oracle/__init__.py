@@ -101,6 +101,7 @@ def _load():
         lib.orc_mlp_n_params.restype = C.c_int
         lib.orc_mlp_features.argtypes = [C.c_double] * 5 + [P]
         lib.orc_mlp_forward.argtypes = [P, P, P]
+        lib.orc_mlp_rt.argtypes = [P, P, P]
         lib.orc_mlp_forward_d.argtypes = [P, P, P]
         lib.orc_mlp_loss_grad.argtypes = [P, C.c_int, P, P, P]
         lib.orc_mlp_loss_grad.restype = C.c_double
@@ -169,6 +170,17 @@ def mlp_features(c, lam_nm, s, d, alpha):
     x = np.zeros(4)
     _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), float(alpha), _ptr(x))
     return x
+
+
+def mlp_rt(params, X):
+    """Served (R, T) of the surrogate for rows X [n,4]: exp(y) - 1e-3, clamped at 0."""
+    lib = _load()
+    X = np.ascontiguousarray(np.atleast_2d(X), np.float64)
+    p = np.ascontiguousarray(params, np.float32)
+    out = np.zeros((X.shape[0], 2))
+    for i in range(X.shape[0]):
+        lib.orc_mlp_rt(_ptr(p), _ptr(X[i]), _ptr(out[i]))
+    return out
 
 
 def mlp_forward(params, X):

@@ -11,6 +11,8 @@
  * where alpha = alpha_clear(lambda) + s dalpha(lambda) is the material's
  * absorption coefficient (1/m) at the coloration state s, so that x3 carries
  * the thickness as the slab's internal transmittance at normal incidence.
+ * The two outputs y are log(R + 1e-3) and log(T + 1e-3); the served values are
+ * R = max(exp(y0) - 1e-3, 0), T = max(exp(y1) - 1e-3, 0) (orc_mlp_rt).
  * Parameters, in this order (8770 floats): W1[64][4], b1[64], W2[64][64], b2[64],
  * W3[64][64], b3[64], W4[2][64], b4[2]; layer l computes z = W h + b.
  * Loss: mean over the batch and both outputs of the squared error.
@@ -183,4 +185,15 @@ double orc_mlp_loss_grad(const float *params, int n, const double *X, const doub
     double l = orc_mlp_loss_grad_d(d, n, X, Tgt, grad);
     free(d);
     return l;
+}
+
+/* Served (R, T) of the network at inputs x: the output map of the header. */
+void orc_mlp_rt(const float *params, const double x[4], double rt[2])
+{
+    double y[2];
+    orc_mlp_forward(params, x, y);
+    for (int k = 0; k < 2; ++k) {
+        const double v = exp(y[k]) - 1e-3;
+        rt[k] = v > 0.0 ? v : 0.0;
+    }
 }

@@ -107,6 +107,7 @@ int orc_num_lights(void *ctx);
 int orc_mlp_n_params(void);
 void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double x[4]);
 void orc_mlp_forward(const float *params, const double x[4], double y[2]);
+void orc_mlp_rt(const float *params, const double x[4], double rt[2]);
 void orc_mlp_forward_d(const double *params, const double x[4], double y[2]);
 double orc_mlp_loss_grad(const float *params, int n, const double *X, const double *Tgt, double *grad);
 double orc_mlp_loss_grad_d(const double *params, int n, const double *X, const double *Tgt, double *grad);

@@ -73,6 +73,13 @@ __device__ __forceinline__ void zero_acc(float acc[8][4]) {
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
 }
 
+// The network predicts log(R + eps) and log(T + eps): a fixed error there is a
+// fixed relative error of R and T well above eps, so a dark pane's small T and
+// a near-normal reflectance keep their relative accuracy.
+constexpr float kOutEps = 1e-3f;
+__device__ __forceinline__ float out_to_rt(float y) { return fmaxf(expf(y) - kOutEps, 0.0f); }
+__device__ __forceinline__ float rt_to_out(float v) { return logf(v + kOutEps); }
+
 // Network inputs from (cos, lambda, s, thickness): cos and s mapped to [-1, 1],
 // lambda over 380-780 nm to [-1, 1], and the thickness through the slab's
 // internal transmittance at normal incidence, exp(-alpha(lambda, s) d) mapped
@@ -274,8 +281,8 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
             features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
             tile_forward(s, act[w], xl, xh, lane, yl, yh);
             if (t == 0) {
-                out[w][kl] = make_float2(yl[0], yl[1]);
-                out[w][kh] = make_float2(yh[0], yh[1]);
+                out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
+                out[w][kh] = make_float2(out_to_rt(yh[0]), out_to_rt(yh[1]));
             }
         }
         __syncwarp();
@@ -642,8 +649,8 @@ __global__ void k_mlp_data(DevScene sc, uint32_t mat, int64_t n, uint32_t seed, 
     float x[4];
     features(c, lam, st, (ac + st * da) * d, x);
     for (int k = 0; k < 4; ++k) X[4 * i + k] = x[k];
-    Y[2 * i] = R_;
-    Y[2 * i + 1] = T_;
+    Y[2 * i] = rt_to_out(R_);
+    Y[2 * i + 1] = rt_to_out(T_);
 }
 
 // Xavier-uniform initial weights from Philox, zero biases.
@@ -697,8 +704,10 @@ __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
         tile_forward(s, act[w], xl, xh, lane, yl, yh);
         if (t == 0) {
             const float2 el = exact_row(a, il), eh = exact_row(a, ih);
-            atomicMax(max_err + 0, __float_as_uint(fmaxf(fabsf(el.x - yl[0]), fabsf(eh.x - yh[0]))));
-            atomicMax(max_err + 1, __float_as_uint(fmaxf(fabsf(el.y - yl[1]), fabsf(eh.y - yh[1]))));
+            atomicMax(max_err + 0,
+                      __float_as_uint(fmaxf(fabsf(el.x - out_to_rt(yl[0])), fabsf(eh.x - out_to_rt(yh[0])))));
+            atomicMax(max_err + 1,
+                      __float_as_uint(fmaxf(fabsf(el.y - out_to_rt(yl[1])), fabsf(eh.y - out_to_rt(yh[1])))));
         }
         __syncwarp();
     }

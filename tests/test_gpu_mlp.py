@@ -103,15 +103,16 @@ def test_inference_matches_fp64_network(oracle_mod, sddm, room41):
     s = rng.uniform(0, 1, n).astype(np.float32)
     d = rng.uniform(0.002, 0.010, n).astype(np.float32)
     R, T = ctx.glass_eval(g, *(torch.from_numpy(a).cuda() for a in (c, b, s, d)), mode="mlp_raw")
-    got = np.stack([R.cpu().numpy(), T.cpu().numpy()], 1)
+    got = np.stack([R.cpu().numpy(), T.cpu().numpy()], 1).astype(np.float64)
     gm = room41.materials[g]
     ac, da = np.asarray(gm.alpha_clear, np.float32), np.asarray(gm.dalpha, np.float32)
     X = np.array([oracle_mod.mlp_features(c[i], room41.lam[b[i]], s[i], d[i], ac[b[i]] + s[i] * da[b[i]])
                   for i in range(n)])
-    want = oracle_mod.mlp_forward(p, X)
-    err = np.abs(got - want)
+    want = oracle_mod.mlp_rt(p, X)
     # BF16 (8-bit significand) rounding of three activation layers and the weights: a few 1e-3 absolute
-    assert err.max() < 2.5e-2 and err.mean() < 5e-3, (err.max(), err.mean())
+    # in the network's log outputs, i.e. relative in the served exp(y) - 1e-3
+    err = np.abs(got - want) / (want + 1e-3)
+    assert err.max() < 3e-2 and err.mean() < 5e-3, (err.max(), err.mean())
     ctx.close()
 
 
@@ -120,7 +121,7 @@ def test_trained_surrogate_accuracy(sddm, room41, trained):
     values look like once the per-batch probe sends bad batches to the exact slab."""
     ctx, g, rep = trained
     assert rep["steps"] == 20000
-    assert rep["final_loss"] < 1e-4, rep
+    assert rep["final_loss"] < 1e-3, rep   # mean squared error of log(R + 1e-3), log(T + 1e-3)
     assert rep["max_abs_err_R"] < 0.15 and rep["max_abs_err_T"] < 0.15, rep
     # random points of the trained box, raw network vs exact slab
     rng = np.random.default_rng(33)

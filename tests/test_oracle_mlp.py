@@ -74,3 +74,18 @@ def test_constant_networks(oracle_mod):
     loss, g = oracle_mod.mlp_loss_grad(p, X, np.zeros((5, 2)))
     assert abs(loss - (want ** 2).mean()) < 1e-9
     assert np.all(g[:8576] == 0.0)       # nothing reaches the constant layers' weights
+
+
+def test_served_output_map(oracle_mod):
+    """Served (R, T) = exp(y) - 1e-3 clamped at 0: a constant network whose
+    output biases are log(v + 1e-3) serves exactly v; outputs below log(1e-3)
+    serve 0."""
+    p = np.zeros(oracle_mod.MLP_PARAMS, np.float32)
+    X = np.random.default_rng(5).uniform(-1, 1, (4, 4))
+    for R, T in ((0.25, 0.5), (0.04, 0.9), (1.0, 0.0)):
+        p[8768], p[8769] = np.log(R + 1e-3), np.log(T + 1e-3)
+        rt = oracle_mod.mlp_rt(p, X)
+        # the float32 biases round log(v + 1e-3) to 2^-24 relative
+        assert np.allclose(rt, [[R, T]] * 4, rtol=1e-6, atol=1e-9)
+    p[8768], p[8769] = np.log(5e-4), np.log(1e-6)
+    assert np.array_equal(oracle_mod.mlp_rt(p, X), np.zeros((4, 2)))
