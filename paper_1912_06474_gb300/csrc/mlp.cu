@@ -32,8 +32,19 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&v);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float sigm(float z) { return __frcp_rn(1.0f + __expf(-z)); }
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// sigmoid(z) = (1 + tanh(z / 2)) / 2 with the hardware tanh (tanh.approx.f32,
+// one SFU operation, relative error about 2^-11 -- below the BF16 rounding the
+// activations take next); SiLU(z) = z sigmoid(z) = h + h tanh(h), h = z / 2.
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
+__device__ __forceinline__ float silu(float z) {
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_fast(h), h);
+}
 __device__ __forceinline__ float dsilu(float z) {
     const float g = sigm(z);
     return g * fmaf(z, 1.0f - g, 1.0f);
@@ -718,7 +729,7 @@ __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
 size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
-    const int blocks = sm_count * 2;
+    const int blocks = sm_count * 4;
     k_mlp_rows<<<blocks, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
