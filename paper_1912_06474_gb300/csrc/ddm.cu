@@ -102,29 +102,63 @@ __device__ __forceinline__ bool grid_enter(const DDMScene &g, V3 o, V3 d, float 
 }
 
 // Distance at which the ray leaves `cell`, and the neighbour it enters
-// (-1 when it leaves the grid). Ties between faces go x, then y, then z.
-__device__ __forceinline__ float cell_exit(const DDMScene &g, int cell, V3 o, V3 d, int &next) {
-    int c[3] = {cell % g.dims[0], (cell / g.dims[0]) % g.dims[1], cell / (g.dims[0] * g.dims[1])};
-    const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+// (-1 when it leaves the grid). Ties between faces go x, then y, then z. The
+// cell's planes and neighbours come from the per-cell table; distances use
+// the ray's reciprocal direction.
+__device__ __forceinline__ float cell_exit(const DDMScene &g, int cell, const Ray &r, int &next) {
+    const float4 p0 = __ldg(g.cell_planes + 2 * cell), p1 = __ldg(g.cell_planes + 2 * cell + 1);
+    const int4 n0 = __ldg(g.cell_next + 2 * cell), n1 = __ldg(g.cell_next + 2 * cell + 1);
     float t = __int_as_float(0x7f800000);
-    int axis = -1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (dd[a] == 0.0f) continue;
-        float plane = g.lo[a] + (float)(dd[a] > 0.0f ? c[a] + 1 : c[a]) * g.cell[a];
-        float ta = (plane - oo[a]) / dd[a];
+    next = -1;
+    if (r.d.x != 0.0f) {
+        const bool pos = r.d.x > 0.0f;
+        const float ta = ((pos ? p0.y : p0.x) - r.o.x) * r.inv.x;
         if (ta < t) {
             t = ta;
-            axis = a;
+            next = pos ? n0.y : n0.x;
         }
     }
-    next = -1;
-    if (axis >= 0) {
-        c[axis] += dd[axis] > 0.0f ? 1 : -1;
-        if (c[axis] >= 0 && c[axis] < g.dims[axis]) next = (c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
+    if (r.d.y != 0.0f) {
+        const bool pos = r.d.y > 0.0f;
+        const float ta = ((pos ? p0.w : p0.z) - r.o.y) * r.inv.y;
+        if (ta < t) {
+            t = ta;
+            next = pos ? n0.w : n0.z;
+        }
+    }
+    if (r.d.z != 0.0f) {
+        const bool pos = r.d.z > 0.0f;
+        const float ta = ((pos ? p1.y : p1.x) - r.o.z) * r.inv.z;
+        if (ta < t) {
+            t = ta;
+            next = pos ? n1.y : n1.x;
+        }
     }
     return t;
 }
+
+// Per-cell planes and face neighbours (one thread per cell).
+__global__ void k_cell_table(DDMScene g, float4 *planes, int4 *next) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= g.n_cells) return;
+    const int c[3] = {cell % g.dims[0], (cell / g.dims[0]) % g.dims[1], cell / (g.dims[0] * g.dims[1])};
+    float lo[3], hi[3];
+    int nb[3][2];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = g.lo[a] + (float)c[a] * g.cell[a];
+        hi[a] = g.lo[a] + (float)(c[a] + 1) * g.cell[a];
+        for (int s = 0; s < 2; ++s) {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[a] += s ? 1 : -1;
+            nb[a][s] = (cc[a] >= 0 && cc[a] < g.dims[a]) ? (cc[2] * g.dims[1] + cc[1]) * g.dims[0] + cc[0] : -1;
+        }
+    }
+    planes[2 * cell] = make_float4(lo[0], hi[0], lo[1], hi[1]);
+    planes[2 * cell + 1] = make_float4(lo[2], hi[2], 0.0f, 0.0f);
+    next[2 * cell] = make_int4(nb[0][0], nb[0][1], nb[1][0], nb[1][1]);
+    next[2 * cell + 1] = make_int4(nb[2][0], nb[2][1], -1, -1);
+}
+
 
 // Block-aggregated append of up to two rays per thread (an extension ray e
 // and a shadow ray s): one global atomic per block and call on the staging
@@ -463,7 +497,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                     ray = make_ray(xyz(r0), xyz(r1));
                     t_cur = r0.w;
                     t_max = r1.w;
-                    t_exit = cell_exit(g, cell, ray.o, ray.d, next);
+                    t_exit = cell_exit(g, cell, ray, next);
                     tmin = fmaxf(0.0f, t_cur - g.eps);
                     node = __ldg(g.root + cell);
                     sp = 0;
@@ -768,7 +802,14 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
 
 // Spectral half of shading: resolve the previous vertex's shadow ray, apply its
 // weight, add this vertex's emission, per bin, with compensated sums.
-__global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
+#ifndef SDDM_SHS_MINB
+#define SDDM_SHS_MINB 4      // resident 256-thread blocks per SM the spectral pass is compiled for
+#endif
+#ifndef SDDM_SHS_UNROLL
+#define SDDM_SHS_UNROLL 4    // bins in flight per thread
+#endif
+constexpr int kShsUnroll = SDDM_SHS_UNROLL;
+__global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) {
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
     const int L = sc.L;
@@ -856,7 +897,7 @@ __global__ void __launch_bounds__(256, 4) k_shade_spectral(KArgs a) {
             const bool need_T = resolve || pend || emit;
             if (need_T) {
                 Kahan NX, NY, NZ, EX, EY, EZ;
-#pragma unroll 4
+#pragma unroll kShsUnroll
                 for (int i = 0; i < L; ++i) {
                     float t = ps.T[(size_t)i * np + q];
                     const float wx = __ldg(sc.wcmf + 3 * i), wy = __ldg(sc.wcmf + 3 * i + 1),
@@ -1259,6 +1300,11 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     *run.launches += 2;   // camera + finalize
 #undef DDM_CHECK
     return SDDM_OK;
+}
+
+cudaError_t build_cell_table(const DDMScene &g, float4 *planes, int4 *next, cudaStream_t stream) {
+    k_cell_table<<<(g.n_cells + 127) / 128, 128, 0, stream>>>(g, planes, next);
+    return cudaGetLastError();
 }
 
 }  // namespace sddm

@@ -728,8 +728,11 @@ __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
 
 size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 
+#ifndef SDDM_MLP_BLOCKS_PER_SM
+#define SDDM_MLP_BLOCKS_PER_SM 4   // inference blocks (8 warps, ~41 KB shared memory) per SM
+#endif
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
-    const int blocks = sm_count * 4;
+    const int blocks = sm_count * SDDM_MLP_BLOCKS_PER_SM;
     k_mlp_rows<<<blocks, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }

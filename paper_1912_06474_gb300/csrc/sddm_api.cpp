@@ -96,7 +96,7 @@ struct sddm_ctx {
     int n_light = 0;
     DevScene dev{};
     DDMScene ddm{};
-    DevBuf d_cell_nodes, d_cell_tris, d_cell_root;
+    DevBuf d_cell_nodes, d_cell_tris, d_cell_root, d_cell_planes, d_cell_next;
     // per-render scratch
     DevBuf d_info, d_state, d_out_tab, d_aov_xyz_tab, d_aov_prim_tab, d_samples, d_first, d_counters, d_err;
     DDMBuffers ddm_buf;
@@ -476,6 +476,15 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     g.nodes = ctx->d_cell_nodes.as<float4>();
     g.tris = ctx->d_cell_tris.as<float4>();
     g.root = ctx->d_cell_root.as<int>();
+    if ((e = ctx->d_cell_planes.ensure(sizeof(float4) * 2 * (size_t)g.n_cells)) ||
+        (e = ctx->d_cell_next.ensure(sizeof(int4) * 2 * (size_t)g.n_cells)))
+        return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_build: device allocation failed")
+                                              : cuda_fail(e, "sddm_build: cell table");
+    g.cell_planes = ctx->d_cell_planes.as<float4>();
+    g.cell_next = ctx->d_cell_next.as<int4>();
+    if ((e = build_cell_table(g, ctx->d_cell_planes.as<float4>(), ctx->d_cell_next.as<int4>(), s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "sddm_build: cell table");
     ctx->opts = o;
     ctx->built = true;
     ++ctx->build_id;

@@ -29,6 +29,10 @@ struct DDMScene {
     const float4 *nodes;  // all cells' BVH nodes
     const float4 *tris;   // all cells' triangle references
     const int *root;      // [n_cells] root node of each cell
+    // per cell: bounding planes (x-, x+, y-, y+), (z-, z+, -, -) and the
+    // neighbours across those faces (-1 outside the grid), 2 entries each
+    const float4 *cell_planes;
+    const int4 *cell_next;
 };
 
 // Path state of one chunk of np path slots (structure of arrays).
@@ -101,6 +105,9 @@ struct DDMRun {
 
 // Run every bounce of one chunk of paths (asynchronous on `stream`).
 int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t stream);
+// Fill g.cell_planes / g.cell_next (2 * n_cells entries each, device memory
+// the caller owns) from the grid's dims, lo and cell size.
+cudaError_t build_cell_table(const DDMScene &g, float4 *planes, int4 *next, cudaStream_t stream);
 cudaError_t check_kernel_image();
 
 }  // namespace sddm
