@@ -88,19 +88,21 @@ __device__ __forceinline__ void child_boxes(const Ray &r, float4 n0, float4 n1, 
 }
 
 // Moller-Trumbore, double sided: returns t of the plane hit inside the
-// triangle (u >= 0, v >= 0, u + v <= 1), or +inf.
+// triangle (u >= 0, v >= 0, u + v <= 1), or +inf. The barycentric tests run
+// on the unscaled numerators against |det| (signs folded in), so the divide
+// is taken only for triangles the ray actually crosses.
 __device__ __forceinline__ float mt_intersect(const Ray &r, V3 v0, V3 e1, V3 e2) {
-    V3 p = cross(r.d, e2);
-    float det = dot(e1, p);
+    const V3 p = cross(r.d, e2);
+    const float det = dot(e1, p);
     if (det == 0.0f) return __int_as_float(0x7f800000);
-    float inv = 1.0f / det;
-    V3 s = r.o - v0;
-    float u = dot(s, p) * inv;
-    if (u < 0.0f || u > 1.0f) return __int_as_float(0x7f800000);
-    V3 q = cross(s, e1);
-    float v = dot(r.d, q) * inv;
-    if (v < 0.0f || u + v > 1.0f) return __int_as_float(0x7f800000);
-    return dot(e2, q) * inv;
+    const float sgn = det > 0.0f ? 1.0f : -1.0f, adet = fabsf(det);
+    const V3 s = r.o - v0;
+    const float us = sgn * dot(s, p);
+    if (us < 0.0f || us > adet) return __int_as_float(0x7f800000);
+    const V3 q = cross(s, e1);
+    const float vs = sgn * dot(r.d, q);
+    if (vs < 0.0f || us + vs > adet) return __int_as_float(0x7f800000);
+    return dot(e2, q) / det;
 }
 
 struct Hit {

@@ -79,6 +79,34 @@ __device__ __forceinline__ void warp_gemm(float acc[8][4], const __nv_bfloat16 *
     }
 }
 
+// acc (16 x 64) += A (16 x 64) * W^T with A already in registers as mma
+// A fragments: fa[kk] holds rows g, g + 8 and columns 16 kk + 2t + {0, 1, 8, 9}
+// -- exactly the accumulator layout of the previous layer (see pack_afrag).
+__device__ __forceinline__ void warp_gemm_reg(float acc[8][4], const uint32_t fa[4][4], const __nv_bfloat16 *W,
+                                              int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t *bp = reinterpret_cast<const uint32_t *>(W + (8 * j + g) * LD + 16 * kk + 2 * t);
+            mma16816(acc[j], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], bp[0], bp[4]);
+        }
+    }
+}
+
+// Activations h (accumulator layout: h[j][0..1] row g, cols 8j + 2t + {0,1};
+// h[j][2..3] row g + 8) as BF16 A fragments of the next layer's mma.
+__device__ __forceinline__ void pack_afrag(const float h[8][4], uint32_t fa[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        fa[kk][0] = pack_bf16x2(h[2 * kk][0], h[2 * kk][1]);
+        fa[kk][1] = pack_bf16x2(h[2 * kk][2], h[2 * kk][3]);
+        fa[kk][2] = pack_bf16x2(h[2 * kk + 1][0], h[2 * kk + 1][1]);
+        fa[kk][3] = pack_bf16x2(h[2 * kk + 1][2], h[2 * kk + 1][3]);
+    }
+}
+
 __device__ __forceinline__ void zero_acc(float acc[8][4]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
@@ -127,13 +155,14 @@ __device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
 
 // The network on the 16 rows of a warp tile; this thread supplies the inputs
 // of rows g and g + 8 and receives their outputs (the same on the 4 lanes of
-// a group). act: the warp's 16 x LD staging tile.
-__device__ void tile_forward(const InferSmem &s, __nv_bfloat16 *act, const float xl[4], const float xh[4], int lane,
-                             float yl[2], float yh[2]) {
-    const int g = lane >> 2, t = lane & 3;
+// a group). Activations stay in registers: each layer's accumulators are
+// packed into the next layer's BF16 A fragments.
+__device__ void tile_forward(const InferSmem &s, const float xl[4], const float xh[4], int lane, float yl[2],
+                             float yh[2]) {
+    const int t = lane & 3;
+    float h[8][4];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        float hl[2], hh[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = 8 * j + 2 * t + e;
@@ -143,29 +172,26 @@ __device__ void tile_forward(const InferSmem &s, __nv_bfloat16 *act, const float
                 zl = fmaf(s.w1[4 * c + k], xl[k], zl);
                 zh = fmaf(s.w1[4 * c + k], xh[k], zh);
             }
-            hl[e] = silu(zl);
-            hh[e] = silu(zh);
+            h[j][e] = silu(zl);
+            h[j][2 + e] = silu(zh);
         }
-        *reinterpret_cast<uint32_t *>(act + g * LD + 8 * j + 2 * t) = pack_bf16x2(hl[0], hl[1]);
-        *reinterpret_cast<uint32_t *>(act + (g + 8) * LD + 8 * j + 2 * t) = pack_bf16x2(hh[0], hh[1]);
     }
-    __syncwarp();
+    uint32_t fa[4][4];
+    pack_afrag(h, fa);
     float acc[8][4];
     zero_acc(acc);
-    warp_gemm<H>(acc, act, s.w2, lane);
-    __syncwarp();
+    warp_gemm_reg(acc, fa, s.w2, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
-        *reinterpret_cast<uint32_t *>(act + g * LD + c) =
-            pack_bf16x2(silu(acc[j][0] + s.b2[c]), silu(acc[j][1] + s.b2[c + 1]));
-        *reinterpret_cast<uint32_t *>(act + (g + 8) * LD + c) =
-            pack_bf16x2(silu(acc[j][2] + s.b2[c]), silu(acc[j][3] + s.b2[c + 1]));
+        h[j][0] = silu(acc[j][0] + s.b2[c]);
+        h[j][1] = silu(acc[j][1] + s.b2[c + 1]);
+        h[j][2] = silu(acc[j][2] + s.b2[c]);
+        h[j][3] = silu(acc[j][3] + s.b2[c + 1]);
     }
-    __syncwarp();
+    pack_afrag(h, fa);
     zero_acc(acc);
-    warp_gemm<H>(acc, act, s.w3, lane);
-    __syncwarp();
+    warp_gemm_reg(acc, fa, s.w3, lane);
     float pl0 = 0.f, pl1 = 0.f, ph0 = 0.f, ph1 = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -248,7 +274,6 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
 // batch is evaluated exactly instead.
 __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
     __shared__ InferSmem s;
-    __shared__ __align__(16) __nv_bfloat16 act[8][16 * LD];
     __shared__ float2 out[8][32];
     load_infer_weights(s, a.params);
     __syncthreads();
@@ -290,7 +315,7 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
             float xl[4], xh[4], yl[2], yh[2];
             features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
             features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
-            tile_forward(s, act[w], xl, xh, lane, yl, yh);
+            tile_forward(s, xl, xh, lane, yl, yh);
             if (t == 0) {
                 out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
                 out[w][kh] = make_float2(out_to_rt(yh[0]), out_to_rt(yh[1]));
@@ -680,7 +705,6 @@ __global__ void k_mlp_init(float *p, uint32_t seed) {
 // Max |error| of R and T over a held-out grid of the trained box (cos, bin, s, d).
 __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
     __shared__ InferSmem s;
-    __shared__ __align__(16) __nv_bfloat16 act[8][16 * LD];
     load_infer_weights(s, a.params);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
@@ -712,7 +736,7 @@ __global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
         float xl[4], xh[4], yl[2], yh[2];
         features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
         features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
-        tile_forward(s, act[w], xl, xh, lane, yl, yh);
+        tile_forward(s, xl, xh, lane, yl, yh);
         if (t == 0) {
             const float2 el = exact_row(a, il), eh = exact_row(a, ih);
             atomicMax(max_err + 0,
