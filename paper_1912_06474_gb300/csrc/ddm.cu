@@ -73,6 +73,15 @@ struct KArgs {
     int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
 };
 
+// Queue bin of a ray: its cell, its kind (extension / shadow) and, where the
+// bin table allows, the octant of its direction, so that the warps draining a
+// cell's queue hold rays that also descend the cell's BVH in the same order.
+__device__ __forceinline__ int ray_bin(const DDMScene &g, int cell, int flags, float dx, float dy, float dz) {
+    const int kb = 2 * cell + (flags & kRayShadow);
+    if (g.n_oct == 1) return kb;
+    return kb * 8 + (dx < 0.0f ? 1 : 0) + (dy < 0.0f ? 2 : 0) + (dz < 0.0f ? 4 : 0);
+}
+
 // ---------------------------------------------------------------- grid
 __device__ __forceinline__ bool grid_enter(const DDMScene &g, V3 o, V3 d, float tmax, float &t0, int &cell) {
     float tn = 0.0f, tf = tmax;
@@ -147,7 +156,8 @@ __device__ __forceinline__ void put_ray(const Queues &Q, unsigned long long slot
     }
 }
 
-__device__ __forceinline__ void block_stage_push2(const Queues &Q, PushSmem &sm, int *bins, bool we, int ce, float4 e0,
+__device__ __forceinline__ void block_stage_push2(const Queues &Q, const DDMScene &g, PushSmem &sm, int *bins, bool we,
+                                                  int ce, float4 e0,
                                                   float4 e1, int4 e2, bool ws, int cs, float4 s0, float4 s1, int4 s2,
                                                   int *err) {
     const unsigned full = 0xffffffffu;
@@ -170,19 +180,19 @@ __device__ __forceinline__ void block_stage_push2(const Queues &Q, PushSmem &sm,
     __syncthreads();   // the next call rewrites warp_off and base
     if (we) {
         put_ray(Q, base + __popc(me & lt), e0, e1, e2, err);
-        const int bin = 2 * ce + (e2.z & kRayShadow);
+        const int bin = ray_bin(g, ce, e2.z, e1.x, e1.y, e1.z);
         const unsigned peers = __match_any_sync(me, bin);
         if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
     }
     if (ws) {
         put_ray(Q, base + __popc(me) + __popc(ms & lt), s0, s1, s2, err);
-        const int bin = 2 * cs + (s2.z & kRayShadow);
+        const int bin = ray_bin(g, cs, s2.z, s1.x, s1.y, s1.z);
         const unsigned peers = __match_any_sync(ms, bin);
         if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
     }
 }
 
-// Per-block (cell, kind) ray counts in shared memory (2 * n_cells ints of
+// Per-block queue-bin ray counts in shared memory (n_bins ints of
 // dynamic shared memory), added to the global counts once per block.
 __device__ __forceinline__ int *block_bins_init(int n_bins) {
     extern __shared__ int s_bins[];
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(256) k_camera(KArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long n_ext = 0;
     __shared__ PushSmem psm;
-    int *bins = block_bins_init(2 * a.g.n_cells);
+    int *bins = block_bins_init(a.g.n_bins);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
         const int64_t q = base + threadIdx.x;
         bool want = false;
@@ -239,9 +249,9 @@ __global__ void __launch_bounds__(256) k_camera(KArgs a) {
                 a.ps.hit1[q] = make_float4(d.x, d.y, d.z, 0.f);
             }
         }
-        block_stage_push2(a.Q, psm, bins, want, cell, r0, r1, r2, false, 0, r0, r1, r2, a.err);
+        block_stage_push2(a.Q, a.g, psm, bins, want, cell, r0, r1, r2, false, 0, r0, r1, r2, a.err);
     }
-    block_bins_flush(a.Q, bins, 2 * a.g.n_cells);
+    block_bins_flush(a.Q, bins, a.g.n_bins);
     block_count3(a.counters + 0, n_ext, nullptr, 0, nullptr, 0);
 }
 
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
     __shared__ int s_bin[kMaxBins];
     __shared__ int s_tmp[256];
     const Queues &Q = a.Q;
-    const int n_cells = 2 * a.g.n_cells;   // bins: (cell, ray kind)
+    const int n_cells = a.g.n_bins;   // bins: (cell, ray kind, octant)
     block_prefix(Q.cnt, n_cells, s_off, s_tmp);
     int total = s_off[n_cells];
     // the per-cell counts must add up to the staged rays, within capacity
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
                 r0[k] = src[0];
                 r1[k] = src[1];
                 r2[k] = src[2];
-                cell[k] = 2 * __float_as_int(r2[k].w) + (__float_as_int(r2[k].z) & kRayShadow);
+                cell[k] = ray_bin(a.g, __float_as_int(r2[k].w), __float_as_int(r2[k].z), r1[k].x, r1[k].y, r1[k].z);
                 rank[k] = atomicAdd(s_bin + cell[k], 1);
             }
         }
@@ -625,7 +635,7 @@ __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
     unsigned long long n_ext = 0, n_sh = 0, n_glass = 0;
     const PathState &ps = a.ps;
     __shared__ PushSmem psm;
-    int *bins = block_bins_init(2 * a.g.n_cells);
+    int *bins = block_bins_init(a.g.n_bins);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
         const int64_t q = base + threadIdx.x;
         bool want_e = false, want_s = false;
@@ -760,9 +770,9 @@ __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
             }
             ps.flags[q] = nfl;
         }
-        block_stage_push2(a.Q, psm, bins, want_e, cell_e, e0, e1, e2, want_s, cell_s, s0, s1, s2, a.err);
+        block_stage_push2(a.Q, a.g, psm, bins, want_e, cell_e, e0, e1, e2, want_s, cell_s, s0, s1, s2, a.err);
     }
-    block_bins_flush(a.Q, bins, 2 * a.g.n_cells);
+    block_bins_flush(a.Q, bins, a.g.n_bins);
     block_count3(a.counters + 0, n_ext, a.counters + 1, n_sh, a.counters + 2, n_glass);
 }
 
@@ -788,8 +798,8 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     const int64_t np = run.path_count;
     const int L = run.sc.L;
-    const int nc = run.g.n_cells;
-    if (nc > kMaxCells) {
+    const int nc = run.g.n_cells, nb = run.g.n_bins;
+    if (nc > kMaxCells || nb > kMaxBins) {
         set_error("sddm_render: the DDM method supports at most 2048 subdomains");
         return SDDM_ERR_INVALID_ARG;
     }
@@ -805,8 +815,8 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
                  oFl = take(4 * np), oPm = take(4 * np), oPc = take(4 * np), oPw = take(4 * np), oG = take(4 * np),
                  oLm = take(4 * np), oSh = take(4 * np), oCo = take(4 * kMaxCross * np), oCm = take(4 * kMaxCross * np),
                  oCc = take(4 * kMaxCross * np), oH0 = take(16 * np), oH1 = take(16 * np), oIn = take(48 * cap),
-                 oSt = take(48 * cap), oCtl = take(32 + 8 * (size_t)nc), oFill = take(8 * (size_t)nc),
-                 oOff = take(4 * (2 * (size_t)nc + 1));
+                 oSt = take(48 * cap), oCtl = take(32 + 4 * (size_t)nb), oFill = take(4 * (size_t)nb),
+                 oOff = take(4 * ((size_t)nb + 1));
     // glass evaluations of each bounce go through a query list, evaluated by the
     // exact slab or the learned model in a dense pass before shading
     const bool use_mlp = run.bsdf_mode == SDDM_BSDF_MLP;
@@ -890,7 +900,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
     const int scatter_blocks = sm * 4;
     const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
-    const size_t ctl_bytes = 32 + 8 * (size_t)nc;
+    const size_t ctl_bytes = 32 + 4 * (size_t)nb;
     cudaError_t e;
 #define DDM_CHECK(x)                                                     \
     do {                                                                 \
@@ -899,12 +909,12 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
     a.b = 0;
     a.last_wave = 0;
-    const size_t bins_smem = sizeof(int) * 2 * (size_t)nc;
+    const size_t bins_smem = sizeof(int) * (size_t)nb;
     k_camera<<<path_blocks, 256, bins_smem, s>>>(a);
     DDM_CHECK(cudaGetLastError());
     for (int b = 1; b <= run.max_depth + 1; ++b) {
         for (int w = 0; w < waves; ++w) {
-            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 8 * (size_t)nc, s));
+            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nb, s));
             k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
             DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));

@@ -473,6 +473,8 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     }
     g.eps = eps;
     g.n_cells = o.grid[0] * o.grid[1] * o.grid[2];
+    g.n_oct = 16 * g.n_cells <= kMaxBins ? 8 : 1;
+    g.n_bins = 2 * g.n_cells * g.n_oct;
     g.nodes = ctx->d_cell_nodes.as<float4>();
     g.tris = ctx->d_cell_tris.as<float4>();
     g.root = ctx->d_cell_root.as<int>();

@@ -19,13 +19,15 @@
 namespace sddm {
 
 constexpr int kMaxCells = 2048;
-constexpr int kMaxBins = 2 * kMaxCells;   // queue sort key: (cell, ray kind)
+constexpr int kMaxBins = 2 * kMaxCells;   // queue sort key: (cell, ray kind[, direction octant])
 
 struct DDMScene {
     int dims[3];
     float lo[3], hi[3], cell[3], inv_cell[3];
     float eps;            // slack of the per-cell acceptance window, metres
     int n_cells;
+    int n_oct;            // direction classes per (cell, kind): 8 octants when 16 n_cells <= kMaxBins, else 1
+    int n_bins;           // 2 n_cells n_oct queue bins
     const float4 *nodes;  // all cells' BVH nodes
     const float4 *tris;   // all cells' triangle references
     const int *root;      // [n_cells] root node of each cell
@@ -67,9 +69,9 @@ struct Queues {
     int64_t cap;          // rays per buffer
     float4 *in;           // [cap][3]
     float4 *stage;        // [cap][3]
-    int *cnt;             // [2 n_cells] rays staged per (cell, kind) bin
-    int *fill;            // [2 n_cells] scatter cursors
-    int *off;             // [2 n_cells + 1] offsets of the sorted `in`
+    int *cnt;             // [n_bins] rays staged per (cell, kind, octant) bin
+    int *fill;            // [n_bins] scatter cursors
+    int *off;             // [n_bins + 1] offsets of the sorted `in`
     unsigned long long *ctl;   // [4]: stage count, claim cursor, -, -
 };
 
