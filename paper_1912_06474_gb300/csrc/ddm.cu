@@ -73,13 +73,20 @@ struct KArgs {
     int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
 };
 
-// Queue bin of a ray: its cell, its kind (extension / shadow) and, where the
-// bin table allows, the octant of its direction, so that the warps draining a
-// cell's queue hold rays that also descend the cell's BVH in the same order.
-__device__ __forceinline__ int ray_bin(const DDMScene &g, int cell, int flags, float dx, float dy, float dz) {
+// Queue bin of a ray: its cell, its kind (extension / shadow) and, as far as
+// the bin table allows, the octant of its direction and the half of the cell
+// (per axis) where it enters, so that the warps draining a cell hold rays that
+// descend the cell's BVH alike. r0 = (origin, t_cur), r1 = (direction, t_max).
+__device__ __forceinline__ int ray_bin(const DDMScene &g, int cell, int flags, float4 r0, float4 r1) {
     const int kb = 2 * cell + (flags & kRayShadow);
     if (g.n_oct == 1) return kb;
-    return kb * 8 + (dx < 0.0f ? 1 : 0) + (dy < 0.0f ? 2 : 0) + (dz < 0.0f ? 4 : 0);
+    const int oct = (r1.x < 0.0f ? 1 : 0) + (r1.y < 0.0f ? 2 : 0) + (r1.z < 0.0f ? 4 : 0);
+    if (g.n_oct == 8) return kb * 8 + oct;
+    const float px = fmaf(r0.w, r1.x, r0.x), py = fmaf(r0.w, r1.y, r0.y), pz = fmaf(r0.w, r1.z, r0.z);
+    const int hx = (int)floorf((px - g.lo[0]) * (2.0f * g.inv_cell[0])) & 1;
+    const int hy = (int)floorf((py - g.lo[1]) * (2.0f * g.inv_cell[1])) & 1;
+    const int hz = (int)floorf((pz - g.lo[2]) * (2.0f * g.inv_cell[2])) & 1;
+    return (kb * 8 + oct) * 8 + hx + 2 * hy + 4 * hz;
 }
 
 // ---------------------------------------------------------------- grid
@@ -180,13 +187,13 @@ __device__ __forceinline__ void block_stage_push2(const Queues &Q, const DDMScen
     __syncthreads();   // the next call rewrites warp_off and base
     if (we) {
         put_ray(Q, base + __popc(me & lt), e0, e1, e2, err);
-        const int bin = ray_bin(g, ce, e2.z, e1.x, e1.y, e1.z);
+        const int bin = ray_bin(g, ce, e2.z, e0, e1);
         const unsigned peers = __match_any_sync(me, bin);
         if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
     }
     if (ws) {
         put_ray(Q, base + __popc(me) + __popc(ms & lt), s0, s1, s2, err);
-        const int bin = ray_bin(g, cs, s2.z, s1.x, s1.y, s1.z);
+        const int bin = ray_bin(g, cs, s2.z, s0, s1);
         const unsigned peers = __match_any_sync(ms, bin);
         if (lane == __ffs(peers) - 1) atomicAdd(bins + bin, __popc(peers));
     }
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(256) k_scatter(KArgs a) {
                 r0[k] = src[0];
                 r1[k] = src[1];
                 r2[k] = src[2];
-                cell[k] = ray_bin(a.g, __float_as_int(r2[k].w), __float_as_int(r2[k].z), r1[k].x, r1[k].y, r1[k].z);
+                cell[k] = ray_bin(a.g, __float_as_int(r2[k].w), __float_as_int(r2[k].z), r0[k], r1[k]);
                 rank[k] = atomicAdd(s_bin + cell[k], 1);
             }
         }

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                 slot[1] = o1;
                 slot[2] = make_float4(__int_as_float(o2.x), __int_as_float(o2.y), __int_as_float(o2.z),
                                       __int_as_float(o2.w));
-                const int bin = ray_bin(g, next, o2.z, o1.x, o1.y, o1.z);
+                const int bin = ray_bin(g, next, o2.z, o0, o1);
                 const unsigned peers = __match_any_sync(mw, bin);
                 if (lane == __ffs(peers) - 1) atomicAdd(Q.cnt + bin, __popc(peers));
             }

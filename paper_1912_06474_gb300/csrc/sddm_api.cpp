@@ -473,7 +473,10 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     }
     g.eps = eps;
     g.n_cells = o.grid[0] * o.grid[1] * o.grid[2];
-    g.n_oct = 16 * g.n_cells <= kMaxBins ? 8 : 1;
+#ifndef SDDM_MAX_SUBBINS
+#define SDDM_MAX_SUBBINS 8   // 64 measured: trace 2% faster, bin bookkeeping elsewhere slower overall
+#endif
+    g.n_oct = (SDDM_MAX_SUBBINS >= 64 && 128 * g.n_cells <= kMaxBins) ? 64 : (SDDM_MAX_SUBBINS >= 8 && 16 * g.n_cells <= kMaxBins) ? 8 : 1;
     g.n_bins = 2 * g.n_cells * g.n_oct;
     g.nodes = ctx->d_cell_nodes.as<float4>();
     g.tris = ctx->d_cell_tris.as<float4>();

@@ -26,7 +26,8 @@ struct DDMScene {
     float lo[3], hi[3], cell[3], inv_cell[3];
     float eps;            // slack of the per-cell acceptance window, metres
     int n_cells;
-    int n_oct;            // direction classes per (cell, kind): 8 octants when 16 n_cells <= kMaxBins, else 1
+    int n_oct;            // sub-bins per (cell, kind): 64 (direction octant x entry half-cell), 8 (octant) or 1,
+                          // the largest that keeps 2 n_cells n_oct <= kMaxBins
     int n_bins;           // 2 n_cells n_oct queue bins
     const float4 *nodes;  // all cells' BVH nodes
     const float4 *tris;   // all cells' triangle references
