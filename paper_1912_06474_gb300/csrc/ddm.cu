@@ -563,8 +563,8 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
 #pragma unroll kShsUnroll
                 for (int i = 0; i < L; ++i) {
                     float t = ps.T[(size_t)i * np + q];
-                    const float wx = __ldg(sc.wcmf + 3 * i), wy = __ldg(sc.wcmf + 3 * i + 1),
-                                wz = __ldg(sc.wcmf + 3 * i + 2);
+                    const float4 w4 = __ldg(sc.wcmf + i);
+                    const float wx = w4.x, wy = w4.y, wz = w4.z;
                     if (resolve) {
                         float tr = 1.0f;
                         for (int k = 0; k < ncr; ++k) {

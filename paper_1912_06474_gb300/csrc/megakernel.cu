@@ -45,9 +45,10 @@ __device__ __forceinline__ void add_xyz(const DevScene &sc, int L, Kahan3 &acc, 
     Kahan X, Y, Z;
     for_bins<LT>(L, [&](int i) {
         float e = f(i);
-        X.add(e * __ldg(sc.wcmf + 3 * i));
-        Y.add(e * __ldg(sc.wcmf + 3 * i + 1));
-        Z.add(e * __ldg(sc.wcmf + 3 * i + 2));
+        const float4 w4 = __ldg(sc.wcmf + i);
+        X.add(e * w4.x);
+        Y.add(e * w4.y);
+        Z.add(e * w4.z);
     });
     acc.add(X.s, Y.s, Z.s);
 }

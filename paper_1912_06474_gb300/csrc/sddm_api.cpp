@@ -364,11 +364,11 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     for (size_t i = 0; i < light_cum.size(); ++i) light_cdf[i] = (float)(light_cum[i] / light_total);
 
     // --- materials, spectral weights
-    std::vector<float> wcmf(3 * (size_t)L), A((size_t)M * L, 0.f), B((size_t)M * L, 0.f), Cc((size_t)M * L, 0.f),
+    std::vector<float> wcmf(4 * (size_t)L, 0.f), A((size_t)M * L, 0.f), B((size_t)M * L, 0.f), Cc((size_t)M * L, 0.f),
         thick(M, 0.f);
     std::vector<int> kinds(M);
     for (int i = 0; i < L; ++i)
-        for (int c = 0; c < 3; ++c) wcmf[3 * i + c] = ctx->quad_w[i] * ctx->cmf[3 * i + c];
+        for (int c = 0; c < 3; ++c) wcmf[4 * i + c] = ctx->quad_w[i] * ctx->cmf[3 * i + c];
     for (int m = 0; m < M; ++m) {
         const Material &mt = ctx->mats[m];
         kinds[m] = mt.kind;
@@ -447,7 +447,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     DevScene &d = ctx->dev;
     d.L = L;
     d.n_mat = M;
-    d.wcmf = ctx->d_wcmf.as<float>();
+    d.wcmf = ctx->d_wcmf.as<float4>();
     d.lam = ctx->d_lam.as<float>();
     d.mat_kind = ctx->d_kind.as<int>();
     d.mat_a = ctx->d_a.as<float>();

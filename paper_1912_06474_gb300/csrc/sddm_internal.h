@@ -38,7 +38,7 @@ constexpr uint32_t kTriGlass = 1u;
 struct DevScene {
     int L;
     int n_mat;
-    const float *wcmf;        // [L][3]  quad_w * cmf
+    const float4 *wcmf;       // [L] (quad_w * cmf_x, quad_w * cmf_y, quad_w * cmf_z, 0)
     const float *lam;         // [L]
     const int *mat_kind;      // [n_mat]
     const float *mat_a;       // [n_mat][L] rho | n | n(glass) | Le
