@@ -1,0 +1,68 @@
+"""Stored expected values (tests/golden/, written by make_golden.py from the
+FP64 oracle; the paper prints no worked example to store instead).
+
+CPU: the oracle still reproduces them, and the slab table obeys the closed
+forms (lossless R + T = 1, T at normal incidence 2n / (n^2 + 1), R, T of an
+absorbing slab inside [0, 1] with R + T < 1). GPU: the tiny-room workload
+rendered by the DDM and the megakernel matches the stored pixels.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1912_06474_gb300 import scenes
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _load(name):
+    return np.loadtxt(os.path.join(HERE, name), comments="#", ndmin=2)
+
+
+def test_slab_table_closed_forms(oracle_mod):
+    t = _load("slab_rt.txt")
+    c, lam, n, alpha, d, R, T = t.T
+    lossless = alpha == 0
+    assert np.all(np.abs(R[lossless] + T[lossless] - 1) <= 1e-12)
+    normal = lossless & (c == 1)
+    assert np.all(np.abs(T[normal] - 2 * n[normal] / (n[normal] ** 2 + 1)) <= 1e-12)
+    lossy = ~lossless
+    assert np.all((R[lossy] >= 0) & (T[lossy] >= 0) & (R[lossy] + T[lossy] < 1))
+    for row in t:
+        r2, t2 = oracle_mod.slab(*row[:5])
+        assert abs(r2 - row[5]) <= 1e-12 and abs(t2 - row[6]) <= 1e-12
+
+
+def test_c1_golden_reproduced_by_oracle(oracle_mod):
+    g = _load("c1_tiny_room_64x64_1spp_d2_L16.txt")
+    pix = g[:, 0].astype(np.int64)
+    sc = scenes.tiny_room(L=16, seed=0)
+    spec = scenes.RenderSpec(64, 64, 1, 2, seed=0, camera=sc.camera)
+    xyz = oracle_mod.Oracle(sc).render_pixels(spec, pix, brute_force=True)["xyz"]
+    assert np.allclose(xyz, g[:, 1:4], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("method,grid", [("ddm", (1, 1, 1)), ("ddm", (2, 2, 2)), ("megakernel", (1, 1, 1))])
+def test_c1_golden_on_gpu(method, grid):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1912_06474_gb300 import sddm
+    g = _load("c1_tiny_room_64x64_1spp_d2_L16.txt")
+    pix, ref, margin, cmin = g[:, 0].astype(np.int64), g[:, 1:4], g[:, 4], g[:, 5]
+    sc = scenes.tiny_room(L=16, seed=0)
+    spec = scenes.RenderSpec(64, 64, 1, 2, seed=0, camera=sc.camera)
+    ctx = sddm.Context(0)
+    ctx.set_scene(sc)
+    ctx.build(grid=grid)
+    imgs, _ = ctx.render([spec], method=method)
+    got = imgs[0].cpu().numpy().reshape(-1, 3)[pix].astype(np.float64)
+    rel = np.abs(got - ref).max(1) / np.maximum(np.abs(ref).max(1), 1e-12)
+    safe = (margin > 1e-5) & (cmin >= 0.02)
+    assert safe.sum() > 0.9 * len(pix)
+    assert rel[safe].max() <= 1e-5, rel[safe].max()
+    assert rel.max() <= 1e-3, rel.max()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+    ctx.close()
