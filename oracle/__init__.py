@@ -57,7 +57,9 @@ class _SceneDesc(C.Structure):
                 ("n_mat", C.c_int), ("mat_kind", C.c_void_p), ("mat_a", C.c_void_p),
                 ("mat_b", C.c_void_p), ("mat_c", C.c_void_p), ("mat_thick", C.c_void_p),
                 ("mat_s", C.c_void_p), ("nv", C.c_int), ("V", C.c_void_p), ("nt", C.c_int),
-                ("F", C.c_void_p), ("mat_id", C.c_void_p), ("obj_id", C.c_void_p)]
+                ("F", C.c_void_p), ("mat_id", C.c_void_p), ("obj_id", C.c_void_p),
+                ("mat_nlayers", C.c_void_p), ("layer_n", C.c_void_p), ("layer_k", C.c_void_p),
+                ("layer_dk", C.c_void_p), ("layer_t", C.c_void_p)]
 
 
 class _RenderDesc(C.Structure):
@@ -86,6 +88,8 @@ def _load():
         lib.orc_u01.restype = C.c_double
         lib.orc_fresnel.argtypes = [C.c_double, C.c_double, C.c_double, P, P]
         lib.orc_slab.argtypes = [C.c_double] * 5 + [P, P]
+        lib.orc_coated_face.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, P, P, P, C.c_int, P, P, P, P]
+        lib.orc_coated_slab.argtypes = [C.c_double] * 5 + [C.c_int, P, P, P, P, P]
         lib.orc_conductor.argtypes = [C.c_double] * 3
         lib.orc_conductor.restype = C.c_double
         lib.orc_branch_proxy.argtypes = [C.c_float, C.c_int, P]
@@ -141,6 +145,34 @@ def slab(c, lam_nm, n, alpha_per_m, thick_m):
     R, T = C.c_double(), C.c_double()
     lib.orc_slab(float(c), float(lam_nm), float(n), float(alpha_per_m), float(thick_m),
                  C.byref(R), C.byref(T))
+    return R.value, T.value
+
+
+def _films(layers):
+    nf = np.ascontiguousarray([f[0] for f in layers], np.float64)
+    kf = np.ascontiguousarray([f[1] for f in layers], np.float64)
+    tf = np.ascontiguousarray([f[2] for f in layers], np.float64)
+    return nf, kf, tf
+
+
+def coated_face(c, lam_nm, n_sub, layers, pol):
+    """One coated face: (R, T) seen from air and (R, T) seen from the glass,
+    for films [(n, k, t_nm), ...] outermost first; pol 0 = s, 1 = p."""
+    lib = _load()
+    nf, kf, tf = _films(layers) if layers else (np.zeros(1), np.zeros(1), np.zeros(1))
+    out = [C.c_double() for _ in range(4)]
+    lib.orc_coated_face(float(c), float(lam_nm), float(n_sub), len(layers), _ptr(nf), _ptr(kf), _ptr(tf),
+                        int(pol), *[C.byref(o) for o in out])
+    return tuple(o.value for o in out)
+
+
+def coated_slab(c, lam_nm, n_sub, alpha_per_m, thick_m, layers):
+    """Slab coated on both faces with films [(n, k, t_nm), ...]: (R, T)."""
+    lib = _load()
+    nf, kf, tf = _films(layers) if layers else (np.zeros(1), np.zeros(1), np.zeros(1))
+    R, T = C.c_double(), C.c_double()
+    lib.orc_coated_slab(float(c), float(lam_nm), float(n_sub), float(alpha_per_m), float(thick_m), len(layers),
+                        _ptr(nf), _ptr(kf), _ptr(tf), C.byref(R), C.byref(T))
     return R.value, T.value
 
 
@@ -240,6 +272,23 @@ def _material_arrays(scene):
     return kind, a, b, c, thick, s
 
 
+def _layer_arrays(scene):
+    L, M = scene.L, len(scene.materials)
+    nl = np.zeros(M, np.int32)
+    ln = np.zeros((M, 4, L), np.float32)
+    lk = np.zeros((M, 4, L), np.float32)
+    ldk = np.zeros((M, 4, L), np.float32)
+    lt = np.zeros((M, 4), np.float32)
+    for i, m in enumerate(scene.materials):
+        if m.kind == GLASS and m.layers:
+            if len(m.layers) > 4:
+                raise ValueError("at most 4 films per face")
+            nl[i] = len(m.layers)
+            for j, f in enumerate(m.layers):
+                ln[i, j], lk[i, j], ldk[i, j], lt[i, j] = f["n"], f["k"], f["dk"], f["t_nm"]
+    return nl, ln, lk, ldk, lt
+
+
 class Oracle:
     """FP64 oracle bound to one scene (inputs copied on construction)."""
 
@@ -247,7 +296,8 @@ class Oracle:
         self.lib = _load()
         self.scene = scene
         kind, a, b, c, thick, s = _material_arrays(scene)
-        keep = dict(lam=np.ascontiguousarray(scene.lam, np.float32),
+        nl, ln, lk, ldk, lt = _layer_arrays(scene)
+        keep = dict(nl=nl, ln=ln, lk=lk, ldk=ldk, lt=lt, lam=np.ascontiguousarray(scene.lam, np.float32),
                     w=np.ascontiguousarray(scene.quad_w, np.float32),
                     cmf=np.ascontiguousarray(scene.cmf, np.float32),
                     kind=kind, a=a, b=b, c=c, thick=thick, s=s,
@@ -258,12 +308,14 @@ class Oracle:
         d = _SceneDesc(scene.L, _ptr(keep["lam"]), _ptr(keep["w"]), _ptr(keep["cmf"]),
                        len(scene.materials), _ptr(kind), _ptr(a), _ptr(b), _ptr(c), _ptr(thick),
                        _ptr(s), int(keep["V"].shape[0]), _ptr(keep["V"]), int(keep["F"].shape[0]),
-                       _ptr(keep["F"]), _ptr(keep["M"]), _ptr(keep["O"]))
+                       _ptr(keep["F"]), _ptr(keep["M"]), _ptr(keep["O"]), _ptr(nl), _ptr(ln), _ptr(lk),
+                       _ptr(ldk), _ptr(lt))
         h = C.c_void_p()
         rc = self.lib.orc_create(C.byref(h), C.byref(d))
         if rc != 0:
             raise RuntimeError(f"orc_create failed ({rc})")
         self._h = h
+        self._keep = keep
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -7,6 +7,7 @@
 
 #define ORC_MAX_L 256
 #define ORC_MAX_CROSS 4
+#define ORC_MAX_FILMS 4
 
 typedef struct {
     double lo[3], hi[3];
@@ -22,6 +23,9 @@ typedef struct {
     double *a, *b, *c;               /* [n_mat*L] */
     float *a_f;                      /* float copy of mat_a (glass real index for the proxy) */
     double *thick, *s;
+    int *nlayers;                    /* [n_mat] coating films per face */
+    double *ln, *lk, *ldk;           /* [n_mat*4*L] film n, k, dk */
+    double *lt;                      /* [n_mat*4] film thickness, nm */
     int nt;
     double *v;                       /* [nt*9]: v0, v1, v2 */
     double *ng;                      /* [nt*3] unit geometric normal, CCW */

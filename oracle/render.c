@@ -65,6 +65,7 @@ void orc_destroy(void *p)
     free(c->lam); free(c->w); free(c->cmf);
     free(c->kind); free(c->a); free(c->b); free(c->c); free(c->a_f);
     free(c->thick); free(c->s);
+    free(c->nlayers); free(c->ln); free(c->lk); free(c->ldk); free(c->lt);
     free(c->v); free(c->ng); free(c->mat); free(c->obj);
     free(c->nodes); free(c->tri_order);
     free(c->light_tri); free(c->light_cdf);
@@ -93,6 +94,24 @@ int orc_create(void **out, const orc_scene_desc *d)
     c->a_f = (float *)malloc(sizeof(float) * ML);
     c->thick = dup_d(d->mat_thick, (size_t)d->n_mat);
     c->s = dup_d(d->mat_s, (size_t)d->n_mat);
+    size_t MF = (size_t)d->n_mat * ORC_MAX_FILMS;
+    c->nlayers = (int *)calloc((size_t)d->n_mat, sizeof(int));
+    c->ln = dup_d(d->layer_n, MF * (size_t)L);
+    c->lk = dup_d(d->layer_k, MF * (size_t)L);
+    c->ldk = dup_d(d->layer_dk, MF * (size_t)L);
+    c->lt = dup_d(d->layer_t, MF);
+    if (!c->nlayers || !c->ln || !c->lk || !c->ldk || !c->lt) {
+        orc_destroy(c);
+        return -2;
+    }
+    for (int m = 0; m < d->n_mat; ++m) {
+        int nl = d->mat_nlayers ? d->mat_nlayers[m] : 0;
+        if (nl < 0 || nl > ORC_MAX_FILMS) {
+            orc_destroy(c);
+            return -1;
+        }
+        c->nlayers[m] = nl;
+    }
     c->nt = d->nt;
     size_t nt = (size_t)d->nt;
     c->v = (double *)malloc(sizeof(double) * 9 * (nt ? nt : 1));
@@ -272,8 +291,17 @@ static void slab_rt(const orc_ctx *c, const orc_render_desc *r, int m, double co
                     double *R, double *T)
 {
     size_t k = (size_t)m * c->L + i;
-    double alpha = c->b[k] + state_s(c, r, m) * c->c[k];
-    orc_slab(cosv, c->lam[i], c->a[k], alpha, c->thick[m], R, T);
+    double s = state_s(c, r, m);
+    double alpha = c->b[k] + s * c->c[k];
+    int J = c->nlayers[m];
+    double nf[ORC_MAX_FILMS], kf[ORC_MAX_FILMS], tf[ORC_MAX_FILMS];
+    for (int j = 0; j < J; ++j) {
+        size_t f = ((size_t)m * ORC_MAX_FILMS + j) * c->L + i;
+        nf[j] = c->ln[f];
+        kf[j] = c->lk[f] + s * c->ldk[f];
+        tf[j] = c->lt[(size_t)m * ORC_MAX_FILMS + j];
+    }
+    orc_coated_slab(cosv, c->lam[i], c->a[k], alpha, c->thick[m], J, nf, kf, tf, R, T);
 }
 
 /* ----------------------------------------------------------- one path --- */

@@ -58,6 +58,12 @@ typedef struct {
     const uint32_t *F;        /* [nt][3] */
     const uint32_t *mat_id;   /* [nt] */
     const uint32_t *obj_id;   /* [nt] */
+    /* thin-film coating of glass materials (both faces); NULL = none */
+    const int32_t *mat_nlayers; /* [n_mat] films per face, 0..4 */
+    const float *layer_n;     /* [n_mat][4][L] film real index */
+    const float *layer_k;     /* [n_mat][4][L] film extinction at s = 0 */
+    const float *layer_dk;    /* [n_mat][4][L] extinction added at s = 1 (k = k + s dk) */
+    const float *layer_t;     /* [n_mat][4] film thickness, nm */
 } orc_scene_desc;
 
 typedef struct {
@@ -91,6 +97,12 @@ double orc_u01(uint32_t x);
 void orc_fresnel(double c, double n, double k, double *Rs, double *Rp);
 void orc_slab(double c, double lam_nm, double n, double alpha_per_m, double thick_m,
               double *R, double *T);
+/* Slab coated on both faces with J thin films (n, k, thickness in nm each):
+ * one face seen from air (Ra, Ta) and from the glass (Rg, Tg), polarisation 0 = s, 1 = p. */
+void orc_coated_face(double c, double lam_nm, double n_sub, int J, const double *nf, const double *kf,
+                     const double *tf_nm, int pol, double *Ra, double *Ta, double *Rg, double *Tg);
+void orc_coated_slab(double c, double lam_nm, double n_sub, double alpha_per_m, double thick_m, int J,
+                     const double *nf, const double *kf, const double *tf_nm, double *R, double *T);
 double orc_conductor(double c, double n, double k);
 float orc_branch_proxy(float c, int L, const float *n);
 void orc_cosine_dir(const double ns[3], double u0, double u1, double out[3]);

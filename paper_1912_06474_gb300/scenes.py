@@ -154,6 +154,10 @@ class Material:
     s_default: float = 0.0
     Le: Optional[np.ndarray] = None           # emitted radiance [L]
     name: str = ""
+    # glass coated on both faces with thin films (up to 4 per face), outermost
+    # first: each a dict n [L], k [L] (extinction at s = 0), dk [L] (added at
+    # s = 1), t_nm (thickness, nm)
+    layers: Optional[list] = None
 
 
 @dataclass
