@@ -160,6 +160,21 @@ int sddm_add_conductor(sddm_ctx *ctx, const float *n, const float *k, uint32_t *
 int sddm_add_glass_slab(sddm_ctx *ctx, const float *n, const float *alpha_clear,
                         const float *dalpha, float thickness_m, float s_default, uint32_t *mat);
 
+/* Glass slab coated on both outer faces with the same stack of n_films thin
+ * films (an electrochromic device; a multilayer extension of the slab of
+ * Sec. 6): the substrate as in sddm_add_glass_slab, films
+ * outermost first, film_n / film_k / film_dk HOST [n_films][L] (real index,
+ * extinction at s = 0, extinction added at s = 1: k = k + s dk),
+ * film_t_nm[n_films] thicknesses in nm. Each face is evaluated exactly by
+ * its characteristic (transfer) matrix per polarisation; the faces combine
+ * incoherently through the substrate. 0 <= n_films <= SDDM_MAX_FILMS; with no
+ * film this is sddm_add_glass_slab. The paper gives the glass by its "Fresnel
+ * definition" (Sec. 6) and has no thin-film model: this call extends it. */
+#define SDDM_MAX_FILMS 4
+int sddm_add_coated_glass(sddm_ctx *ctx, const float *n, const float *alpha_clear, const float *dalpha,
+                          float thickness_m, float s_default, int n_films, const float *film_n, const float *film_k,
+                          const float *film_dk, const float *film_t_nm, uint32_t *mat);
+
 /* One-sided area light of radiance Le[L] >= 0 toward its counter-clockwise
  * normal, black to reflection (the light sources of Eq. 3, here with area). */
 int sddm_add_emitter(sddm_ctx *ctx, const float *Le, uint32_t *mat);

@@ -103,7 +103,7 @@ def _load():
         lib.orc_num_lights.argtypes = [P]
         lib.orc_num_lights.restype = C.c_int
         lib.orc_mlp_n_params.restype = C.c_int
-        lib.orc_mlp_features.argtypes = [C.c_double] * 5 + [P]
+        lib.orc_mlp_features.argtypes = [C.c_double] * 6 + [P]
         lib.orc_mlp_forward.argtypes = [P, P, P]
         lib.orc_mlp_rt.argtypes = [P, P, P]
         lib.orc_mlp_forward_d.argtypes = [P, P, P]
@@ -196,11 +196,13 @@ def cosine_dir(ns, u0, u1):
 MLP_PARAMS = 8770
 
 
-def mlp_features(c, lam_nm, s, d, alpha):
+def mlp_features(c, lam_nm, s, d, alpha, film_absorbance=0.0):
     """Network inputs of one row: cos, wavelength (nm), coloration state,
-    thickness (m) and the absorption coefficient alpha(lambda, s) (1/m)."""
+    thickness (m), the absorption coefficient alpha(lambda, s) (1/m) and the
+    coating films' normal-incidence absorbance sum 4 pi k t / lambda."""
     x = np.zeros(4)
-    _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), float(alpha), _ptr(x))
+    _load().orc_mlp_features(float(c), float(lam_nm), float(s), float(d), float(alpha), float(film_absorbance),
+                             _ptr(x))
     return x
 
 

@@ -7,10 +7,12 @@
  * thickness): 4 inputs -> 64 -> 64 -> 64 SiLU units -> 2 outputs (R, T).
  * Inputs are mapped to [-1, 1]:
  *   x0 = 2 cos - 1, x1 = 2 (lambda - 380) / 400 - 1, x2 = 2 s - 1,
- *   x3 = 2 exp(-alpha d) - 1,
+ *   x3 = 2 exp(-(alpha d + A_f)) - 1,
  * where alpha = alpha_clear(lambda) + s dalpha(lambda) is the material's
  * absorption coefficient (1/m) at the coloration state s, so that x3 carries
- * the thickness as the slab's internal transmittance at normal incidence.
+ * the thickness as the slab's internal transmittance at normal incidence, and
+ * A_f = sum_j 4 pi k_j t_j / lambda is the normal-incidence absorbance of any
+ * coating films (0 for bare glass).
  * The two outputs y are log(R + 1e-3) and log(T + 1e-3); the served values are
  * R = max(exp(y0) - 1e-3, 0), T = max(exp(y1) - 1e-3, 0) (orc_mlp_rt).
  * Parameters, in this order (8770 floats): W1[64][4], b1[64], W2[64][64], b2[64],
@@ -37,12 +39,13 @@
 
 int orc_mlp_n_params(void) { return N_PARAMS; }
 
-void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double x[4])
+void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double film_absorbance,
+                      double x[4])
 {
     x[0] = 2.0 * c - 1.0;
     x[1] = 2.0 * (lam_nm - 380.0) / 400.0 - 1.0;
     x[2] = 2.0 * s - 1.0;
-    x[3] = 2.0 * exp(-alpha * d) - 1.0;
+    x[3] = 2.0 * exp(-(alpha * d + film_absorbance)) - 1.0;
 }
 
 static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }

@@ -117,7 +117,8 @@ int orc_num_lights(void *ctx);
 
 /* Glass surrogate network (mlp.c): 4 -> 64 -> 64 -> 64 (SiLU) -> 2, 8770 parameters. */
 int orc_mlp_n_params(void);
-void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double x[4]);
+void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double film_absorbance,
+                      double x[4]);
 void orc_mlp_forward(const float *params, const double x[4], double y[2]);
 void orc_mlp_rt(const float *params, const double x[4], double rt[2]);
 void orc_mlp_forward_d(const double *params, const double x[4], double y[2]);

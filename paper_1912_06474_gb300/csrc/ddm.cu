@@ -472,6 +472,7 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
 #define SDDM_SHS_UNROLL 4    // bins in flight per thread
 #endif
 constexpr int kShsUnroll = SDDM_SHS_UNROLL;
+template <bool FILMS>
 __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) {
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
@@ -544,7 +545,6 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
             const float *Le_b = sc.mat_a + (size_t)mat * L;
             const float *pA = sc.mat_a + (size_t)(pm < 0 ? 0 : pm) * L;
             const float *pB = sc.mat_b + (size_t)(pm < 0 ? 0 : pm) * L;
-            const float *pC = sc.mat_c + (size_t)(pm < 0 ? 0 : pm) * L;
             const float ps_state = (pend && pkind == kGlass) ? st_of(a.rb, r, pm, sc.n_mat) : 0.f;
             const float pthick = (pend && pkind == kGlass) ? __ldg(sc.mat_thick + pm) : 0.f;
             const float pwabs = fabsf(pw);
@@ -572,10 +572,8 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
                                 tr *= a.glass_res[(size_t)cq[k] * L + i].y;
                                 continue;
                             }
-                            const size_t kk = (size_t)cmat[k] * L + i;
                             float R_, T_;
-                            slab_RT(ccos[k], __ldg(sc.lam + i), __ldg(sc.mat_a + kk),
-                                    __ldg(sc.mat_b + kk) + cst[k] * __ldg(sc.mat_c + kk), cth[k], R_, T_);
+                            glass_rt<FILMS>(sc, cmat[k], i, ccos[k], cst[k], cth[k], R_, T_);
                             tr *= T_;
                         }
                         const float c = t * __ldg(rho_prev + i) * __ldg(Le_l + i) * G * tr;
@@ -596,8 +594,7 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
                             w = (preflect ? rt.x : rt.y) * pwabs;
                         } else {
                             float R_, T_;
-                            slab_RT(pcos, __ldg(sc.lam + i), __ldg(pA + i), __ldg(pB + i) + ps_state * __ldg(pC + i),
-                                    pthick, R_, T_);
+                            glass_rt<FILMS>(sc, pm, i, pcos, ps_state, pthick, R_, T_);
                             w = (preflect ? R_ : T_) * pwabs;
                         }
                         t *= w;
@@ -952,7 +949,10 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
                 DDM_CHECK(launch_slab_rows(mr, run.sm_count, s));
             *run.launches += 2;
         }
-        k_shade_spectral<<<path_blocks, 256, 0, s>>>(a);
+        if (run.sc.mat_nfilm)
+            k_shade_spectral<true><<<path_blocks, 256, 0, s>>>(a);
+        else
+            k_shade_spectral<false><<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         k_shade_continue<<<path_blocks, 256, bins_smem, s>>>(a);
         DDM_CHECK(cudaGetLastError());

@@ -297,6 +297,137 @@ __device__ __forceinline__ void slab_RT(float c, float lam_nm, float n, float al
     T = 0.5f * tau * (qs * ds + qp * dp);
 }
 
+// ---------------------------------------------------- coated glass (thin films)
+// Complex numbers for the thin-film characteristic matrices.
+struct Cx {
+    float r, i;
+};
+__device__ __forceinline__ Cx cx(float r, float i = 0.0f) { return Cx{r, i}; }
+__device__ __forceinline__ Cx operator+(Cx a, Cx b) { return Cx{a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ Cx operator-(Cx a, Cx b) { return Cx{a.r - b.r, a.i - b.i}; }
+__device__ __forceinline__ Cx operator*(Cx a, Cx b) { return Cx{fmaf(a.r, b.r, -a.i * b.i), fmaf(a.r, b.i, a.i * b.r)}; }
+__device__ __forceinline__ Cx operator*(float s, Cx a) { return Cx{s * a.r, s * a.i}; }
+__device__ __forceinline__ float cx_abs2(Cx a) { return fmaf(a.r, a.r, a.i * a.i); }
+__device__ __forceinline__ Cx cx_div(Cx a, Cx b) {
+    const float d = __frcp_rn(cx_abs2(b));
+    return Cx{d * fmaf(a.r, b.r, a.i * b.i), d * fmaf(a.i, b.r, -a.r * b.i)};
+}
+__device__ __forceinline__ Cx cx_sqrt(Cx z) {   // principal root
+    const float m = sqrtf(sqrtf(cx_abs2(z)));
+    const float h = 0.5f * atan2f(z.i, z.r);
+    float sh, ch;
+    sincosf(h, &sh, &ch);
+    return Cx{m * ch, m * sh};
+}
+
+// Up to kMaxFilms films per face.
+constexpr int kMaxFilms = 4;
+
+// Glass coated on both faces with the same stack of J thin films (outermost
+// first): each face is a coherent stack evaluated by its characteristic
+// matrix (per film: complex index n + i k, cos theta = sqrt(1 - sin^2 / n^2)
+// on the decaying branch, tilted admittance n cos (s) or n / cos (p), phase
+// delta = 2 pi n t cos / lambda, M = [[cos d, -i sin d / eta], [-i eta sin d, cos d]]),
+// from air onto the glass and from the glass out to air (films reversed);
+// the thick substrate (real index, tau = exp(-alpha d / cos_t)) combines the
+// faces incoherently:
+//   R = R_a + T_a T_g R_g tau^2 / (1 - R_g^2 tau^2),  T = T_a T_g tau / (1 - R_g^2 tau^2),
+// per polarisation, averaged.
+static __device__ __noinline__ void coated_RT(float c, float lam_nm, float n_sub, float alpha, float thick, int J,
+                                       const float *nf, const float *kf, const float *tf_nm, float &R, float &T) {
+    if (c <= 0.0f) {
+        R = 1.0f;
+        T = 0.0f;
+        return;
+    }
+    c = fminf(fmaxf(c, 1e-8f), 1.0f);
+    const float s2 = fmaf(-c, c, 1.0f);
+    const float ct_sub = sqrtf(fmaf(-s2, __frcp_rn(n_sub * n_sub), 1.0f));
+    const float tau = expf(-alpha * thick / ct_sub), t2 = tau * tau;
+    Cx N[kMaxFilms], CT[kMaxFilms], CD[kMaxFilms], SD[kMaxFilms];
+    for (int j = 0; j < J; ++j) {
+        N[j] = cx(nf[j], kf[j]);
+        const Cx n2 = N[j] * N[j];
+        Cx ct = cx_sqrt(cx(1.0f) - cx_div(cx(s2), n2));
+        if ((N[j] * ct).i < 0.0f) ct = (-1.0f) * ct;
+        CT[j] = ct;
+        const Cx delta = (6.283185307179586f * tf_nm[j] / lam_nm) * (N[j] * ct);
+        float sa, ca;
+        sincosf(delta.r, &sa, &ca);
+        const float ep = expf(delta.i), em = expf(-delta.i);
+        const float chb = 0.5f * (ep + em), shb = 0.5f * (ep - em);
+        CD[j] = cx(ca * chb, -sa * shb);   // cos(a + ib)
+        SD[j] = cx(sa * chb, ca * shb);    // sin(a + ib)
+    }
+    float Rsum = 0.0f, Tsum = 0.0f;
+    for (int pol = 0; pol < 2; ++pol) {
+        const float eta0 = pol == 0 ? c : __frcp_rn(c);
+        const float etas = pol == 0 ? n_sub * ct_sub : n_sub / ct_sub;
+        Cx m00 = cx(1.0f), m01 = cx(0.0f), m10 = cx(0.0f), m11 = cx(1.0f);   // M_1 ... M_J
+        Cx g00 = cx(1.0f), g01 = cx(0.0f), g10 = cx(0.0f), g11 = cx(1.0f);   // M_J ... M_1
+        for (int j = 0; j < J; ++j) {
+            const Cx eta = pol == 0 ? N[j] * CT[j] : cx_div(N[j], CT[j]);
+            const Cx a = CD[j];
+            const Cx b = cx_div(cx(SD[j].i, -SD[j].r), eta);   // -i sin / eta
+            const Cx d = eta * cx(SD[j].i, -SD[j].r);          // -i eta sin
+            Cx t00 = m00 * a + m01 * d, t01 = m00 * b + m01 * a, t10 = m10 * a + m11 * d, t11 = m10 * b + m11 * a;
+            m00 = t00;
+            m01 = t01;
+            m10 = t10;
+            m11 = t11;
+            t00 = a * g00 + b * g10;
+            t01 = a * g01 + b * g11;
+            t10 = d * g00 + a * g10;
+            t11 = d * g01 + a * g11;
+            g00 = t00;
+            g01 = t01;
+            g10 = t10;
+            g11 = t11;
+        }
+        const Cx B = m00 + etas * m01, C = m10 + etas * m11;
+        const Cx dn = eta0 * B + C, nu = eta0 * B - C;
+        const float id = __frcp_rn(cx_abs2(dn));
+        const float Ra = cx_abs2(nu) * id, Ta = 4.0f * eta0 * etas * id;
+        const Cx B2 = g00 + eta0 * g01, C2 = g10 + eta0 * g11;
+        const Cx dn2 = etas * B2 + C2, nu2 = etas * B2 - C2;
+        const float id2 = __frcp_rn(cx_abs2(dn2));
+        const float Rg = cx_abs2(nu2) * id2, Tg = 4.0f * etas * eta0 * id2;
+        const float den = __frcp_rn(fmaf(-Rg * Rg, t2, 1.0f));
+        Rsum += fmaf(Ta * Tg * Rg * t2, den, Ra);
+        Tsum += Ta * Tg * tau * den;
+    }
+    R = 0.5f * Rsum;
+    T = 0.5f * Tsum;
+}
+
+// R, T of glass material m at wavelength bin i: the bare absorbing slab, or
+// the coated slab when the material carries films (film k = k + s dk).
+// Kernels are instantiated with FILMS = false for scenes without coated glass,
+// which keeps the film code (and its call) out of them entirely.
+template <bool FILMS = true>
+__device__ __forceinline__ void glass_rt(const DevScene &sc, int m, int i, float c, float s, float thick, float &R,
+                                         float &T) {
+    const size_t k = (size_t)m * sc.L + i;
+    const float alpha = __ldg(sc.mat_b + k) + s * __ldg(sc.mat_c + k);
+    if constexpr (!FILMS) {
+        slab_RT(c, __ldg(sc.lam + i), __ldg(sc.mat_a + k), alpha, thick, R, T);
+    } else {
+        const int J = sc.mat_nfilm ? __ldg(sc.mat_nfilm + m) : 0;
+        if (J == 0) {
+            slab_RT(c, __ldg(sc.lam + i), __ldg(sc.mat_a + k), alpha, thick, R, T);
+            return;
+        }
+        float nf[kMaxFilms], kf[kMaxFilms], tf[kMaxFilms];
+        for (int j = 0; j < J; ++j) {
+            const size_t f = ((size_t)m * kMaxFilms + j) * sc.L + i;
+            nf[j] = __ldg(sc.film_n + f);
+            kf[j] = __ldg(sc.film_k + f) + s * __ldg(sc.film_dk + f);
+            tf[j] = __ldg(sc.film_t + (size_t)m * kMaxFilms + j);
+        }
+        coated_RT(c, __ldg(sc.lam + i), __ldg(sc.mat_a + k), alpha, thick, J, nf, kf, tf, R, T);
+    }
+}
+
 // Glass branch probability: clamp(mean over bins of the lossless slab
 // reflectance 2 rho / (1 + rho), averaged over polarisations, 0.05, 0.95).
 // It decides an integer, so it is evaluated with explicitly rounded

@@ -53,7 +53,7 @@ __device__ __forceinline__ void add_xyz(const DevScene &sc, int L, Kahan3 &acc, 
     acc.add(X.s, Y.s, Z.s);
 }
 
-template <int LT, bool COUNT>
+template <int LT, bool COUNT, bool FILMS>
 __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.path_count) return;
@@ -144,11 +144,9 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
                             float tr = 1.0f;
                             for (int q = 0; q < cr.n; ++q) {
                                 const int m = cmat[q];
-                                const float al = __ldg(sc.mat_b + (size_t)m * L + i) +
-                                                 state_of(a.rb, r, m, sc.n_mat) * __ldg(sc.mat_c + (size_t)m * L + i);
                                 float R_, T_;
-                                slab_RT(ccos[q], __ldg(sc.lam + i), __ldg(sc.mat_a + (size_t)m * L + i), al,
-                                        __ldg(sc.mat_thick + m), R_, T_);
+                                glass_rt<FILMS>(sc, m, i, ccos[q], state_of(a.rb, r, m, sc.n_mat), __ldg(sc.mat_thick + m), R_,
+                                         T_);
                                 tr *= T_;
                             }
                             return T.v[i] * __ldg(rho + i) * __ldg(Le + i) * G * tr;
@@ -189,8 +187,7 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
             ++n_glass;
             for_bins<LT>(L, [&](int i) {
                 float R_, T_;
-                const float al = __ldg(mB + i) + s * __ldg(sc.mat_c + (size_t)mat * L + i);
-                slab_RT(c, __ldg(sc.lam + i), __ldg(mA + i), al, th, R_, T_);
+                glass_rt<FILMS>(sc, mat, i, c, s, th, R_, T_);
                 T.v[i] *= (reflect ? R_ : T_) * wsel;
             });
             if (reflect) {
@@ -228,24 +225,25 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
     }
 }
 
+template <bool COUNT, bool FILMS>
+static void launch_mk(const MegaArgs &a, unsigned nb, int threads, cudaStream_t stream) {
+    switch (a.sc.L) {
+        case 8: k_megakernel<8, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
+        case 16: k_megakernel<16, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
+        default: k_megakernel<0, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
+    }
+}
+
 cudaError_t launch_megakernel(const MegaArgs &a, cudaStream_t stream) {
     if (a.path_count <= 0) return cudaSuccess;
     const int threads = 128;
     const int64_t blocks = (a.path_count + threads - 1) / threads;
     const unsigned nb = (unsigned)blocks;
-    if (a.count_traversal) {
-        switch (a.sc.L) {
-            case 8: k_megakernel<8, true><<<nb, threads, 0, stream>>>(a); break;
-            case 16: k_megakernel<16, true><<<nb, threads, 0, stream>>>(a); break;
-            default: k_megakernel<0, true><<<nb, threads, 0, stream>>>(a); break;
-        }
-    } else {
-        switch (a.sc.L) {
-            case 8: k_megakernel<8, false><<<nb, threads, 0, stream>>>(a); break;
-            case 16: k_megakernel<16, false><<<nb, threads, 0, stream>>>(a); break;
-            default: k_megakernel<0, false><<<nb, threads, 0, stream>>>(a); break;
-        }
-    }
+    const bool films = a.sc.mat_nfilm != nullptr;
+    if (a.count_traversal)
+        films ? launch_mk<true, true>(a, nb, threads, stream) : launch_mk<true, false>(a, nb, threads, stream);
+    else
+        films ? launch_mk<false, true>(a, nb, threads, stream) : launch_mk<false, false>(a, nb, threads, stream);
     return cudaGetLastError();
 }
 

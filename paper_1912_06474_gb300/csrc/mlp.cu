@@ -122,7 +122,8 @@ __device__ __forceinline__ float rt_to_out(float v) { return logf(v + kOutEps); 
 // Network inputs from (cos, lambda, s, thickness): cos and s mapped to [-1, 1],
 // lambda over 380-780 nm to [-1, 1], and the thickness through the slab's
 // internal transmittance at normal incidence, exp(-alpha(lambda, s) d) mapped
-// to [-1, 1] (alpha = alpha_clear + s dalpha, the material's absorption law).
+// to [-1, 1] (alpha = alpha_clear + s dalpha, the material's absorption law),
+// times that of any coating film (exp(-4 pi k t / lambda) each).
 // Angle, Fresnel and the multiple reflections are left to the network.
 __device__ __forceinline__ void features(float c, float lam, float s, float alpha_d, float x[4]) {
     x[0] = 2.0f * c - 1.0f;
@@ -223,10 +224,22 @@ struct RowIn {
     int mat, bin;
 };
 
-// alpha(lambda, s) * d of a row: the absorption law at the row's bin.
+// Normal-incidence absorbance of a row's glass: alpha(lambda, s) d of the
+// substrate plus, for coated glass, 4 pi k_j(lambda, s) t_j / lambda of each
+// film (Beer-Lambert through every absorbing layer, interference left out).
+template <bool FILMS = true>
 __device__ __forceinline__ float row_alpha_d(const DevScene &sc, const RowIn &in) {
     const size_t k = (size_t)in.mat * sc.L + in.bin;
-    return (__ldg(sc.mat_b + k) + in.s * __ldg(sc.mat_c + k)) * in.d;
+    float a = (__ldg(sc.mat_b + k) + in.s * __ldg(sc.mat_c + k)) * in.d;
+    if constexpr (FILMS) {
+        const int J = sc.mat_nfilm ? __ldg(sc.mat_nfilm + in.mat) : 0;
+        for (int j = 0; j < J; ++j) {
+            const size_t f = ((size_t)in.mat * kMaxFilms + j) * sc.L + in.bin;
+            const float kj = __ldg(sc.film_k + f) + in.s * __ldg(sc.film_dk + f);
+            a = fmaf(12.566370614359172f * kj, __ldg(sc.film_t + (size_t)in.mat * kMaxFilms + j) / in.lam, a);
+        }
+    }
+    return a;
 }
 
 __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t total, RowIn &in) {
@@ -261,10 +274,10 @@ __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t t
     return true;
 }
 
+template <bool FILMS = true>
 __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
-    const size_t k = (size_t)in.mat * a.sc.L + in.bin;
     float R_, T_;
-    slab_RT(in.c, in.lam, __ldg(a.sc.mat_a + k), __ldg(a.sc.mat_b + k) + in.s * __ldg(a.sc.mat_c + k), in.d, R_, T_);
+    glass_rt<FILMS>(a.sc, in.mat, in.bin, in.c, in.s, in.d, R_, T_);
     return make_float2(R_, T_);
 }
 
@@ -272,6 +285,7 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
 // batch, chosen by Philox, is also evaluated exactly; if it is off by more
 // than 1e-3 in R or T, or if any row lies outside the trained box, the whole
 // batch is evaluated exactly instead.
+template <bool FILMS>
 __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
     __shared__ InferSmem s;
     __shared__ float2 out[8][32];
@@ -313,8 +327,8 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
             row_input(a, kl < nvalid ? r0 + kl : total, total, il);
             row_input(a, kh < nvalid ? r0 + kh : total, total, ih);
             float xl[4], xh[4], yl[2], yh[2];
-            features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
-            features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
+            features(il.c, il.lam, il.s, row_alpha_d<FILMS>(a.sc, il), xl);
+            features(ih.c, ih.lam, ih.s, row_alpha_d<FILMS>(a.sc, ih), xh);
             tile_forward(s, xl, xh, lane, yl, yh);
             if (t == 0) {
                 out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
@@ -333,12 +347,12 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
         const int pick = (int)(pr.x % (uint32_t)nvalid);
         int bad = 0;
         if (lane == pick) {
-            const float2 e = exact_row(a, in);
+            const float2 e = exact_row<FILMS>(a, in);
             bad = fabsf(e.x - y.x) > kMlpProbeTol || fabsf(e.y - y.y) > kMlpProbeTol;
         }
         bad = __shfl_sync(kFull, bad, pick);
         if (!a.raw && (!box_ok || bad)) {
-            if (valid) y = exact_row(a, in);
+            if (valid) y = exact_row<FILMS>(a, in);
             if (lane == 0) ++n_fb;
         }
         if (valid) {
@@ -356,6 +370,7 @@ __global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
 
 // The exact slab for the same query rows, one thread per (query, bin): the
 // glass evaluations of a bounce as one dense, divergence-free pass.
+template <bool FILMS>
 __global__ void __launch_bounds__(256) k_slab_rows(MlpRows a) {
     int64_t total = a.n;
     if (a.mode == 1) {
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(256) k_slab_rows(MlpRows a) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
         RowIn in;
         row_input(a, r, total, in);
-        const float2 y = exact_row(a, in);
+        const float2 y = exact_row<FILMS>(a, in);
         if (a.mode == 0) {
             a.R[r] = y.x;
             a.T[r] = y.y;
@@ -681,9 +696,24 @@ __global__ void k_mlp_data(DevScene sc, uint32_t mat, int64_t n, uint32_t seed, 
     const float ac = (1.0f - f) * __ldg(sc.mat_b + k0) + f * __ldg(sc.mat_b + k1);
     const float da = (1.0f - f) * __ldg(sc.mat_c + k0) + f * __ldg(sc.mat_c + k1);
     float R_, T_;
-    slab_RT(c, lam, nn, ac + st * da, d, R_, T_);
+    const int J = sc.mat_nfilm ? __ldg(sc.mat_nfilm + mat) : 0;
+    float film_a = 0.0f;   // the films' normal-incidence absorbance (feature x3)
+    if (J == 0) {
+        slab_RT(c, lam, nn, ac + st * da, d, R_, T_);
+    } else {   // coated glass: film curves interpolated between the same bins
+        float nf[kMaxFilms], kf[kMaxFilms], tf[kMaxFilms];
+        for (int j = 0; j < J; ++j) {
+            const size_t f0 = ((size_t)mat * kMaxFilms + j) * L + lo, f1 = ((size_t)mat * kMaxFilms + j) * L + hi;
+            nf[j] = (1.0f - f) * __ldg(sc.film_n + f0) + f * __ldg(sc.film_n + f1);
+            kf[j] = (1.0f - f) * (__ldg(sc.film_k + f0) + st * __ldg(sc.film_dk + f0)) +
+                    f * (__ldg(sc.film_k + f1) + st * __ldg(sc.film_dk + f1));
+            tf[j] = __ldg(sc.film_t + (size_t)mat * kMaxFilms + j);
+        }
+        coated_RT(c, lam, nn, ac + st * da, d, J, nf, kf, tf, R_, T_);
+        for (int j = 0; j < J; ++j) film_a = fmaf(12.566370614359172f * kf[j], tf[j] / lam, film_a);
+    }
     float x[4];
-    features(c, lam, st, (ac + st * da) * d, x);
+    features(c, lam, st, (ac + st * da) * d + film_a, x);
     for (int k = 0; k < 4; ++k) X[4 * i + k] = x[k];
     Y[2 * i] = rt_to_out(R_);
     Y[2 * i + 1] = rt_to_out(T_);
@@ -757,12 +787,18 @@ size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 #endif
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
     const int blocks = sm_count * SDDM_MLP_BLOCKS_PER_SM;
-    k_mlp_rows<<<blocks, 256, 0, stream>>>(a);
+    if (a.sc.mat_nfilm)
+        k_mlp_rows<true><<<blocks, 256, 0, stream>>>(a);
+    else
+        k_mlp_rows<false><<<blocks, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
-    k_slab_rows<<<sm_count * 8, 256, 0, stream>>>(a);
+    if (a.sc.mat_nfilm)
+        k_slab_rows<true><<<sm_count * 8, 256, 0, stream>>>(a);
+    else
+        k_slab_rows<false><<<sm_count * 8, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

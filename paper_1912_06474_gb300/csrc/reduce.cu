@@ -69,10 +69,8 @@ __global__ void k_glass_eval(DevScene sc, uint32_t mat, int n, const float *cos_
     const int L = sc.L;
     int i = bin[q];
     i = i < 0 ? 0 : (i >= L ? L - 1 : i);
-    const size_t k = (size_t)mat * L + i;
-    const float al = sc.mat_b[k] + s[q] * sc.mat_c[k];
     float r_, t_;
-    slab_RT(cos_t[q], sc.lam[i], sc.mat_a[k], al, thick[q], r_, t_);
+    glass_rt(sc, (int)mat, i, cos_t[q], s[q], thick[q], r_, t_);
     R[q] = r_;
     T[q] = t_;
 }

@@ -91,6 +91,7 @@ struct sddm_ctx {
     sddm_build_opts opts{};
     // device scene
     DevBuf d_wcmf, d_lam, d_kind, d_a, d_b, d_c, d_thick, d_tri_n, d_tri_obj, d_light_v, d_light_cdf;
+    DevBuf d_nfilm, d_film_n, d_film_k, d_film_dk, d_film_t;
     DevBuf d_gnodes, d_gtris;
     float light_area = 0.f;
     int n_light = 0;
@@ -250,6 +251,35 @@ int sddm_add_glass_slab(sddm_ctx *ctx, const float *n, const float *alpha_clear,
     return add_mat(ctx, std::move(m), mat, "sddm_add_glass_slab");
 }
 
+int sddm_add_coated_glass(sddm_ctx *ctx, const float *n, const float *alpha_clear, const float *dalpha,
+                          float thickness_m, float s_default, int n_films, const float *film_n, const float *film_k,
+                          const float *film_dk, const float *film_t_nm, uint32_t *mat) {
+    NEED_SPECTRUM("sddm_add_coated_glass");
+    if (n_films < 0 || n_films > SDDM_MAX_FILMS || (n_films > 0 && (!film_n || !film_k || !film_dk || !film_t_nm)))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_coated_glass: 0..4 films with n, k, dk and thickness arrays");
+    const int L = ctx->L;
+    for (int j = 0; j < n_films; ++j) {
+        if (!finite_range(film_n + (size_t)j * L, L, 1.0f, 10.f) || !finite_range(film_k + (size_t)j * L, L, 0.0f, 10.f) ||
+            !finite_range(film_dk + (size_t)j * L, L, -10.f, 10.f) || !(film_t_nm[j] >= 0.0f && film_t_nm[j] < 1e5f))
+            return fail(SDDM_ERR_INVALID_ARG,
+                        "sddm_add_coated_glass: film n in [1,10], k >= 0, 0 <= thickness < 1e5 nm");
+        for (int i = 0; i < L; ++i)
+            if (film_k[(size_t)j * L + i] + film_dk[(size_t)j * L + i] < 0.0f)
+                return fail(SDDM_ERR_INVALID_ARG, "sddm_add_coated_glass: film k + dk must stay >= 0");
+    }
+    uint32_t id = 0;
+    int rc = sddm_add_glass_slab(ctx, n, alpha_clear, dalpha, thickness_m, s_default, &id);
+    if (rc != SDDM_OK) return rc;
+    Material &m = ctx->mats[id];
+    m.n_film = n_films;
+    m.film_n.assign(film_n ? film_n : n, (film_n ? film_n : n) + (size_t)n_films * L);
+    m.film_k.assign(film_k ? film_k : n, (film_k ? film_k : n) + (size_t)n_films * L);
+    m.film_dk.assign(film_dk ? film_dk : n, (film_dk ? film_dk : n) + (size_t)n_films * L);
+    for (int j = 0; j < n_films; ++j) m.film_t[j] = film_t_nm[j];
+    if (mat) *mat = id;
+    return SDDM_OK;
+}
+
 int sddm_add_emitter(sddm_ctx *ctx, const float *Le, uint32_t *mat) {
     NEED_SPECTRUM("sddm_add_emitter");
     if (!Le || !finite_range(Le, ctx->L, 0.0f, 1e12f)) return fail(SDDM_ERR_INVALID_ARG, "sddm_add_emitter: Le >= 0");
@@ -379,6 +409,30 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         }
         thick[m] = mt.thick;
     }
+    // coating films of glass materials, [m][4][L] (+ thickness [m][4])
+    bool any_film = false;
+    for (int m = 0; m < M; ++m) any_film |= ctx->mats[m].n_film > 0;
+    std::vector<int> nfilm(M, 0);
+    std::vector<float> FN, FK, FDK, FT;
+    if (any_film) {
+        FN.assign((size_t)M * 4 * L, 1.f);
+        FK.assign((size_t)M * 4 * L, 0.f);
+        FDK.assign((size_t)M * 4 * L, 0.f);
+        FT.assign((size_t)M * 4, 0.f);
+        for (int m = 0; m < M; ++m) {
+            const Material &mt = ctx->mats[m];
+            nfilm[m] = mt.n_film;
+            for (int j = 0; j < mt.n_film; ++j) {
+                for (int i = 0; i < L; ++i) {
+                    const size_t f = ((size_t)m * 4 + j) * L + i;
+                    FN[f] = mt.film_n[(size_t)j * L + i];
+                    FK[f] = mt.film_k[(size_t)j * L + i];
+                    FDK[f] = mt.film_dk[(size_t)j * L + i];
+                }
+                FT[(size_t)m * 4 + j] = mt.film_t[j];
+            }
+        }
+    }
 
     // --- hierarchies: global, and the subdomain grid
     int n_threads = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
@@ -439,7 +493,10 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         (e = ctx->d_tri_obj.upload(tri_obj, s)) || (e = ctx->d_light_v.upload(light_v, s)) ||
         (e = ctx->d_light_cdf.upload(light_cdf, s)) || (e = ctx->d_gnodes.upload(global.nodes, s)) ||
         (e = ctx->d_gtris.upload(global.tris, s)) || (e = ctx->d_cell_nodes.upload(cell_nodes, s)) ||
-        (e = ctx->d_cell_tris.upload(cell_tris, s)) || (e = ctx->d_cell_root.upload(cell_root, s)))
+        (e = ctx->d_cell_tris.upload(cell_tris, s)) || (e = ctx->d_cell_root.upload(cell_root, s)) ||
+        (any_film && ((e = ctx->d_nfilm.upload(nfilm, s)) || (e = ctx->d_film_n.upload(FN, s)) ||
+                      (e = ctx->d_film_k.upload(FK, s)) || (e = ctx->d_film_dk.upload(FDK, s)) ||
+                      (e = ctx->d_film_t.upload(FT, s)))))
         return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_build: device allocation failed")
                                               : cuda_fail(e, "sddm_build: upload");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sddm_build: synchronize");
@@ -454,6 +511,11 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     d.mat_b = ctx->d_b.as<float>();
     d.mat_c = ctx->d_c.as<float>();
     d.mat_thick = ctx->d_thick.as<float>();
+    d.mat_nfilm = any_film ? ctx->d_nfilm.as<int>() : nullptr;
+    d.film_n = any_film ? ctx->d_film_n.as<float>() : nullptr;
+    d.film_k = any_film ? ctx->d_film_k.as<float>() : nullptr;
+    d.film_dk = any_film ? ctx->d_film_dk.as<float>() : nullptr;
+    d.film_t = any_film ? ctx->d_film_t.as<float>() : nullptr;
     d.tri_n = ctx->d_tri_n.as<float4>();
     d.tri_obj = ctx->d_tri_obj.as<int>();
     d.n_light = (int)light_cdf.size();
@@ -989,7 +1051,12 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
 
 // ---------------------------------------------------- learned glass surrogate
 static bool same_curves(const Material &a, const Material &b) {
-    return a.kind == kGlass && b.kind == kGlass && a.a == b.a && a.b == b.b && a.c == b.c;
+    if (!(a.kind == kGlass && b.kind == kGlass && a.a == b.a && a.b == b.b && a.c == b.c && a.n_film == b.n_film &&
+          a.film_n == b.film_n && a.film_k == b.film_k && a.film_dk == b.film_dk))
+        return false;
+    for (int j = 0; j < a.n_film; ++j)
+        if (a.film_t[j] != b.film_t[j]) return false;
+    return true;
 }
 
 static int mlp_net_for(sddm_ctx *ctx, uint32_t mat, bool create, sddm_ctx::MlpNet **out) {

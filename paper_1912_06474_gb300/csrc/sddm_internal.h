@@ -45,6 +45,12 @@ struct DevScene {
     const float *mat_b;       // [n_mat][L] -   | k | alpha_clear | rho (diffuse emitter)
     const float *mat_c;       // [n_mat][L] -   | - | dalpha
     const float *mat_thick;   // [n_mat]
+    // thin-film coatings of glass materials (both faces; NULL when no material has one)
+    const int *mat_nfilm;     // [n_mat] films per face, 0..4
+    const float *film_n;      // [n_mat][4][L] real index
+    const float *film_k;      // [n_mat][4][L] extinction at s = 0
+    const float *film_dk;     // [n_mat][4][L] extinction added at s = 1
+    const float *film_t;      // [n_mat][4] thickness, nm
     const float4 *tri_n;      // [nt] unit CCW normal, .w = material id (int bits)
     const int *tri_obj;       // [nt]
     int n_light;
@@ -82,6 +88,10 @@ struct Material {
     int kind;
     std::vector<float> a, b, c;
     float thick = 0.f, s_default = 0.f;
+    // coating films (glass): per film n, k, dk curves [L] and thickness (nm)
+    int n_film = 0;
+    std::vector<float> film_n, film_k, film_dk;   // [n_film][L]
+    float film_t[4] = {0.f, 0.f, 0.f, 0.f};
 };
 
 // A built BVH in device-ready packed form.

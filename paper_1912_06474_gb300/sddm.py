@@ -26,7 +26,8 @@ METHODS = {"megakernel": METHOD_MEGAKERNEL, "ddm": METHOD_DDM}
 BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP, "mlp_raw": BSDF_MLP_RAW}
 
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
-            "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_emitter",
+            "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_coated_glass",
+            "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
             "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
             "sddm_render_noalloc", "sddm_mlp_train", "sddm_mlp_get_weights", "sddm_mlp_set_weights",
@@ -95,6 +96,7 @@ def _load():
         "sddm_add_lambertian": ([P, P, P], I),
         "sddm_add_conductor": ([P, P, P, P], I),
         "sddm_add_glass_slab": ([P, P, P, P, C.c_float, C.c_float, P], I),
+        "sddm_add_coated_glass": ([P, P, P, P, C.c_float, C.c_float, C.c_int, P, P, P, P, P], I),
         "sddm_add_emitter": ([P, P, P], I),
         "sddm_add_diffuse_emitter": ([P, P, P, P], I),
         "sddm_set_mesh": ([P, P, I, P, I, P, P], I),
@@ -181,6 +183,15 @@ class Context:
                 _check(lib.sddm_add_lambertian(h, _ptr(_f32(m.rho)), C.byref(mid)))
             elif m.kind == S.CONDUCTOR:
                 _check(lib.sddm_add_conductor(h, _ptr(_f32(m.n)), _ptr(_f32(m.k)), C.byref(mid)))
+            elif m.kind == S.GLASS and m.layers:
+                fn = _f32(np.stack([f["n"] for f in m.layers]))
+                fk = _f32(np.stack([f["k"] for f in m.layers]))
+                fd = _f32(np.stack([f["dk"] for f in m.layers]))
+                ft = _f32([f["t_nm"] for f in m.layers])
+                _check(lib.sddm_add_coated_glass(h, _ptr(_f32(m.n)), _ptr(_f32(m.alpha_clear)),
+                                                 _ptr(_f32(m.dalpha)), float(m.thickness_m), float(m.s_default),
+                                                 len(m.layers), _ptr(fn), _ptr(fk), _ptr(fd), _ptr(ft),
+                                                 C.byref(mid)))
             elif m.kind == S.GLASS:
                 _check(lib.sddm_add_glass_slab(h, _ptr(_f32(m.n)), _ptr(_f32(m.alpha_clear)),
                                                _ptr(_f32(m.dalpha)), float(m.thickness_m),

@@ -89,3 +89,15 @@ def test_served_output_map(oracle_mod):
         assert np.allclose(rt, [[R, T]] * 4, rtol=1e-6, atol=1e-9)
     p[8768], p[8769] = np.log(5e-4), np.log(1e-6)
     assert np.array_equal(oracle_mod.mlp_rt(p, X), np.zeros((4, 2)))
+
+
+def test_feature_film_absorbance_adds_to_the_substrate(oracle_mod):
+    """Coating films enter x3 through their Beer-Lambert absorbance: a film of
+    absorbance A multiplies the transmittance by exp(-A), exactly as extra
+    substrate absorption alpha' d = alpha d + A would."""
+    for A in (0.0, 0.3, 1.7):
+        a = oracle_mod.mlp_features(0.4, 650.0, 0.7, 0.004, 25.0, A)[3]
+        b = oracle_mod.mlp_features(0.4, 650.0, 0.7, 0.004, 25.0 + A / 0.004)[3]
+        assert abs(a - b) <= 1e-12
+        t0 = (oracle_mod.mlp_features(0.4, 650.0, 0.7, 0.004, 25.0)[3] + 1) / 2
+        assert abs((a + 1) / 2 - t0 * np.exp(-A)) <= 1e-12
