@@ -306,6 +306,19 @@ int sddm_set_profiling(sddm_ctx *ctx, int flags);
 int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, const int32_t *bin,
                     const float *s, const float *thickness_m, float *R, float *T, int mode);
 
+/* Reflectance spectra of RGB values by Cohen and Kappauf's Matrice-R theory
+ * (Sec. 3: a spectrum is its fundamental, which carries the colour stimulus,
+ * plus a metameric black with X = Y = Z = 0; the fundamental of a stimulus
+ * follows from one matrix equation): XYZ = M rgb, then
+ * rho = A (A^T A)^-1 XYZ with A_i = w_i cmf(lambda_i) / sum_i w_i ybar_i, the
+ * context's bins, weights and colour-matching functions (sddm_set_spectrum;
+ * rho = 1 has Y = 1). rgb: HOST [n][3]; rgb_to_xyz: HOST [3][3] row-major, or
+ * NULL for linear sRGB with the D65 white; spectra: HOST [n][L] written.
+ * clamp01 != 0 limits the result to [0, 1] (physical reflectances; the round
+ * trip back to the same RGB then holds only where nothing was clamped). */
+int sddm_rgb_to_spectrum(sddm_ctx *ctx, int n, const float *rgb, const float *rgb_to_xyz, float *spectra,
+                         int clamp01);
+
 /* Philox4x32-10 block for counters ctr[n][4] under key {key0, key1}: out[n][4]
  * words. ctr and out are DEVICE arrays. */
 int sddm_philox(sddm_ctx *ctx, int n, const uint32_t *ctr, uint32_t key0, uint32_t key1,

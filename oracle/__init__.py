@@ -400,3 +400,51 @@ class Oracle:
         occ = self.lib.orc_shadow(self._h, _ptr(o), _ptr(d), float(tmax), int(excl_prim),
                                   1 if brute_force else 0, C.byref(ncr), _ptr(cobj), _ptr(ccos))
         return bool(occ), list(zip(cobj[:ncr.value].tolist(), ccos[:ncr.value].tolist()))
+
+
+# --------------------------------------------------------------------------
+# RGB -> spectrum by Cohen and Kappauf's matrix R (Sec. 3 of the paper: every
+# spectrum splits into a fundamental, which carries its colour stimulus, and a
+# metameric black, which has X = Y = Z = 0; the fundamental of a stimulus
+# follows from one matrix equation). FP64, numpy.
+# --------------------------------------------------------------------------
+# Linear sRGB primaries with the D65 white, RGB -> XYZ (IEC 61966-2-1).
+SRGB_TO_XYZ = np.array([[0.4124, 0.3576, 0.1805],
+                        [0.2126, 0.7152, 0.0722],
+                        [0.0193, 0.1192, 0.9505]])
+
+
+def color_basis(quad_w, cmf):
+    """A [L,3]: the XYZ of a reflectance spectrum rho under an equal-energy
+    illuminant is A^T rho, with A = w_i cmf(lambda_i) / sum_i w_i ybar_i
+    (so that rho = 1 has Y = 1)."""
+    W = np.asarray(quad_w, np.float64)[:, None] * np.asarray(cmf, np.float64)
+    return W / W[:, 1].sum()
+
+
+def matrice_r(A):
+    """Cohen's matrix R = A (A^T A)^-1 A^T, the orthogonal projector onto the
+    colour-stimulus space: R N is the fundamental of spectrum N."""
+    return A @ np.linalg.solve(A.T @ A, A.T)
+
+
+def fundamental_from_xyz(xyz, A):
+    """The fundamental spectrum with tristimulus xyz: A (A^T A)^-1 xyz."""
+    return A @ np.linalg.solve(A.T @ A, np.asarray(xyz, np.float64).T)
+
+
+def rgb_to_spectrum(rgb, quad_w, cmf, rgb_to_xyz=None, clamp=False):
+    """Spectra [n,L] of RGB values [n,3]: XYZ = M rgb, then the fundamental;
+    with clamp, limited to [0, 1] afterwards."""
+    A = color_basis(quad_w, cmf)
+    M = SRGB_TO_XYZ if rgb_to_xyz is None else np.asarray(rgb_to_xyz, np.float64)
+    xyz = np.atleast_2d(np.asarray(rgb, np.float64)) @ M.T
+    s = fundamental_from_xyz(xyz, A).T
+    return np.clip(s, 0.0, 1.0) if clamp else s
+
+
+def spectrum_to_rgb(spec, quad_w, cmf, rgb_to_xyz=None):
+    A = color_basis(quad_w, cmf)
+    M = SRGB_TO_XYZ if rgb_to_xyz is None else np.asarray(rgb_to_xyz, np.float64)
+    xyz = np.atleast_2d(np.asarray(spec, np.float64)) @ A
+    return np.linalg.solve(M, xyz.T).T

@@ -75,6 +75,28 @@ __global__ void k_glass_eval(DevScene sc, uint32_t mat, int n, const float *cos_
     T[q] = t_;
 }
 
+// Spectra of RGB values: rho_i = sum_k Q[i][k] rgb_k with Q = A (A^T A)^-1 M
+// (Cohen's fundamental of the stimulus XYZ = M rgb), optionally clamped to
+// [0, 1]. One thread per (value, bin).
+__global__ void k_rgb_to_spectrum(int n, int L, const float *Q, const float *rgb, float *out, int clamp01) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * L) return;
+    const int q = (int)(t / L), i = (int)(t - (int64_t)q * L);
+    float v = Q[3 * i] * rgb[3 * q];
+    v = fmaf(Q[3 * i + 1], rgb[3 * q + 1], v);
+    v = fmaf(Q[3 * i + 2], rgb[3 * q + 2], v);
+    if (clamp01) v = fminf(fmaxf(v, 0.0f), 1.0f);
+    out[t] = v;
+}
+
+cudaError_t launch_rgb_to_spectrum(int n, int L, const float *Q, const float *rgb, float *out, int clamp01,
+                                   cudaStream_t stream) {
+    const int64_t total = (int64_t)n * L;
+    if (total == 0) return cudaSuccess;
+    k_rgb_to_spectrum<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(n, L, Q, rgb, out, clamp01);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_glass_eval(const DevScene &sc, uint32_t mat, int n, const float *cos_t, const int32_t *bin,
                               const float *s, const float *thick, float *R, float *T, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;

@@ -1332,6 +1332,57 @@ int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, 
     return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_glass_eval");
 }
 
+int sddm_rgb_to_spectrum(sddm_ctx *ctx, int n, const float *rgb, const float *rgb_to_xyz, float *spectra,
+                         int clamp01) {
+    NEED_SPECTRUM("sddm_rgb_to_spectrum");
+    if (n < 0 || (n > 0 && (!rgb || !spectra)) || n > (1 << 24))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_rgb_to_spectrum: 0 <= n <= 2^24 values, rgb and spectra required");
+    const int L = ctx->L;
+    // A = w_i cmf_i / sum_i w_i ybar_i; Q = A (A^T A)^-1 M, in double on the host (3 x 3 solve)
+    const double srgb[9] = {0.4124, 0.3576, 0.1805, 0.2126, 0.7152, 0.0722, 0.0193, 0.1192, 0.9505};
+    double M[9];
+    for (int k = 0; k < 9; ++k) M[k] = rgb_to_xyz ? (double)rgb_to_xyz[k] : srgb[k];
+    std::vector<double> A((size_t)L * 3);
+    double ysum = 0.0;
+    for (int i = 0; i < L; ++i) ysum += (double)ctx->quad_w[i] * ctx->cmf[3 * i + 1];
+    if (!(ysum > 0.0)) return fail(SDDM_ERR_INVALID_ARG, "sddm_rgb_to_spectrum: the spectrum has no luminance");
+    for (int i = 0; i < L; ++i)
+        for (int c = 0; c < 3; ++c) A[3 * i + c] = (double)ctx->quad_w[i] * ctx->cmf[3 * i + c] / ysum;
+    double G[9] = {0};   // A^T A
+    for (int i = 0; i < L; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[3 * a + b] += A[3 * i + a] * A[3 * i + b];
+    const double det = G[0] * (G[4] * G[8] - G[5] * G[7]) - G[1] * (G[3] * G[8] - G[5] * G[6]) +
+                       G[2] * (G[3] * G[7] - G[4] * G[6]);
+    if (!(std::fabs(det) > 0.0)) return fail(SDDM_ERR_INVALID_ARG, "sddm_rgb_to_spectrum: singular colour basis");
+    const double Gi[9] = {(G[4] * G[8] - G[5] * G[7]) / det, (G[2] * G[7] - G[1] * G[8]) / det,
+                          (G[1] * G[5] - G[2] * G[4]) / det, (G[5] * G[6] - G[3] * G[8]) / det,
+                          (G[0] * G[8] - G[2] * G[6]) / det, (G[2] * G[3] - G[0] * G[5]) / det,
+                          (G[3] * G[7] - G[4] * G[6]) / det, (G[1] * G[6] - G[0] * G[7]) / det,
+                          (G[0] * G[4] - G[1] * G[3]) / det};
+    std::vector<float> Q((size_t)L * 3);
+    for (int i = 0; i < L; ++i)
+        for (int k = 0; k < 3; ++k) {
+            double v = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) v += A[3 * i + a] * Gi[3 * a + b] * M[3 * b + k];
+            Q[3 * i + k] = (float)v;
+        }
+    if (n == 0) return SDDM_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    DevBuf dq, din, dout;
+    cudaStream_t s = ctx->stream;
+    if (e == cudaSuccess) e = dq.upload(Q, s);
+    if (e == cudaSuccess) e = din.ensure(sizeof(float) * 3 * (size_t)n);
+    if (e == cudaSuccess) e = dout.ensure(sizeof(float) * (size_t)n * L);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(din.p, rgb, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_rgb_to_spectrum(n, L, dq.as<float>(), din.as<float>(), dout.as<float>(), clamp01, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(spectra, dout.p, sizeof(float) * (size_t)n * L, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_rgb_to_spectrum");
+}
+
 int sddm_philox(sddm_ctx *ctx, int n, const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out) {
     if (!ctx || n < 0 || (n > 0 && (!ctr || !out))) return fail(SDDM_ERR_INVALID_ARG, "sddm_philox: bad arguments");
     if ((reinterpret_cast<uintptr_t>(ctr) | reinterpret_cast<uintptr_t>(out)) & 15)

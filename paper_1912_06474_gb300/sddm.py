@@ -27,6 +27,7 @@ BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP, "mlp_raw": BSDF_MLP_RAW}
 
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
             "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_coated_glass",
+            "sddm_rgb_to_spectrum",
             "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
             "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
@@ -97,6 +98,7 @@ def _load():
         "sddm_add_conductor": ([P, P, P, P], I),
         "sddm_add_glass_slab": ([P, P, P, P, C.c_float, C.c_float, P], I),
         "sddm_add_coated_glass": ([P, P, P, P, C.c_float, C.c_float, C.c_int, P, P, P, P, P], I),
+        "sddm_rgb_to_spectrum": ([P, C.c_int, P, P, P, C.c_int], I),
         "sddm_add_emitter": ([P, P, P], I),
         "sddm_add_diffuse_emitter": ([P, P, P, P], I),
         "sddm_set_mesh": ([P, P, I, P, I, P, P], I),
@@ -362,6 +364,16 @@ class Context:
         _check(lib.sddm_glass_eval(self._h, int(mat), n, cos_t.data_ptr(), bins.data_ptr(), s.data_ptr(),
                                    thick.data_ptr(), R.data_ptr(), T.data_ptr(), BSDFS[mode]))
         return R, T
+
+    def rgb_to_spectrum(self, rgb, rgb_to_xyz=None, clamp=False):
+        """sddm_rgb_to_spectrum: spectra [n, L] (numpy float32) of RGB values [n, 3]
+        on the spectrum of the current scene (set_scene first)."""
+        rgb = np.ascontiguousarray(np.atleast_2d(rgb), np.float32)
+        out = np.zeros((rgb.shape[0], self.scene.L), np.float32)
+        m = None if rgb_to_xyz is None else np.ascontiguousarray(rgb_to_xyz, np.float32)
+        _check(lib.sddm_rgb_to_spectrum(self._h, int(rgb.shape[0]), _ptr(rgb), _ptr(m) if m is not None else None,
+                                        _ptr(out), 1 if clamp else 0))
+        return out
 
     def philox(self, ctr, key0, key1):
         """sddm_philox on a CUDA int32/uint32 tensor [n,4]; returns [n,4] words (int32 view)."""
