@@ -28,7 +28,8 @@ def test_rgb_to_spectrum_matches_oracle(oracle_mod, L):
         if not clamp:
             assert np.abs(back - rgb).max() <= 1e-5
         else:
-            ok = np.all((want >= 0) & (want <= 1), axis=1)
+            free = oracle_mod.rgb_to_spectrum(rgb.astype(np.float64), sc.quad_w, sc.cmf, clamp=False)
+            ok = np.all((free >= 0) & (free <= 1), axis=1)
             assert np.abs(back[ok] - rgb[ok]).max() <= 1e-5
             print(f"L={L}: {ok.mean():.1%} of the RGB values have a physical fundamental")
     ctx.close()
