@@ -66,6 +66,10 @@ typedef struct {
     int64_t queue_capacity;   /* rays per subdomain queue (0 = automatic) */
     int blocks_per_sm;        /* persistent blocks per SM for the DDM trace (0 = automatic) */
     int64_t paths_in_flight;  /* path slots processed at once (0 = automatic) */
+    int bvh_in_host_memory;   /* 1: the subdomain BVHs (nodes and triangle references) stay in pinned host
+                                 memory that the trace kernel reads over the coherent host link (NVLink-C2C
+                                 on Grace-based GPUs) instead of a copy in HBM -- for scenes whose subdomains
+                                 exceed device memory (Sec. 5 loads subdomains up to a memory limit); 0 = HBM */
 } sddm_build_opts;
 
 typedef struct {

@@ -37,6 +37,39 @@ static int fail(int code, const std::string &msg) {
 }
 
 // Owned device allocation.
+// Pinned host memory mapped into the device's address space: the GPU reads it
+// directly (over NVLink-C2C on Grace-based systems) without a copy in HBM.
+struct HostBuf {
+    void *h = nullptr, *d = nullptr;
+    size_t bytes = 0;
+    HostBuf() = default;
+    HostBuf(const HostBuf &) = delete;
+    HostBuf &operator=(const HostBuf &) = delete;
+    ~HostBuf() { release(); }
+    void release() {
+        if (h) cudaFreeHost(h);
+        h = d = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    cudaError_t upload(const std::vector<T> &v) {
+        release();
+        const size_t n = std::max<size_t>(v.size() * sizeof(T), 16);
+        cudaError_t e = cudaHostAlloc(&h, n, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            h = nullptr;
+            return e;
+        }
+        bytes = n;
+        if (!v.empty()) std::memcpy(h, v.data(), v.size() * sizeof(T));
+        return cudaHostGetDevicePointer(&d, h, 0);
+    }
+    template <typename T>
+    const T *as() const {
+        return static_cast<const T *>(d);
+    }
+};
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -98,6 +131,7 @@ struct sddm_ctx {
     DevScene dev{};
     DDMScene ddm{};
     DevBuf d_cell_nodes, d_cell_tris, d_cell_root, d_cell_planes, d_cell_next;
+    HostBuf h_cell_nodes, h_cell_tris;   // the same, in host memory (bvh_in_host_memory)
     // per-render scratch
     DevBuf d_info, d_state, d_out_tab, d_aov_xyz_tab, d_aov_prim_tab, d_samples, d_first, d_counters, d_err;
     DDMBuffers ddm_buf;
@@ -338,7 +372,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     default_opts(o);
     if (o.grid[0] > 64 || o.grid[1] > 64 || o.grid[2] > 64 || o.leaf_size > kMaxLeaf || o.sah_bins < 4 ||
         o.sah_bins > 64 || o.queue_capacity < 0 || o.blocks_per_sm < 0 || o.blocks_per_sm > 32 ||
-        o.paths_in_flight < 0)
+        o.paths_in_flight < 0 || o.bvh_in_host_memory < 0 || o.bvh_in_host_memory > 1)
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: options out of range");
     // every mesh material must exist (the material list may have changed since set_mesh)
     for (uint32_t m : ctx->mat_id)
@@ -492,8 +526,10 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         (e = ctx->d_c.upload(Cc, s)) || (e = ctx->d_thick.upload(thick, s)) || (e = ctx->d_tri_n.upload(tri_n, s)) ||
         (e = ctx->d_tri_obj.upload(tri_obj, s)) || (e = ctx->d_light_v.upload(light_v, s)) ||
         (e = ctx->d_light_cdf.upload(light_cdf, s)) || (e = ctx->d_gnodes.upload(global.nodes, s)) ||
-        (e = ctx->d_gtris.upload(global.tris, s)) || (e = ctx->d_cell_nodes.upload(cell_nodes, s)) ||
-        (e = ctx->d_cell_tris.upload(cell_tris, s)) || (e = ctx->d_cell_root.upload(cell_root, s)) ||
+        (e = ctx->d_gtris.upload(global.tris, s)) ||
+        (o.bvh_in_host_memory ? ((e = ctx->h_cell_nodes.upload(cell_nodes)) || (e = ctx->h_cell_tris.upload(cell_tris)))
+                              : ((e = ctx->d_cell_nodes.upload(cell_nodes, s)) || (e = ctx->d_cell_tris.upload(cell_tris, s)))) ||
+        (e = ctx->d_cell_root.upload(cell_root, s)) ||
         (any_film && ((e = ctx->d_nfilm.upload(nfilm, s)) || (e = ctx->d_film_n.upload(FN, s)) ||
                       (e = ctx->d_film_k.upload(FK, s)) || (e = ctx->d_film_dk.upload(FDK, s)) ||
                       (e = ctx->d_film_t.upload(FT, s)))))
@@ -540,8 +576,17 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
 #endif
     g.n_oct = (SDDM_MAX_SUBBINS >= 64 && 128 * g.n_cells <= kMaxBins) ? 64 : (SDDM_MAX_SUBBINS >= 8 && 16 * g.n_cells <= kMaxBins) ? 8 : 1;
     g.n_bins = 2 * g.n_cells * g.n_oct;
-    g.nodes = ctx->d_cell_nodes.as<float4>();
-    g.tris = ctx->d_cell_tris.as<float4>();
+    if (o.bvh_in_host_memory) {
+        g.nodes = ctx->h_cell_nodes.as<float4>();
+        g.tris = ctx->h_cell_tris.as<float4>();
+        ctx->d_cell_nodes.release();
+        ctx->d_cell_tris.release();
+    } else {
+        g.nodes = ctx->d_cell_nodes.as<float4>();
+        g.tris = ctx->d_cell_tris.as<float4>();
+        ctx->h_cell_nodes.release();
+        ctx->h_cell_tris.release();
+    }
     g.root = ctx->d_cell_root.as<int>();
     if ((e = ctx->d_cell_planes.ensure(sizeof(float4) * 2 * (size_t)g.n_cells)) ||
         (e = ctx->d_cell_next.ensure(sizeof(int4) * 2 * (size_t)g.n_cells)))
