@@ -67,7 +67,7 @@ class _RenderDesc(C.Structure):
                 ("seed", C.c_uint32), ("render_id", C.c_uint32), ("nee", C.c_int),
                 ("cam_pos", C.c_double * 3), ("cam_look", C.c_double * 3), ("cam_up", C.c_double * 3),
                 ("vfov_deg", C.c_double), ("ortho_height", C.c_double), ("s_override", C.c_void_p),
-                ("brute_force", C.c_int)]
+                ("brute_force", C.c_int), ("photon_map", C.c_void_p)]
 
 
 def _load():
@@ -88,6 +88,11 @@ def _load():
         lib.orc_u01.restype = C.c_double
         lib.orc_fresnel.argtypes = [C.c_double, C.c_double, C.c_double, P, P]
         lib.orc_slab.argtypes = [C.c_double] * 5 + [P, P]
+        lib.orc_photon_map_build.argtypes = [P, P, C.c_int64, C.c_double, C.c_int]
+        lib.orc_photon_map_build.restype = C.c_void_p
+        lib.orc_photon_map_free.argtypes = [P]
+        lib.orc_photon_map_get.argtypes = [P, P, P, P]
+        lib.orc_photon_map_get.restype = C.c_int64
         lib.orc_coated_face.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, P, P, P, C.c_int, P, P, P, P]
         lib.orc_coated_slab.argtypes = [C.c_double] * 5 + [C.c_int, P, P, P, P, P]
         lib.orc_conductor.argtypes = [C.c_double] * 3
@@ -291,6 +296,24 @@ def _layer_arrays(scene):
     return nl, ln, lk, ldk, lt
 
 
+class _PhotonMap:
+    """Owned oracle photon map (freed with the object)."""
+
+    def __init__(self, lib, h, L):
+        self.lib, self.h, self.L = lib, C.c_void_p(h), L
+
+    def photons(self):
+        n = self.lib.orc_photon_map_get(self.h, None, None, None)
+        pos, dirs, pw = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, self.L))
+        self.lib.orc_photon_map_get(self.h, _ptr(pos), _ptr(dirs), _ptr(pw))
+        return pos, dirs, pw
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.orc_photon_map_free(self.h)
+            self.h = None
+
+
 class Oracle:
     """FP64 oracle bound to one scene (inputs copied on construction)."""
 
@@ -352,7 +375,16 @@ class Oracle:
         self.lib.orc_camera_ray(C.byref(r), float(px), float(py), _ptr(o), _ptr(d))
         return o, d
 
-    def render_pixels(self, spec, pix=None, n_threads=0, per_sample=False, brute_force=False):
+    def photon_map(self, spec, n_photons, radius, n_threads=0):
+        """Photon map of this scene for the render ``spec`` (its seed, render id,
+        depth and coloration states): a handle for render_pixels."""
+        r, keep = self._render_desc(spec, False)
+        h = self.lib.orc_photon_map_build(self._h, C.byref(r), int(n_photons), float(radius), int(n_threads))
+        if not h:
+            raise RuntimeError("orc_photon_map_build failed")
+        return _PhotonMap(self.lib, h, self.scene.L)
+
+    def render_pixels(self, spec, pix=None, n_threads=0, per_sample=False, brute_force=False, photon_map=None):
         """Render the listed pixels (all if None). Returns a dict with ``xyz``
         [n,3]; with ``per_sample`` also ``sample_xyz`` [n,spp,3], ``first_prim``
         [n,spp], ``margin`` [n,spp] and ``cos_min`` [n,spp]; ``segments`` = (extension, shadow)."""
@@ -361,6 +393,8 @@ class Oracle:
         pix = np.ascontiguousarray(pix, dtype=np.int64)
         n = int(pix.shape[0])
         r, s_keep = self._render_desc(spec, brute_force)
+        if photon_map is not None:
+            r.photon_map = photon_map.h
         xyz = np.zeros((n, 3), np.float64)
         sx = fp = mg = cm = None
         if per_sample:

@@ -304,6 +304,335 @@ static void slab_rt(const orc_ctx *c, const orc_render_desc *r, int m, double co
     orc_coated_slab(cosv, c->lam[i], c->a[k], alpha, c->thick[m], J, nf, kf, tf, R, T);
 }
 
+/* ------------------------------------------------------- photon map --- */
+typedef struct {
+    int L;
+    int64_t n;                 /* stored photons */
+    double *pos, *dir, *pow;   /* [n][3], [n][3], [n][L] */
+    double radius;
+    double lo[3];              /* grid over the stored photons, cell = radius */
+    int dims[3];
+    int64_t *cell_start;       /* [cells + 1] */
+    int64_t *order;            /* photon indices sorted by cell */
+} orc_pmap;
+
+static void pm_slot_u(uint32_t i, uint32_t b, uint32_t slot, const orc_render_desc *r, double u[4])
+{
+    philox_u(i, 0xffffffffu, b, slot, r, u);
+}
+
+/* Trace photon i; write its deposits (at most D - 1) into rec[k] = {x, d, valid}, pw[k][L]. */
+static void trace_photon(const orc_ctx *c, const orc_render_desc *r, uint32_t i, double phi0_scale,
+                         double *rec, double *pw, double *Phi)
+{
+    const int L = c->L, D = r->max_depth;
+    for (int k = 0; k < D - 1; ++k)
+        rec[7 * k + 6] = 0.0;
+    if (c->n_light == 0 || D < 2)
+        return;
+    double u[4];
+    pm_slot_u(i, 0u, SLOT_LIGHT, r, u);
+    int li = c->n_light - 1;
+    for (int k = 0; k < c->n_light; ++k)
+        if (u[0] < (double)c->light_cdf[k]) {
+            li = k;
+            break;
+        }
+    int lt = c->light_tri[li];
+    const double *lv = c->v + 9 * (size_t)lt, *nl = c->ng + 3 * (size_t)lt;
+    double su = sqrt(u[1]);
+    double b0 = 1.0 - su, b1 = u[2] * su, b2 = 1.0 - b0 - b1;
+    double o[3], d[3];
+    for (int a = 0; a < 3; ++a)
+        o[a] = b0 * lv[a] + b1 * lv[3 + a] + b2 * lv[6 + a] + RAY_OFFSET * nl[a];
+    pm_slot_u(i, 0u, SLOT_BSDF, r, u);
+    orc_cosine_dir(nl, u[0], u[1], d);
+    const double *Le = c->a + (size_t)c->mat[lt] * L;
+    for (int l = 0; l < L; ++l)
+        Phi[l] = Le[l] * PI * c->light_area * phi0_scale;
+    int excl_prim = lt, excl_obj = -1, changed = 0;
+    for (int b = 1; b <= D - 1; ++b) {
+        orc_hit h;
+        if (!orc_trace_closest(c, o, d, excl_prim, excl_obj, r->brute_force, &h, NULL))
+            return;
+        int tri = h.prim, mat = c->mat[tri], kind = c->kind[mat];
+        const double *ng = c->ng + 3 * (size_t)tri;
+        double x[3] = {o[0] + h.t * d[0], o[1] + h.t * d[1], o[2] + h.t * d[2]};
+        double cd = dot3(d, ng);
+        double ns[3];
+        for (int a = 0; a < 3; ++a)
+            ns[a] = cd < 0.0 ? ng[a] : -ng[a];
+        const double *mA = c->a + (size_t)mat * L, *mB = c->b + (size_t)mat * L;
+        if (kind == ORC_EMITTER)
+            return;
+        if (kind == ORC_LAMBERT || kind == ORC_DIFFUSE_EMITTER) {
+            if (changed) {
+                double *q = rec + 7 * (b - 1);
+                for (int a = 0; a < 3; ++a) {
+                    q[a] = x[a];
+                    q[3 + a] = d[a];
+                }
+                q[6] = 1.0;
+                for (int l = 0; l < L; ++l)
+                    pw[(size_t)(b - 1) * L + l] = Phi[l];
+            }
+            if (b == D - 1)
+                return;
+            const double *rho = kind == ORC_LAMBERT ? mA : mB;
+            pm_slot_u(i, (uint32_t)b, SLOT_BSDF, r, u);
+            orc_cosine_dir(ns, u[0], u[1], d);
+            for (int l = 0; l < L; ++l)
+                Phi[l] *= rho[l];
+            for (int a = 0; a < 3; ++a)
+                o[a] = x[a] + RAY_OFFSET * ns[a];
+            excl_prim = tri;
+            excl_obj = -1;
+            changed = 1;
+        } else if (kind == ORC_CONDUCTOR) {
+            if (b == D - 1)
+                return;
+            double cosv = fabs(cd);
+            for (int l = 0; l < L; ++l)
+                Phi[l] *= orc_conductor(cosv, mA[l], mB[l]);
+            for (int a = 0; a < 3; ++a) {
+                d[a] = d[a] - 2.0 * cd * ng[a];
+                o[a] = x[a] + RAY_OFFSET * ns[a];
+            }
+            excl_prim = tri;
+            excl_obj = -1;
+            changed = 1;
+        } else {
+            if (b == D - 1)
+                return;
+            double cosv = fabs(cd);
+            float pr = orc_branch_proxy((float)cosv, L, c->a_f + (size_t)mat * L);
+            pm_slot_u(i, (uint32_t)b, SLOT_GLASS, r, u);
+            int reflect = u[0] < (double)pr;
+            for (int l = 0; l < L; ++l) {
+                double Rr, Tt;
+                slab_rt(c, r, mat, cosv, l, &Rr, &Tt);
+                Phi[l] *= reflect ? Rr / (double)pr : Tt / (1.0 - (double)pr);
+            }
+            if (reflect) {
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = d[a] - 2.0 * cd * ng[a];
+                    o[a] = x[a] + RAY_OFFSET * ns[a];
+                }
+                excl_prim = tri;
+                excl_obj = -1;
+                changed = 1;
+            } else {
+                for (int a = 0; a < 3; ++a)
+                    o[a] = x[a] - RAY_OFFSET * ns[a];
+                excl_prim = tri;
+                excl_obj = c->obj[tri];
+            }
+        }
+    }
+}
+
+typedef struct {
+    const orc_ctx *c;
+    const orc_render_desc *r;
+    int64_t n;
+    double scale;
+    double *rec, *pw;
+    atomic_llong next;
+} orc_pjob;
+
+static void *photon_worker(void *arg)
+{
+    orc_pjob *jb = (orc_pjob *)arg;
+    const int L = jb->c->L, D = jb->r->max_depth;
+    double *Phi = (double *)malloc(sizeof(double) * (size_t)L);
+    if (!Phi)
+        return NULL;
+    for (;;) {
+        int64_t i0 = atomic_fetch_add(&jb->next, 64);
+        if (i0 >= jb->n)
+            break;
+        int64_t i1 = i0 + 64 < jb->n ? i0 + 64 : jb->n;
+        for (int64_t i = i0; i < i1; ++i)
+            trace_photon(jb->c, jb->r, (uint32_t)i, jb->scale, jb->rec + (size_t)i * 7 * (D - 1),
+                         jb->pw + (size_t)i * (D - 1) * L, Phi);
+    }
+    free(Phi);
+    return NULL;
+}
+
+void orc_photon_map_free(void *p)
+{
+    orc_pmap *pm = (orc_pmap *)p;
+    if (!pm)
+        return;
+    free(pm->pos); free(pm->dir); free(pm->pow); free(pm->cell_start); free(pm->order);
+    free(pm);
+}
+
+static int64_t pm_cell(const orc_pmap *pm, const double *x)
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        int k = (int)floor((x[a] - pm->lo[a]) / pm->radius);
+        c[a] = k < 0 ? 0 : (k >= pm->dims[a] ? pm->dims[a] - 1 : k);
+    }
+    return ((int64_t)c[2] * pm->dims[1] + c[1]) * pm->dims[0] + c[0];
+}
+
+void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int n_threads)
+{
+    const orc_ctx *c = (const orc_ctx *)ctx;
+    if (!c || !r || n_photons < 1 || !(radius > 0.0) || r->max_depth < 2)
+        return NULL;
+    const int L = c->L, D = r->max_depth;
+    size_t slots = (size_t)n_photons * (size_t)(D - 1);
+    double *rec = (double *)malloc(sizeof(double) * 7 * slots);
+    double *pw = (double *)malloc(sizeof(double) * slots * (size_t)L);
+    orc_pmap *pm = (orc_pmap *)calloc(1, sizeof(orc_pmap));
+    if (!rec || !pw || !pm) {
+        free(rec); free(pw); free(pm);
+        return NULL;
+    }
+    orc_pjob jb = {c, r, n_photons, 1.0 / (double)n_photons, rec, pw};
+    atomic_init(&jb.next, 0);
+    if (n_threads <= 0) {
+        long nc = sysconf(_SC_NPROCESSORS_ONLN);
+        n_threads = nc > 0 ? (int)nc : 1;
+    }
+    if (n_threads > 512)
+        n_threads = 512;
+    pthread_t th[512];
+    int started = 0;
+    for (int t = 0; t < n_threads; ++t) {
+        if (pthread_create(&th[t], NULL, photon_worker, &jb) != 0)
+            break;
+        ++started;
+    }
+    if (started == 0)
+        photon_worker(&jb);
+    for (int t = 0; t < started; ++t)
+        pthread_join(th[t], NULL);
+    /* compact the stored photons in slot order */
+    int64_t n = 0;
+    for (size_t s = 0; s < slots; ++s)
+        n += rec[7 * s + 6] != 0.0;
+    pm->L = L;
+    pm->n = n;
+    pm->radius = radius;
+    pm->pos = (double *)malloc(sizeof(double) * 3 * (size_t)(n ? n : 1));
+    pm->dir = (double *)malloc(sizeof(double) * 3 * (size_t)(n ? n : 1));
+    pm->pow = (double *)malloc(sizeof(double) * (size_t)L * (size_t)(n ? n : 1));
+    if (!pm->pos || !pm->dir || !pm->pow) {
+        free(rec); free(pw);
+        orc_photon_map_free(pm);
+        return NULL;
+    }
+    int64_t k = 0;
+    for (size_t s = 0; s < slots; ++s) {
+        if (rec[7 * s + 6] == 0.0)
+            continue;
+        for (int a = 0; a < 3; ++a) {
+            pm->pos[3 * k + a] = rec[7 * s + a];
+            pm->dir[3 * k + a] = rec[7 * s + 3 + a];
+        }
+        memcpy(pm->pow + (size_t)k * L, pw + s * (size_t)L, sizeof(double) * (size_t)L);
+        ++k;
+    }
+    free(rec);
+    free(pw);
+    /* uniform grid of cell size = radius over the photons */
+    double hi[3];
+    for (int a = 0; a < 3; ++a) {
+        pm->lo[a] = INFINITY;
+        hi[a] = -INFINITY;
+    }
+    for (int64_t q = 0; q < n; ++q)
+        for (int a = 0; a < 3; ++a) {
+            pm->lo[a] = fmin(pm->lo[a], pm->pos[3 * q + a]);
+            hi[a] = fmax(hi[a], pm->pos[3 * q + a]);
+        }
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (n == 0) {
+            pm->lo[a] = 0.0;
+            hi[a] = 0.0;
+        }
+        pm->dims[a] = (int)floor((hi[a] - pm->lo[a]) / radius) + 1;
+        cells *= pm->dims[a];
+    }
+    pm->cell_start = (int64_t *)calloc((size_t)cells + 1, sizeof(int64_t));
+    pm->order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!pm->cell_start || !pm->order) {
+        orc_photon_map_free(pm);
+        return NULL;
+    }
+    for (int64_t q = 0; q < n; ++q)
+        pm->cell_start[pm_cell(pm, pm->pos + 3 * q) + 1]++;
+    for (int64_t cidx = 0; cidx < cells; ++cidx)
+        pm->cell_start[cidx + 1] += pm->cell_start[cidx];
+    int64_t *fill = (int64_t *)calloc((size_t)cells, sizeof(int64_t));
+    if (!fill) {
+        orc_photon_map_free(pm);
+        return NULL;
+    }
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t cc = pm_cell(pm, pm->pos + 3 * q);
+        pm->order[pm->cell_start[cc] + fill[cc]++] = q;
+    }
+    free(fill);
+    return pm;
+}
+
+int64_t orc_photon_map_get(const void *p, double *pos, double *dir, double *power)
+{
+    const orc_pmap *pm = (const orc_pmap *)p;
+    if (!pm)
+        return -1;
+    if (pos)
+        memcpy(pos, pm->pos, sizeof(double) * 3 * (size_t)pm->n);
+    if (dir)
+        memcpy(dir, pm->dir, sizeof(double) * 3 * (size_t)pm->n);
+    if (power)
+        memcpy(power, pm->pow, sizeof(double) * (size_t)pm->L * (size_t)pm->n);
+    return pm->n;
+}
+
+/* Radiance estimate at a diffuse point x seen from the side ns: the power of
+ * the photons within the radius that arrived on that side, over pi r^2,
+ * times rho / pi (added to Ls with the path throughput T). */
+static void pm_gather(const orc_pmap *pm, const double *x, const double *ns, const double *rho, const double *T,
+                      double *Ls)
+{
+    if (pm->n == 0)
+        return;
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; ++a) {
+        c0[a] = (int)floor((x[a] - pm->radius - pm->lo[a]) / pm->radius);
+        c1[a] = (int)floor((x[a] + pm->radius - pm->lo[a]) / pm->radius);
+        c0[a] = c0[a] < 0 ? 0 : c0[a];
+        c1[a] = c1[a] >= pm->dims[a] ? pm->dims[a] - 1 : c1[a];
+    }
+    const int L = pm->L;
+    const double r2 = pm->radius * pm->radius, norm = 1.0 / (PI * r2);
+    for (int cz = c0[2]; cz <= c1[2]; ++cz)
+        for (int cy = c0[1]; cy <= c1[1]; ++cy)
+            for (int cx = c0[0]; cx <= c1[0]; ++cx) {
+                int64_t cc = ((int64_t)cz * pm->dims[1] + cy) * pm->dims[0] + cx;
+                for (int64_t s = pm->cell_start[cc]; s < pm->cell_start[cc + 1]; ++s) {
+                    int64_t q = pm->order[s];
+                    const double *xp = pm->pos + 3 * q;
+                    double dx = xp[0] - x[0], dy = xp[1] - x[1], dz = xp[2] - x[2];
+                    if (dx * dx + dy * dy + dz * dz >= r2)
+                        continue;
+                    if (dot3(pm->dir + 3 * q, ns) >= 0.0)
+                        continue;
+                    const double *pw = pm->pow + (size_t)q * L;
+                    for (int l = 0; l < L; ++l)
+                        Ls[l] += T[l] * rho[l] / PI * pw[l] * norm;
+                }
+            }
+}
+
 /* ----------------------------------------------------------- one path --- */
 typedef struct {
     double *T, *Lsum;     /* [L] */
@@ -411,6 +740,10 @@ static void trace_path(const orc_ctx *c, const orc_render_desc *r, int px, int p
                         }
                     }
                 }
+            }
+            if (r->photon_map) {   /* photon mapping: indirect and caustic light from the map, then stop */
+                pm_gather((const orc_pmap *)r->photon_map, x, ns, rho, T, Ls);
+                break;
             }
             if (b == r->max_depth)
                 break;

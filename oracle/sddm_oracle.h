@@ -75,7 +75,23 @@ typedef struct {
     double ortho_height;      /* > 0: orthographic camera of this height */
     const float *s_override;  /* [n_mat] or NULL; a negative entry keeps the default */
     int brute_force;          /* 1: test every triangle and compute decision margins */
+    const void *photon_map;   /* NULL, or a photon map (orc_photon_map_build): at the first diffuse
+                                 vertex the path adds next-event light and the photons' radiance
+                                 estimate, then stops */
 } orc_render_desc;
+
+/* Photon map (Sec. 4, global illumination by photon mapping). Photons leave
+ * the lights (triangle by area, uniform point, cosine direction from the front
+ * face, power pi Le A / N each), follow the same interactions as paths (diffuse
+ * bounce, conductor mirror, glass branch) for at most max_depth - 1 hits, and
+ * are stored at every diffuse hit once their direction has been changed by a
+ * diffuse bounce or a reflection (light reaching a surface straight, through
+ * glass or not, is next-event light). Random numbers: Philox counter (photon,
+ * 0xffffffff, hit, slot), key (seed, render id). */
+void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int n_threads);
+void orc_photon_map_free(void *pm);
+/* Stored photons: count, and optionally positions [n][3], directions [n][3], power [n][L]. */
+int64_t orc_photon_map_get(const void *pm, double *pos, double *dir, double *power);
 
 int  orc_create(void **out, const orc_scene_desc *d);
 void orc_destroy(void *ctx);
