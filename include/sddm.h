@@ -227,6 +227,41 @@ int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats
  * streams or threads) race on it. Output: d->xyz_out, DEVICE, as sddm_render. */
 int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st);
 
+/* Photon pass of a photon-mapping render (filled by sddm_render_photon_map). */
+typedef struct {
+    int64_t photons;          /* photons emitted */
+    int64_t photon_segments;  /* closest-hit queries of the photon pass */
+    int64_t stored;           /* photons stored in the map */
+    int64_t grid_cells;       /* cells of the uniform grid the map is sorted into */
+    double photon_ms;         /* device time of the photon pass and grid build */
+    int64_t kernel_launches;  /* kernels of the photon pass and grid build */
+} sddm_photon_stats;
+
+/* Render one image by photon mapping (Sec. 4: global illumination computed
+ * with photons emitted from the light sources). First n_photons photons leave
+ * the area lights -- triangle chosen by area, uniform point, cosine-distributed
+ * direction about the front face, power pi Le A_total / n_photons each --
+ * and follow the interactions camera paths follow (diffuse bounce weighted by
+ * rho, Fresnel mirror for conductors, the glass branch with the same branch
+ * probability and R/P, T/(1-P) weights, absorbing glass at its state in
+ * d->glass_s) for at most max_depth - 1 hits over the global BVH. A photon is
+ * stored at each diffuse hit reached after a diffuse bounce or a reflection
+ * changed its direction (light arriving in a straight line, through glass or
+ * not, is next-event light). Random numbers: Philox counter (photon,
+ * 0xffffffff, hit, slot), key (seed, render_id), slots as for paths. Then the
+ * camera pass of sddm_render with the megakernel: emission and the shadow ray
+ * at the first diffuse vertex as usual, plus rho/pi times the power of the
+ * stored photons within `radius` whose direction points into the visible
+ * side, over pi radius^2; the path stops there. d->method must be
+ * SDDM_METHOD_MEGAKERNEL, d->bsdf_mode SDDM_BSDF_EXACT, d->nee 1, d->max_depth
+ * >= 2, radius > 0, n_photons * (max_depth - 1) < 2^31 (else
+ * SDDM_ERR_INVALID_ARG). The map lives in library-owned device memory: 16
+ * bytes x 2 + 4 L bytes per photon and bounce, reused by later calls; too
+ * little device memory gives SDDM_ERR_OOM. Synchronous; outputs as
+ * sddm_render (d->xyz_out DEVICE). st and pst may be NULL. */
+int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_photons, float radius,
+                           sddm_stats *st, sddm_photon_stats *pst);
+
 /* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}), the
  * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per
  * chunk ({2^21, 2^22, 2^23}; the ray queues are sized from it, two rays per

@@ -482,18 +482,19 @@ static int64_t pm_cell(const orc_pmap *pm, const double *x)
 void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int n_threads)
 {
     const orc_ctx *c = (const orc_ctx *)ctx;
-    if (!c || !r || n_photons < 1 || !(radius > 0.0) || r->max_depth < 2)
+    if (!c || !r || n_photons < 0 || !(radius > 0.0) || r->max_depth < 2)
         return NULL;
     const int L = c->L, D = r->max_depth;
     size_t slots = (size_t)n_photons * (size_t)(D - 1);
-    double *rec = (double *)malloc(sizeof(double) * 7 * slots);
-    double *pw = (double *)malloc(sizeof(double) * slots * (size_t)L);
+    /* no photons: an empty map */
+    double *rec = (double *)malloc(sizeof(double) * 7 * (slots ? slots : 1));
+    double *pw = (double *)malloc(sizeof(double) * (slots ? slots : 1) * (size_t)L);
     orc_pmap *pm = (orc_pmap *)calloc(1, sizeof(orc_pmap));
     if (!rec || !pw || !pm) {
         free(rec); free(pw); free(pm);
         return NULL;
     }
-    orc_pjob jb = {c, r, n_photons, 1.0 / (double)n_photons, rec, pw};
+    orc_pjob jb = {c, r, n_photons, n_photons ? 1.0 / (double)n_photons : 0.0, rec, pw};
     atomic_init(&jb.next, 0);
     if (n_threads <= 0) {
         long nc = sysconf(_SC_NPROCESSORS_ONLN);

@@ -10,9 +10,14 @@
 // the reflection/refraction laws (cosine-distributed diffuse, Fresnel-weighted
 // mirror for metals, R- or T-weighted mirror/straight branch for glass).
 // Spectral values over the L bins are turned into XYZ with a compensated sum.
+// With a photon map (PM) the path ends at its first diffuse vertex, after the
+// emission and the next-event light there, with the photons' radiance estimate
+// (Sec. 4's photon mapping for global illumination): rho / pi times the power
+// of the photons within radius r that arrived on the visible side, over pi r^2.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "photon.cuh"
 
 namespace sddm {
 
@@ -53,7 +58,7 @@ __device__ __forceinline__ void add_xyz(const DevScene &sc, int L, Kahan3 &acc, 
     acc.add(X.s, Y.s, Z.s);
 }
 
-template <int LT, bool COUNT, bool FILMS>
+template <int LT, bool COUNT, bool FILMS, bool PM>
 __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.path_count) return;
@@ -154,6 +159,17 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
                     }
                 }
             }
+            if constexpr (PM) {
+                Spectrum<LT> S;
+                for_bins<LT>(L, [&](int i) { S.v[i] = 0.0f; });
+                pm_gather_visit(a.pm, xh, ns, [&](int slot) {
+                    const float *pw = a.pm.pow + (size_t)slot * L;
+                    for_bins<LT>(L, [&](int i) { S.v[i] += __ldg(pw + i); });
+                });
+                const float norm = 1.0f / (3.14159265358979f * 3.14159265358979f * a.pm.radius * a.pm.radius);
+                add_xyz<LT>(sc, L, acc, [&](int i) { return T.v[i] * __ldg(rho + i) * S.v[i] * norm; });
+                break;
+            }
             if (b == ri.max_depth) break;
             uint4 xb = philox4x32_10(make_uint4(p, j, (uint32_t)b, kSlotBsdf), k0, k1);
             d = cosine_dir(ns, u01(xb.x), u01(xb.y));
@@ -225,12 +241,12 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
     }
 }
 
-template <bool COUNT, bool FILMS>
+template <bool COUNT, bool FILMS, bool PM = false>
 static void launch_mk(const MegaArgs &a, unsigned nb, int threads, cudaStream_t stream) {
     switch (a.sc.L) {
-        case 8: k_megakernel<8, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
-        case 16: k_megakernel<16, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
-        default: k_megakernel<0, COUNT, FILMS><<<nb, threads, 0, stream>>>(a); break;
+        case 8: k_megakernel<8, COUNT, FILMS, PM><<<nb, threads, 0, stream>>>(a); break;
+        case 16: k_megakernel<16, COUNT, FILMS, PM><<<nb, threads, 0, stream>>>(a); break;
+        default: k_megakernel<0, COUNT, FILMS, PM><<<nb, threads, 0, stream>>>(a); break;
     }
 }
 
@@ -240,7 +256,9 @@ cudaError_t launch_megakernel(const MegaArgs &a, cudaStream_t stream) {
     const int64_t blocks = (a.path_count + threads - 1) / threads;
     const unsigned nb = (unsigned)blocks;
     const bool films = a.sc.mat_nfilm != nullptr;
-    if (a.count_traversal)
+    if (a.pm.on)
+        films ? launch_mk<false, true, true>(a, nb, threads, stream) : launch_mk<false, false, true>(a, nb, threads, stream);
+    else if (a.count_traversal)
         films ? launch_mk<true, true>(a, nb, threads, stream) : launch_mk<true, false>(a, nb, threads, stream);
     else
         films ? launch_mk<false, true>(a, nb, threads, stream) : launch_mk<false, false>(a, nb, threads, stream);

@@ -19,6 +19,7 @@
 #include "sddm_internal.h"
 #include "sddm_ddm.h"
 #include "sddm_mlp.h"
+#include "sddm_photon.h"
 
 namespace sddm {
 
@@ -135,6 +136,10 @@ struct sddm_ctx {
     // per-render scratch
     DevBuf d_info, d_state, d_out_tab, d_aov_xyz_tab, d_aov_prim_tab, d_samples, d_first, d_counters, d_err;
     DDMBuffers ddm_buf;
+    // photon map (sddm_render_photon_map): slots, grid, and the view the
+    // megakernel reads while pm_view.on
+    DevBuf pm_state, pm_scratch, pm_pos, pm_dir, pm_pow, pm_cnt, pm_start, pm_fill, pm_order, pm_sums, pm_cntr;
+    PhotonGridView pm_view{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int profile = 0;
     // learned glass surrogates: one network may serve several materials
@@ -823,6 +828,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
                 a.counters = ctx->d_counters.as<unsigned long long>();
                 a.error_flag = ctx->d_err.as<int>();
                 a.count_traversal = count_trav;
+                a.pm = ctx->pm_view;
                 cudaEvent_t t0 = nullptr, t1 = nullptr;
                 if (time_trace) {
                     if ((e = ctx->ddm_buf.event_pair(t0, t1)) || (e = cudaEventRecord(t0, s)))
@@ -876,7 +882,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         }
         return SDDM_OK;
     };
-    const bool graphable = ctx->graphs_enabled && !count_trav && !time_trace;
+    const bool graphable = ctx->graphs_enabled && !count_trav && !time_trace && !ctx->pm_view.on;
     std::string key;
     if (graphable) {
         char buf[256];
@@ -960,6 +966,106 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         }
         st->trace_ms = tms;
         st->trace_launches = ctx->ddm_buf.events_used / 2;
+    }
+    return SDDM_OK;
+}
+
+int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_photons, float radius,
+                           sddm_stats *st, sddm_photon_stats *pst) {
+    int rc = validate_desc(ctx, d, 1);
+    if (rc != SDDM_OK) return rc;
+    if (d->method != SDDM_METHOD_MEGAKERNEL || d->bsdf_mode != SDDM_BSDF_EXACT)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: needs the megakernel method and the exact glass model");
+    if (!d->nee || d->max_depth < 2)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: needs nee = 1 and max_depth >= 2");
+    if (!(radius > 0.0f) || !std::isfinite(radius))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: radius must be positive and finite");
+    const int64_t per = d->max_depth - 1;
+    if (n_photons < 0 || n_photons > ((int64_t)1 << 31) / per - 1)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: n_photons * (max_depth - 1) must stay below 2^31");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_render_photon_map: cudaSetDevice");
+    const int M = (int)ctx->mats.size(), L = ctx->L;
+    const int64_t slots = n_photons * per;
+    std::vector<float> state(M);
+    for (int m = 0; m < M; ++m) state[m] = material_state(ctx, *d, m);
+    // grid over the scene box, cells of side >= radius, at most ~2^24 cells
+    const DDMScene &g = ctx->ddm;
+    PhotonGridView v{};
+    double ext[3], vol = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        ext[a] = std::max<double>(g.hi[a] - g.lo[a], 1e-6);
+        vol *= ext[a];
+    }
+    const double cell = std::max<double>(radius, std::cbrt(vol / (double)(1 << 24)) * 1.01);
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        v.lo[a] = g.lo[a];
+        v.dims[a] = (int)std::floor(ext[a] / cell) + 1;
+        cells *= v.dims[a];
+    }
+    v.cell = (float)cell;
+    v.radius = radius;
+    const size_t sl = (size_t)std::max<int64_t>(slots, 1);
+    cudaStream_t s = ctx->stream;
+    if ((e = ctx->pm_state.upload(state, s)) ||
+        (e = ctx->pm_scratch.ensure(sizeof(float) * (size_t)std::max<int64_t>(n_photons, 1) * L)) ||
+        (e = ctx->pm_pos.ensure(sizeof(float4) * sl)) || (e = ctx->pm_dir.ensure(sizeof(float4) * sl)) ||
+        (e = ctx->pm_pow.ensure(sizeof(float) * sl * L)) || (e = ctx->pm_cnt.ensure(sizeof(int) * (size_t)cells)) ||
+        (e = ctx->pm_start.ensure(sizeof(int) * (size_t)(cells + 1))) ||
+        (e = ctx->pm_fill.ensure(sizeof(int) * (size_t)cells)) || (e = ctx->pm_order.ensure(sizeof(int) * sl)) ||
+        (e = ctx->pm_sums.ensure(sizeof(int) * (size_t)(cells / 1024 + 1))) ||
+        (e = ctx->pm_cntr.ensure(2 * sizeof(unsigned long long))))
+        return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render_photon_map: device allocation failed")
+                                              : cuda_fail(e, "sddm_render_photon_map: scratch");
+    if ((e = cudaEventRecord(ctx->ev0, s)) || (e = cudaMemsetAsync(ctx->pm_pos.p, 0, sizeof(float4) * sl, s)) ||
+        (e = cudaMemsetAsync(ctx->pm_cntr.p, 0, 2 * sizeof(unsigned long long), s)))
+        return cuda_fail(e, "sddm_render_photon_map: memset");
+    unsigned long long *cntr = ctx->pm_cntr.as<unsigned long long>();
+    int64_t launches = 0;
+    if (n_photons > 0) {
+        PhotonTraceArgs ta;
+        ta.n_photons = n_photons;
+        ta.max_depth = d->max_depth;
+        ta.seed = d->seed;
+        ta.render_id = d->render_id;
+        ta.state_s = ctx->pm_state.as<float>();
+        ta.scratch = ctx->pm_scratch.as<float>();
+        ta.pos = ctx->pm_pos.as<float4>();
+        ta.dir = ctx->pm_dir.as<float4>();
+        ta.pow = ctx->pm_pow.as<float>();
+        ta.segments = cntr;
+        if ((e = launch_photon_trace(ctx->dev, ta, s)) != cudaSuccess)
+            return cuda_fail(e, "sddm_render_photon_map: photon launch");
+        launches += 1;
+    }
+    v.pos = ctx->pm_pos.as<float4>();
+    v.dir = ctx->pm_dir.as<float4>();
+    v.pow = ctx->pm_pow.as<float>();
+    v.cell_start = ctx->pm_start.as<int>();
+    v.order = ctx->pm_order.as<int>();
+    if ((e = build_photon_grid(v, slots, ctx->pm_cnt.as<int>(), ctx->pm_start.as<int>(), ctx->pm_fill.as<int>(),
+                               ctx->pm_order.as<int>(), ctx->pm_sums.as<int>(), cntr + 1, s)) != cudaSuccess)
+        return cuda_fail(e, "sddm_render_photon_map: grid build");
+    launches += slots > 0 ? 5 : 3;
+    unsigned long long hc[2];
+    if ((e = cudaEventRecord(ctx->ev1, s)) ||
+        (e = cudaMemcpyAsync(hc, cntr, sizeof(hc), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+        return cuda_fail(e, "sddm_render_photon_map: photon pass");
+    float pms = 0.f;
+    cudaEventElapsedTime(&pms, ctx->ev0, ctx->ev1);
+    v.on = 1;
+    ctx->pm_view = v;
+    rc = sddm_render(ctx, d, 1, st);
+    ctx->pm_view = PhotonGridView{};
+    if (rc != SDDM_OK) return rc;
+    if (pst) {
+        pst->photons = n_photons;
+        pst->photon_segments = (int64_t)hc[0];
+        pst->stored = (int64_t)hc[1];
+        pst->grid_cells = cells;
+        pst->photon_ms = pms;
+        pst->kernel_launches = launches;
     }
     return SDDM_OK;
 }

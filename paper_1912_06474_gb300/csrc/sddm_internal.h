@@ -138,6 +138,20 @@ float material_state(const sddm_ctx *ctx, const sddm_render_desc &x, int m);
 
 // Kernel launchers (defined in .cu files), all asynchronous on `stream`.
 namespace sddm {
+// Stored photons of a photon map (Sec. 4 global illumination) sorted into a
+// uniform grid of cubic cells of side `cell` >= radius starting at lo.
+struct PhotonGridView {
+    int on;                   // 0: no photon map in this render
+    const float4 *pos;        // [slots] (x, 1 = stored / 0 = empty slot)
+    const float4 *dir;        // [slots] incoming direction
+    const float *pow;         // [slots][L] power
+    const int *cell_start;    // [cells + 1]
+    const int *order;         // stored slots sorted by cell
+    float lo[3];
+    int dims[3];
+    float cell, radius;
+};
+
 struct MegaArgs {
     DevScene sc;
     RenderBatch rb;
@@ -147,6 +161,7 @@ struct MegaArgs {
     unsigned long long *counters;      // [8]: ext, shadow, glass, crossings, fallbacks, nodes, tris, visits
     int *error_flag;
     int count_traversal;
+    PhotonGridView pm = {};            // photon map gathered at the first diffuse vertex (pm.on)
 };
 cudaError_t launch_megakernel(const MegaArgs &a, cudaStream_t stream);
 

@@ -1,0 +1,27 @@
+// Photon map construction (photon.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sddm_internal.h"
+
+namespace sddm {
+
+struct PhotonTraceArgs {
+    int64_t n_photons;
+    int max_depth;              // photons take at most max_depth - 1 hits
+    uint32_t seed, render_id;
+    const float *state_s;       // [n_mat] coloration state of this render
+    float *scratch;             // [n_photons][L] power in flight
+    float4 *pos, *dir;          // [n_photons * (max_depth - 1)]
+    float *pow;                 // [n_photons * (max_depth - 1)][L]
+    unsigned long long *segments;
+};
+cudaError_t launch_photon_trace(const DevScene &sc, const PhotonTraceArgs &a, cudaStream_t stream);
+// Sort the stored slots into the grid g (dims, lo, cell set by the caller);
+// fills g.cell_start / g.order from the given buffers ([cells + 1], [slots]).
+cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int *cnt, int *start, int *fill, int *order,
+                              int *scan_sums, unsigned long long *stored, cudaStream_t stream);
+
+}  // namespace sddm

@@ -27,7 +27,7 @@ BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP, "mlp_raw": BSDF_MLP_RAW}
 
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
             "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_coated_glass",
-            "sddm_rgb_to_spectrum",
+            "sddm_rgb_to_spectrum", "sddm_render_photon_map",
             "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
             "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
@@ -83,6 +83,14 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PhotonStats(C.Structure):
+    _fields_ = [("photons", C.c_int64), ("photon_segments", C.c_int64), ("stored", C.c_int64),
+                ("grid_cells", C.c_int64), ("photon_ms", C.c_double), ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -111,6 +119,8 @@ def _load():
         "sddm_philox": ([P, I, P, C.c_uint32, C.c_uint32, P], I),
         "sddm_set_profiling": ([P, I], I),
         "sddm_render_noalloc": ([P, C.POINTER(RenderDesc), C.POINTER(Stats)], I),
+        "sddm_render_photon_map": ([P, C.POINTER(RenderDesc), C.c_int64, C.c_float, C.POINTER(Stats),
+                                    C.POINTER(PhotonStats)], I),
         "sddm_mlp_train": ([P, C.c_uint32, C.POINTER(MlpTrainOpts), C.POINTER(MlpReport)], I),
         "sddm_mlp_get_weights": ([P, C.c_uint32, P], I),
         "sddm_mlp_set_weights": ([P, C.c_uint32, P, C.c_float, C.c_float], I),
@@ -286,6 +296,19 @@ class Context:
         _check(lib.sddm_render_noalloc(self._h, arr, C.byref(st)))
         self.last_stats = st.as_dict()
         return self.last_stats
+
+    def render_photon_map(self, spec, n_photons, radius):
+        """sddm_render_photon_map: photon pass of n_photons from the lights, then
+        the megakernel camera pass gathering the map within ``radius`` at the
+        first diffuse vertex. Returns (image [H,W,3] CUDA float32, stats,
+        photon stats)."""
+        import torch
+        img = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=torch.device("cuda", self.device))
+        arr, _keep = self._descs([spec], "megakernel", "exact", [img.data_ptr()], None, None)
+        st, pst = Stats(), PhotonStats()
+        _check(lib.sddm_render_photon_map(self._h, arr, int(n_photons), float(radius), C.byref(st), C.byref(pst)))
+        self.last_stats = st.as_dict()
+        return img, self.last_stats, pst.as_dict()
 
     def render_host(self, specs, outs: Sequence[np.ndarray], method="ddm", bsdf="exact"):
         """sddm_render_host: outputs are host (pinned or pageable) float32 arrays [H,W,3]."""

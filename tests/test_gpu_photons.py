@@ -1,0 +1,116 @@
+"""GPU photon mapping (Sec. 4, global illumination by photon mapping) through
+the C ABI (sddm_render_photon_map) against the FP64 oracle's photon map.
+
+Both sides draw the same Philox numbers for every photon and camera path, so
+they trace the same photons; they differ only where FP32 and FP64 take a
+different discrete decision (a grazing hit, a photon on the gather radius).
+Acceptance: image relative RMSE at most 1e-3 against the oracle rendering
+with its own photon map, stored photon counts within 1e-3 of the photons
+emitted, and the furnace's closed form away from the box's edges.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1912_06474_gb300 import scenes
+from tests.helpers import rel_rmse
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+
+@pytest.fixture(scope="module")
+def sddm():
+    from paper_1912_06474_gb300 import sddm as m
+    return m
+
+
+def _both(oracle_mod, sddm, sc, spec, n, r):
+    t0 = time.perf_counter()
+    orc = oracle_mod.Oracle(sc)
+    pm = orc.photon_map(spec, n, r)
+    ref = orc.render_pixels(spec, photon_map=pm)["xyz"].reshape(spec.height, spec.width, 3)
+    t_orc = time.perf_counter() - t0
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        ctx.build()
+        img, st, pst = ctx.render_photon_map(spec, n, r)
+        torch.cuda.synchronize()
+        img = img.cpu().numpy()
+    finally:
+        ctx.close()
+    print(f"\n  photons {n}: oracle {t_orc:.2f} s, GPU photon pass {pst['photon_ms']:.3f} ms "
+          f"({pst['photon_segments']} segments, {pst['stored']} stored, {pst['grid_cells']} cells), "
+          f"camera pass {st['gpu_ms']:.3f} ms")
+    return img, ref, pst, len(pm.photons()[0])
+
+
+@pytest.mark.parametrize("s", [0.0, 0.8])
+def test_tiny_room_photon_map(oracle_mod, sddm, s):
+    sc = scenes.tiny_room(L=16)
+    glass = {m: s for m in sc.glass_materials()}
+    spec = scenes.RenderSpec(64, 48, 4, 5, seed=3, camera=sc.camera, glass_s=glass, nee=True)
+    n = 100000
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.15)
+    assert abs(pst["stored"] - n_ref) <= 1e-3 * n, (pst["stored"], n_ref)
+    assert pst["photons"] == n
+    err = rel_rmse(img, ref)
+    print(f"  image rel-RMSE vs oracle {err:.2e}")
+    assert err <= 1e-3
+
+
+def test_furnace_photon_map(oracle_mod, sddm):
+    D, rho0, Le0 = 5, 0.6, 0.7
+    sc = scenes.furnace_box(L=8, rho0=rho0, Le0=Le0)
+    spec = scenes.RenderSpec(32, 32, 2, D, seed=1, camera=sc.camera, nee=True)
+    n = 200000
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.1)
+    # every photon is stored once per hit from its second hit on, none escapes
+    # (in FP64; an FP32 ray may slip through a box corner now and then)
+    assert n_ref == n * (D - 2)
+    assert n * (D - 2) - 1e-4 * n <= pst["stored"] <= n * (D - 2)
+    assert rel_rmse(img, ref) <= 1e-3
+    r0, L0 = float(np.float32(rho0)), float(np.float32(Le0))
+    want = L0 * sum(r0 ** j for j in range(D)) * (sc.quad_w.astype(np.float64)[:, None]
+                                                 * sc.cmf.astype(np.float64)).sum(0)
+    centre = img[8:24, 8:24].mean((0, 1))
+    assert np.all(np.abs(centre / want - 1) < 0.01), centre / want
+
+
+def test_depth_two_and_no_photons(oracle_mod, sddm):
+    """D = 2: photons reach surfaces only straight from the lights, so nothing
+    is stored; no photons at all: the map is empty. Either way the image is
+    emission plus next-event light at the first diffuse vertex."""
+    sc = scenes.tiny_room(L=16)
+    spec2 = scenes.RenderSpec(40, 30, 2, 2, seed=5, camera=sc.camera, nee=True)
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec2, 20000, 0.2)
+    assert pst["stored"] == 0 and n_ref == 0
+    assert rel_rmse(img, ref) <= 1e-3
+    spec5 = scenes.RenderSpec(40, 30, 2, 5, seed=5, camera=sc.camera, nee=True)
+    img0, ref0, pst0, _ = _both(oracle_mod, sddm, sc, spec5, 0, 0.2)
+    assert pst0["stored"] == 0 and pst0["photon_segments"] == 0
+    assert rel_rmse(img0, ref0) <= 1e-3
+
+
+def test_photon_map_argument_checks(sddm):
+    sc = scenes.tiny_room(L=16)
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        ctx.build()
+        for spec, n, r in [(scenes.RenderSpec(8, 8, 1, 1, camera=sc.camera), 100, 0.1),
+                           (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera, nee=False), 100, 0.1),
+                           (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 100, 0.0),
+                           (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 100, float("nan")),
+                           (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), -1, 0.1),
+                           (scenes.RenderSpec(8, 8, 1, 64, camera=sc.camera), 1 << 26, 0.1)]:
+            with pytest.raises(sddm.SddmError):
+                ctx.render_photon_map(spec, n, r)
+        # the context still renders afterwards
+        img, st, pst = ctx.render_photon_map(scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 1000, 0.1)
+        assert pst["photons"] == 1000 and np.isfinite(img.cpu().numpy()).all()
+    finally:
+        ctx.close()

@@ -52,3 +52,18 @@ def test_furnace_radiance_away_from_edges(oracle_mod):
                                                      * sc.cmf.astype(np.float64)).sum(0)
     centre = img[8:24, 8:24].mean((0, 1))
     assert np.all(np.abs(centre / want - 1) < 0.01), centre / want
+
+
+def test_empty_map_leaves_emission_and_direct_light(oracle_mod):
+    """No photons: the path still stops at its first diffuse vertex, so the
+    furnace shows emission plus one bounce of next-event light, Le0 (1 + rho0)
+    (the closed box irradiates every point with pi Le0)."""
+    sc, _, rho0, Le0 = _furnace(5)
+    spec = scenes.RenderSpec(32, 32, 16, 5, seed=2, camera=sc.camera, nee=True)
+    orc = oracle_mod.Oracle(sc)
+    pm = orc.photon_map(spec, 0, 0.1)
+    assert len(pm.photons()[0]) == 0
+    img = orc.render_pixels(spec, photon_map=pm)["xyz"].reshape(32, 32, 3)
+    want = Le0 * (1 + rho0) * (sc.quad_w.astype(np.float64)[:, None] * sc.cmf.astype(np.float64)).sum(0)
+    mean = img.mean((0, 1))
+    assert np.all(np.abs(mean / want - 1) < 0.01), mean / want
