@@ -238,7 +238,11 @@ typedef struct {
 } sddm_photon_stats;
 
 /* Render one image by photon mapping (Sec. 4: global illumination computed
- * with photons emitted from the light sources). First n_photons photons leave
+ * with photons emitted from the light sources), by d->method: with
+ * SDDM_METHOD_DDM the photons travel through the same subdomain ray queues and
+ * trace kernel as camera paths (Sec. 5), in chunks of paths_in_flight photons;
+ * with SDDM_METHOD_MEGAKERNEL one thread traces each photon over the global
+ * BVH. First n_photons photons leave
  * the area lights -- triangle chosen by area, uniform point, cosine-distributed
  * direction about the front face, power pi Le A_total / n_photons each --
  * and follow the interactions camera paths follow (diffuse bounce weighted by
@@ -252,10 +256,10 @@ typedef struct {
  * camera pass of sddm_render with the megakernel: emission and the shadow ray
  * at the first diffuse vertex as usual, plus rho/pi times the power of the
  * stored photons within `radius` whose direction points into the visible
- * side, over pi radius^2; the path stops there. d->method must be
- * SDDM_METHOD_MEGAKERNEL, d->bsdf_mode SDDM_BSDF_EXACT, d->nee 1, d->max_depth
- * >= 2, radius > 0, n_photons * (max_depth - 1) < 2^31 (else
- * SDDM_ERR_INVALID_ARG). The map lives in library-owned device memory: 16
+ * side, over pi radius^2; the path stops there. The photon pass evaluates
+ * glass exactly; the camera pass follows d->bsdf_mode (the learned model runs
+ * with the DDM method only). Needs d->nee 1, d->max_depth >= 2, radius > 0,
+ * n_photons * (max_depth - 1) < 2^31 (else SDDM_ERR_INVALID_ARG). The map lives in library-owned device memory: 16
  * bytes x 2 + 4 L bytes per photon and bounce, reused by later calls; too
  * little device memory gives SDDM_ERR_OOM. Synchronous; outputs as
  * sddm_render (d->xyz_out DEVICE). st and pst may be NULL. */

@@ -28,6 +28,8 @@
 #include "device_common.cuh"
 #include "sddm_ddm.h"
 #include "sddm_mlp.h"
+#include "sddm_ddm_photon.h"
+#include "photon.cuh"
 
 namespace sddm {
 
@@ -71,6 +73,7 @@ struct KArgs {
     int *cross_query;     // [kMaxCross][np]
     const float2 *glass_res;
     int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
+    PhotonGridView pm;    // photon map: gather at the first diffuse vertex, no continuation there
 };
 
 // Queue bin of a ray: its cell, its kind (extension / shadow) and, as far as
@@ -718,7 +721,7 @@ __global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
                     ps.pend_mat[q] = mat;
                     nfl |= kFlPend;
                     nfl &= ~kFlPrevSpec;
-                    if (b < ri.max_depth) {
+                    if (b < ri.max_depth && !a.pm.on) {
                         uint4 xb = philox4x32_10(make_uint4(p, j, (uint32_t)b, kSlotBsdf), k0, k1);
                         const V3 dn = cosine_dir(ns, u01(xb.x), u01(xb.y));
                         const V3 on = x + kRayOffset * ns;
@@ -789,6 +792,8 @@ __global__ void k_finalize(KArgs a) {
     a.sample_xyz[3 * q + 2] = a.ps.acc[2 * np + q];
 }
 
+#include "ddm_photon.cuh"
+
 __global__ void k_image_probe() {}
 
 cudaError_t check_kernel_image() {
@@ -799,7 +804,17 @@ cudaError_t check_kernel_image() {
 // ------------------------------------------------------------- host side
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers &buf, cudaStream_t s);
+
 int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
+    return trace_chunk(run, PhotonGridView{}, buf, s);
+}
+
+int ddm_trace_chunk_pm(const DDMRun &run, const PhotonGridView &pm, DDMBuffers &buf, cudaStream_t s) {
+    return trace_chunk(run, pm, buf, s);
+}
+
+static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers &buf, cudaStream_t s) {
     const int64_t np = run.path_count;
     const int L = run.sc.L;
     const int nc = run.g.n_cells, nb = run.g.n_bins;
@@ -885,6 +900,7 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     a.cross_query = (int *)(m + oCq);
     a.glass_res = (const float2 *)(m + oRes);
     a.block_cnt = (int *)(m + oBc);
+    a.pm = pmv;
     MlpRows mr{};
     if (use_queries) {
         mr.params = run.mlp_params;
@@ -954,6 +970,11 @@ int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
         else
             k_shade_spectral<false><<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
+        if (a.pm.on) {
+            k_ddm_gather<<<path_blocks, 256, 0, s>>>(a);
+            DDM_CHECK(cudaGetLastError());
+            *run.launches += 1;
+        }
         k_shade_continue<<<path_blocks, 256, bins_smem, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         *run.launches += 2;

@@ -20,6 +20,7 @@
 #include "sddm_ddm.h"
 #include "sddm_mlp.h"
 #include "sddm_photon.h"
+#include "sddm_ddm_photon.h"
 
 namespace sddm {
 
@@ -140,6 +141,7 @@ struct sddm_ctx {
     // megakernel reads while pm_view.on
     DevBuf pm_state, pm_scratch, pm_pos, pm_dir, pm_pow, pm_cnt, pm_start, pm_fill, pm_order, pm_sums, pm_cntr;
     PhotonGridView pm_view{};
+    DDMBuffers pm_ddm_buf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int profile = 0;
     // learned glass surrogates: one network may serve several materials
@@ -861,7 +863,8 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
                 run.mlp_dmin = mlp_dmin;
                 run.mlp_dmax = mlp_dmax;
                 run.probe_key = d[0].seed ^ 0x9e3779b9u;
-                int rc2 = ddm_trace_chunk(run, ctx->ddm_buf, s);
+                int rc2 = ctx->pm_view.on ? ddm_trace_chunk_pm(run, ctx->pm_view, ctx->ddm_buf, s)
+                                          : ddm_trace_chunk(run, ctx->ddm_buf, s);
                 if (rc2 != SDDM_OK) return rc2;
             }
             ReduceArgs ra;
@@ -974,8 +977,8 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
                            sddm_stats *st, sddm_photon_stats *pst) {
     int rc = validate_desc(ctx, d, 1);
     if (rc != SDDM_OK) return rc;
-    if (d->method != SDDM_METHOD_MEGAKERNEL || d->bsdf_mode != SDDM_BSDF_EXACT)
-        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: needs the megakernel method and the exact glass model");
+    if (d->method == SDDM_METHOD_MEGAKERNEL && d->bsdf_mode != SDDM_BSDF_EXACT)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: the megakernel method needs the exact glass model");
     if (!d->nee || d->max_depth < 2)
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: needs nee = 1 and max_depth >= 2");
     if (!(radius > 0.0f) || !std::isfinite(radius))
@@ -1015,15 +1018,40 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
         (e = ctx->pm_start.ensure(sizeof(int) * (size_t)(cells + 1))) ||
         (e = ctx->pm_fill.ensure(sizeof(int) * (size_t)cells)) || (e = ctx->pm_order.ensure(sizeof(int) * sl)) ||
         (e = ctx->pm_sums.ensure(sizeof(int) * (size_t)(cells / 1024 + 1))) ||
-        (e = ctx->pm_cntr.ensure(2 * sizeof(unsigned long long))))
+        (e = ctx->pm_cntr.ensure(16 * sizeof(unsigned long long))))
         return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render_photon_map: device allocation failed")
                                               : cuda_fail(e, "sddm_render_photon_map: scratch");
     if ((e = cudaEventRecord(ctx->ev0, s)) || (e = cudaMemsetAsync(ctx->pm_pos.p, 0, sizeof(float4) * sl, s)) ||
-        (e = cudaMemsetAsync(ctx->pm_cntr.p, 0, 2 * sizeof(unsigned long long), s)))
+        (e = cudaMemsetAsync(ctx->pm_cntr.p, 0, 16 * sizeof(unsigned long long), s)))
         return cuda_fail(e, "sddm_render_photon_map: memset");
     unsigned long long *cntr = ctx->pm_cntr.as<unsigned long long>();
     int64_t launches = 0;
-    if (n_photons > 0) {
+    if (n_photons > 0 && d->method == SDDM_METHOD_DDM) {
+        // through the subdomain queues, in chunks of at most paths_in_flight photons
+        const int64_t chunk = ctx->opts.paths_in_flight > 0 ? ctx->opts.paths_in_flight : (int64_t)1 << 22;
+        for (int64_t b0 = 0; b0 < n_photons; b0 += chunk) {
+            DDMPhotonRun pr;
+            pr.sc = ctx->dev;
+            pr.g = ctx->ddm;
+            pr.begin = b0;
+            pr.count = std::min(chunk, n_photons - b0);
+            pr.n_total = n_photons;
+            pr.max_depth = d->max_depth;
+            pr.seed = d->seed;
+            pr.render_id = d->render_id;
+            pr.state_s = ctx->pm_state.as<float>();
+            pr.pos = ctx->pm_pos.as<float4>();
+            pr.dir = ctx->pm_dir.as<float4>();
+            pr.pow = ctx->pm_pow.as<float>();
+            pr.counters = ctx->pm_cntr.as<unsigned long long>() + 2;
+            pr.error_flag = ctx->pm_cntr.as<int>() + 20;
+            pr.sm_count = ctx->sm_count;
+            pr.blocks_per_sm = ctx->opts.blocks_per_sm;
+            pr.launches = &launches;
+            const int rc2 = ddm_photon_pass(pr, ctx->pm_ddm_buf, s);
+            if (rc2 != SDDM_OK) return rc2;
+        }
+    } else if (n_photons > 0) {
         PhotonTraceArgs ta;
         ta.n_photons = n_photons;
         ta.max_depth = d->max_depth;
@@ -1048,10 +1076,18 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
                                ctx->pm_order.as<int>(), ctx->pm_sums.as<int>(), cntr + 1, s)) != cudaSuccess)
         return cuda_fail(e, "sddm_render_photon_map: grid build");
     launches += slots > 0 ? 5 : 3;
-    unsigned long long hc[2];
+    unsigned long long hc[16];
     if ((e = cudaEventRecord(ctx->ev1, s)) ||
         (e = cudaMemcpyAsync(hc, cntr, sizeof(hc), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "sddm_render_photon_map: photon pass");
+    // counters: [0] megakernel photon segments, [1] stored, [2..9] DDM pass (segments at 2), int error word at [10]
+    int perr;
+    std::memcpy(&perr, hc + 10, sizeof perr);
+    if (perr != 0) {
+        char msg[128];
+        std::snprintf(msg, sizeof msg, "sddm_render_photon_map: device reported error %d in the photon pass", perr);
+        return fail(perr == 1 ? SDDM_ERR_QUEUE_OVERFLOW : SDDM_ERR_DEVICE_CHECK, msg);
+    }
     float pms = 0.f;
     cudaEventElapsedTime(&pms, ctx->ev0, ctx->ev1);
     v.on = 1;
@@ -1061,7 +1097,7 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
     if (rc != SDDM_OK) return rc;
     if (pst) {
         pst->photons = n_photons;
-        pst->photon_segments = (int64_t)hc[0];
+        pst->photon_segments = (int64_t)(hc[0] + hc[2]);
         pst->stored = (int64_t)hc[1];
         pst->grid_cells = cells;
         pst->photon_ms = pms;

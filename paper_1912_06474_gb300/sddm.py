@@ -297,14 +297,14 @@ class Context:
         self.last_stats = st.as_dict()
         return self.last_stats
 
-    def render_photon_map(self, spec, n_photons, radius):
+    def render_photon_map(self, spec, n_photons, radius, method="ddm", bsdf="exact"):
         """sddm_render_photon_map: photon pass of n_photons from the lights, then
-        the megakernel camera pass gathering the map within ``radius`` at the
-        first diffuse vertex. Returns (image [H,W,3] CUDA float32, stats,
+        the camera pass gathering the map within ``radius`` at the first diffuse
+        vertex, both by ``method``. Returns (image [H,W,3] CUDA float32, stats,
         photon stats)."""
         import torch
         img = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=torch.device("cuda", self.device))
-        arr, _keep = self._descs([spec], "megakernel", "exact", [img.data_ptr()], None, None)
+        arr, _keep = self._descs([spec], method, bsdf, [img.data_ptr()], None, None)
         st, pst = Stats(), PhotonStats()
         _check(lib.sddm_render_photon_map(self._h, arr, int(n_photons), float(radius), C.byref(st), C.byref(pst)))
         self.last_stats = st.as_dict()

@@ -27,7 +27,10 @@ def sddm():
     return m
 
 
-def _both(oracle_mod, sddm, sc, spec, n, r):
+METHODS = [("megakernel", (1, 1, 1)), ("ddm", (1, 1, 1)), ("ddm", (2, 2, 2)), ("ddm", (4, 4, 2))]
+
+
+def _both(oracle_mod, sddm, sc, spec, n, r, method="ddm", grid=(2, 2, 2)):
     t0 = time.perf_counter()
     orc = oracle_mod.Oracle(sc)
     pm = orc.photon_map(spec, n, r)
@@ -36,25 +39,26 @@ def _both(oracle_mod, sddm, sc, spec, n, r):
     ctx = sddm.Context(0)
     try:
         ctx.set_scene(sc)
-        ctx.build()
-        img, st, pst = ctx.render_photon_map(spec, n, r)
+        ctx.build(grid=grid)
+        img, st, pst = ctx.render_photon_map(spec, n, r, method=method)
         torch.cuda.synchronize()
         img = img.cpu().numpy()
     finally:
         ctx.close()
-    print(f"\n  photons {n}: oracle {t_orc:.2f} s, GPU photon pass {pst['photon_ms']:.3f} ms "
+    print(f"\n  {method} {grid} photons {n}: oracle {t_orc:.2f} s, GPU photon pass {pst['photon_ms']:.3f} ms "
           f"({pst['photon_segments']} segments, {pst['stored']} stored, {pst['grid_cells']} cells), "
           f"camera pass {st['gpu_ms']:.3f} ms")
     return img, ref, pst, len(pm.photons()[0])
 
 
+@pytest.mark.parametrize("method,grid", METHODS)
 @pytest.mark.parametrize("s", [0.0, 0.8])
-def test_tiny_room_photon_map(oracle_mod, sddm, s):
+def test_tiny_room_photon_map(oracle_mod, sddm, s, method, grid):
     sc = scenes.tiny_room(L=16)
     glass = {m: s for m in sc.glass_materials()}
     spec = scenes.RenderSpec(64, 48, 4, 5, seed=3, camera=sc.camera, glass_s=glass, nee=True)
     n = 100000
-    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.15)
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.15, method, grid)
     assert abs(pst["stored"] - n_ref) <= 1e-3 * n, (pst["stored"], n_ref)
     assert pst["photons"] == n
     err = rel_rmse(img, ref)
@@ -62,12 +66,13 @@ def test_tiny_room_photon_map(oracle_mod, sddm, s):
     assert err <= 1e-3
 
 
-def test_furnace_photon_map(oracle_mod, sddm):
+@pytest.mark.parametrize("method,grid", [("megakernel", (1, 1, 1)), ("ddm", (2, 2, 2))])
+def test_furnace_photon_map(oracle_mod, sddm, method, grid):
     D, rho0, Le0 = 5, 0.6, 0.7
     sc = scenes.furnace_box(L=8, rho0=rho0, Le0=Le0)
     spec = scenes.RenderSpec(32, 32, 2, D, seed=1, camera=sc.camera, nee=True)
     n = 200000
-    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.1)
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.1, method, grid)
     # every photon is stored once per hit from its second hit on, none escapes
     # (in FP64; an FP32 ray may slip through a box corner now and then)
     assert n_ref == n * (D - 2)
@@ -80,17 +85,18 @@ def test_furnace_photon_map(oracle_mod, sddm):
     assert np.all(np.abs(centre / want - 1) < 0.01), centre / want
 
 
-def test_depth_two_and_no_photons(oracle_mod, sddm):
+@pytest.mark.parametrize("method", ["megakernel", "ddm"])
+def test_depth_two_and_no_photons(oracle_mod, sddm, method):
     """D = 2: photons reach surfaces only straight from the lights, so nothing
     is stored; no photons at all: the map is empty. Either way the image is
     emission plus next-event light at the first diffuse vertex."""
     sc = scenes.tiny_room(L=16)
     spec2 = scenes.RenderSpec(40, 30, 2, 2, seed=5, camera=sc.camera, nee=True)
-    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec2, 20000, 0.2)
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec2, 20000, 0.2, method)
     assert pst["stored"] == 0 and n_ref == 0
     assert rel_rmse(img, ref) <= 1e-3
     spec5 = scenes.RenderSpec(40, 30, 2, 5, seed=5, camera=sc.camera, nee=True)
-    img0, ref0, pst0, _ = _both(oracle_mod, sddm, sc, spec5, 0, 0.2)
+    img0, ref0, pst0, _ = _both(oracle_mod, sddm, sc, spec5, 0, 0.2, method)
     assert pst0["stored"] == 0 and pst0["photon_segments"] == 0
     assert rel_rmse(img0, ref0) <= 1e-3
 
@@ -101,6 +107,9 @@ def test_photon_map_argument_checks(sddm):
     try:
         ctx.set_scene(sc)
         ctx.build()
+        with pytest.raises(sddm.SddmError):   # the learned glass model needs the DDM method
+            ctx.render_photon_map(scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 100, 0.1, method="megakernel",
+                                  bsdf="mlp")
         for spec, n, r in [(scenes.RenderSpec(8, 8, 1, 1, camera=sc.camera), 100, 0.1),
                            (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera, nee=False), 100, 0.1),
                            (scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 100, 0.0),
@@ -112,5 +121,44 @@ def test_photon_map_argument_checks(sddm):
         # the context still renders afterwards
         img, st, pst = ctx.render_photon_map(scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 1000, 0.1)
         assert pst["photons"] == 1000 and np.isfinite(img.cpu().numpy()).all()
+    finally:
+        ctx.close()
+
+
+@pytest.fixture(scope="module")
+def hotel_pm(oracle_mod):
+    sc = scenes.hotel_room(L=41, seed=0)
+    spec = scenes.hotel_room_render(sc, 512, 512, 16, 5, seed=0)
+    n, r = 1 << 20, 0.05
+    orc = oracle_mod.Oracle(sc)
+    t0 = time.perf_counter()
+    pm = orc.photon_map(spec, n, r)
+    pix = scenes.pixel_subset(512, 512, 2048, seed=1)
+    ref = orc.render_pixels(spec, pix, photon_map=pm)["xyz"]
+    print(f"\n  oracle hotel photon map + 2048 px: {time.perf_counter() - t0:.1f} s")
+    return sc, spec, n, r, pix, ref, len(pm.photons()[0])
+
+
+@pytest.mark.parametrize("method,grid", [("megakernel", (1, 1, 1)), ("ddm", (4, 4, 2))])
+def test_hotel_room_photon_map(sddm, hotel_pm, method, grid):
+    """The benchmark's hotel room (512 x 512 x 16 spp, depth 5, 41 bins) with
+    2^20 photons, on 2048 seeded pixels the oracle computes one by one; then
+    the photon pass alone at 2^22 photons for its throughput."""
+    sc, spec, n, r, pix, ref, n_ref = hotel_pm
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        ctx.build(grid=grid)
+        img, st, pst = ctx.render_photon_map(spec, n, r, method=method)
+        got = img.cpu().numpy().reshape(-1, 3)[pix]
+        e = rel_rmse(got, ref)
+        assert abs(pst["stored"] - n_ref) <= 1e-3 * n, (pst["stored"], n_ref)
+        small = scenes.RenderSpec(16, 16, 1, 5, seed=0, camera=spec.camera)
+        ctx.render_photon_map(small, 1 << 22, r, method=method)
+        _, _, p4 = ctx.render_photon_map(small, 1 << 22, r, method=method)
+        print(f"\n  hotel {method} {grid}: rel-RMSE on {len(pix)} px = {e:.2e}; camera pass {st['gpu_ms']:.2f} ms; "
+              f"photon pass 2^22 photons {p4['photon_ms']:.2f} ms, {p4['photon_segments']} segments = "
+              f"{p4['photon_segments'] / p4['photon_ms'] / 1e3:.1f} Mseg/s, {p4['stored']} stored")
+        assert e <= 1e-3
     finally:
         ctx.close()
