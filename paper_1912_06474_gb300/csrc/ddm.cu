@@ -806,6 +806,18 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers &buf, cudaStream_t s);
 
+// Blocks for a grid-stride kernel: at most `want`, rounded down to whole waves
+// of the blocks that fit on the SMs at once, so that no partial last wave runs
+// on a fraction of the machine.
+template <typename K>
+static unsigned whole_waves(K kernel, int threads, size_t smem, int sm, unsigned want) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        return want;
+    const unsigned wave = (unsigned)(per_sm * sm);
+    return want <= wave ? want : want / wave * wave;
+}
+
 int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
     return trace_chunk(run, PhotonGridView{}, buf, s);
 }
@@ -918,9 +930,12 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers 
     }
 
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
-    const int scatter_blocks = sm * 4;
+    const unsigned scatter_blocks = whole_waves(k_scatter, 256, 0, sm, (unsigned)sm * 4);
     const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
     const size_t ctl_bytes = 32 + 4 * (size_t)nb;
+    const unsigned cont_blocks = whole_waves(k_shade_continue, 256, sizeof(int) * (size_t)nb, sm, path_blocks);
+    // the glass count and gather passes share one partition of the path slots
+    const unsigned glass_blocks = whole_waves(k_glass_gather, 256, 0, sm, path_blocks);
     cudaError_t e;
 #define DDM_CHECK(x)                                                     \
     do {                                                                 \
@@ -954,9 +969,9 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers 
         }
         a.b = b;
         if (use_queries && b >= 2) {
-            k_glass_count<<<path_blocks, 256, 0, s>>>(a);
+            k_glass_count<<<glass_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
-            k_glass_gather<<<path_blocks, 256, 0, s>>>(a);
+            k_glass_gather<<<glass_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
             *run.launches += 1;
             if (use_mlp)
@@ -975,7 +990,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers 
             DDM_CHECK(cudaGetLastError());
             *run.launches += 1;
         }
-        k_shade_continue<<<path_blocks, 256, bins_smem, s>>>(a);
+        k_shade_continue<<<cont_blocks, 256, bins_smem, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         *run.launches += 2;
     }

@@ -285,8 +285,13 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
 // batch, chosen by Philox, is also evaluated exactly; if it is off by more
 // than 1e-3 in R or T, or if any row lies outside the trained box, the whole
 // batch is evaluated exactly instead.
+#ifndef SDDM_MLP_MINB
+#define SDDM_MLP_MINB 4   // resident inference blocks per SM asked of the register allocator: 64 registers
+                          // with ~100 B of spills, 32 warps per SM (+3% on the hotel bench against 80
+                          // registers and 24 warps)
+#endif
 template <bool FILMS>
-__global__ void __launch_bounds__(256) k_mlp_rows(MlpRows a) {
+__global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
     __shared__ InferSmem s;
     __shared__ float2 out[8][32];
     load_infer_weights(s, a.params);
@@ -785,8 +790,18 @@ size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 #ifndef SDDM_MLP_BLOCKS_PER_SM
 #define SDDM_MLP_BLOCKS_PER_SM 4   // inference blocks (8 warps, ~41 KB shared memory) per SM
 #endif
+// Blocks of a grid-stride row kernel: per SM, the most that fit at once (at
+// most `cap`), so that the grid is one whole wave.
+template <typename K>
+static int resident_per_sm(K kernel, int cap) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) return cap;
+    return n < cap ? n : cap;
+}
+
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
-    const int blocks = sm_count * SDDM_MLP_BLOCKS_PER_SM;
+    const int blocks = sm_count * (a.sc.mat_nfilm ? resident_per_sm(k_mlp_rows<true>, SDDM_MLP_BLOCKS_PER_SM)
+                                                  : resident_per_sm(k_mlp_rows<false>, SDDM_MLP_BLOCKS_PER_SM));
     if (a.sc.mat_nfilm)
         k_mlp_rows<true><<<blocks, 256, 0, stream>>>(a);
     else
@@ -796,9 +811,9 @@ cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream)
 
 cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
     if (a.sc.mat_nfilm)
-        k_slab_rows<true><<<sm_count * 8, 256, 0, stream>>>(a);
+        k_slab_rows<true><<<sm_count * resident_per_sm(k_slab_rows<true>, 8), 256, 0, stream>>>(a);
     else
-        k_slab_rows<false><<<sm_count * 8, 256, 0, stream>>>(a);
+        k_slab_rows<false><<<sm_count * resident_per_sm(k_slab_rows<false>, 8), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
