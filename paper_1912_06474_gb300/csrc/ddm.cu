@@ -293,7 +293,11 @@ __device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp) {
 // Sort the staged rays by cell. Each block bins a tile of 1024 rays in shared
 // memory and reserves one range per (tile, cell) with a single global atomic.
 constexpr int kScatterRaysPerThread = 4;
-__global__ void __launch_bounds__(256) k_scatter(KArgs a) {
+#ifndef SDDM_SCATTER_MINB
+#define SDDM_SCATTER_MINB 4  // resident 256-thread blocks per SM the scatter is compiled for (64
+                             // registers, no spills, 4 blocks instead of 3)
+#endif
+__global__ void __launch_bounds__(256, SDDM_SCATTER_MINB) k_scatter(KArgs a) {
     __shared__ int s_off[kMaxBins + 1];
     __shared__ int s_bin[kMaxBins];
     __shared__ int s_tmp[256];
@@ -469,10 +473,12 @@ __global__ void __launch_bounds__(256) k_glass_gather(KArgs a) {
 // Spectral half of shading: resolve the previous vertex's shadow ray, apply its
 // weight, add this vertex's emission, per bin, with compensated sums.
 #ifndef SDDM_SHS_MINB
-#define SDDM_SHS_MINB 4      // resident 256-thread blocks per SM the spectral pass is compiled for
+#define SDDM_SHS_MINB 6      // resident 256-thread blocks per SM the spectral pass is compiled for (40
+                             // registers with some spills: 48 warps hide the per-bin load latency; +1.7%
+                             // on the hotel bench against 4 blocks, 8 blocks -1.6%)
 #endif
 #ifndef SDDM_SHS_UNROLL
-#define SDDM_SHS_UNROLL 4    // bins in flight per thread
+#define SDDM_SHS_UNROLL 2    // bins in flight per thread (8: -6%)
 #endif
 constexpr int kShsUnroll = SDDM_SHS_UNROLL;
 template <bool FILMS>
@@ -633,7 +639,11 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
 
 // Continuation half of shading: next-event sample toward the lights and the
 // next direction at this vertex, appended to the ray staging area.
-__global__ void __launch_bounds__(256) k_shade_continue(KArgs a) {
+#ifndef SDDM_SHC_MINB
+#define SDDM_SHC_MINB 4      // resident 256-thread blocks per SM the continuation pass is compiled for
+                             // (64 registers instead of 77, 4 blocks instead of 3)
+#endif
+__global__ void __launch_bounds__(256, SDDM_SHC_MINB) k_shade_continue(KArgs a) {
     const int64_t np = a.ps.np;
     const DevScene &sc = a.sc;
     const int L = sc.L;
