@@ -133,26 +133,34 @@ __device__ __forceinline__ void features(float c, float lam, float s, float alph
 }
 
 // ------------------------------------------------------------- inference
+// The hidden layers' weights and biases are stored halved: the layer then
+// produces h = z / 2 directly (halving is exact in binary floating point, so
+// the activations are bit for bit those of the unscaled layer), and
+// SiLU(z) = h + h tanh(h) costs one SFU operation and one FMA.
 struct InferSmem {
-    __nv_bfloat16 w2[H * LD], w3[H * LD];
-    float w1[H * 4], b1[H], b2[H], b3[H], w4[2 * H], b4[2];
+    __nv_bfloat16 w2[H * LD], w3[H * LD];   // W / 2
+    float w1[H * 4], b1[H], b2[H], b3[H];   // W1 / 2, b / 2
+    float w4[2 * H], b4[2];
 };
 
 __device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
     for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
         const int r = i >> 6, c = i & 63;
-        s.w2[r * LD + c] = __float2bfloat16_rn(p[OFF_W2 + i]);
-        s.w3[r * LD + c] = __float2bfloat16_rn(p[OFF_W3 + i]);
+        s.w2[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W2 + i]);
+        s.w3[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W3 + i]);
     }
-    for (int i = threadIdx.x; i < H * 4; i += blockDim.x) s.w1[i] = bf16r(p[OFF_W1 + i]);
+    for (int i = threadIdx.x; i < H * 4; i += blockDim.x) s.w1[i] = 0.5f * bf16r(p[OFF_W1 + i]);
     for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) s.w4[i] = bf16r(p[OFF_W4 + i]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        s.b1[i] = p[OFF_B1 + i];
-        s.b2[i] = p[OFF_B2 + i];
-        s.b3[i] = p[OFF_B3 + i];
+        s.b1[i] = 0.5f * p[OFF_B1 + i];
+        s.b2[i] = 0.5f * p[OFF_B2 + i];
+        s.b3[i] = 0.5f * p[OFF_B3 + i];
     }
     if (threadIdx.x < 2) s.b4[threadIdx.x] = p[OFF_B4 + threadIdx.x];
 }
+
+// SiLU of z given h = z / 2.
+__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
 
 // The network on the 16 rows of a warp tile; this thread supplies the inputs
 // of rows g and g + 8 and receives their outputs (the same on the 4 lanes of
@@ -173,8 +181,8 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
                 zl = fmaf(s.w1[4 * c + k], xl[k], zl);
                 zh = fmaf(s.w1[4 * c + k], xh[k], zh);
             }
-            h[j][e] = silu(zl);
-            h[j][2 + e] = silu(zh);
+            h[j][e] = silu_h(zl);
+            h[j][2 + e] = silu_h(zh);
         }
     }
     uint32_t fa[4][4];
@@ -185,21 +193,29 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
-        h[j][0] = silu(acc[j][0] + s.b2[c]);
-        h[j][1] = silu(acc[j][1] + s.b2[c + 1]);
-        h[j][2] = silu(acc[j][2] + s.b2[c]);
-        h[j][3] = silu(acc[j][3] + s.b2[c + 1]);
+        h[j][0] = silu_h(acc[j][0] + s.b2[c]);
+        h[j][1] = silu_h(acc[j][1] + s.b2[c + 1]);
+        h[j][2] = silu_h(acc[j][2] + s.b2[c]);
+        h[j][3] = silu_h(acc[j][3] + s.b2[c + 1]);
     }
     pack_afrag(h, fa);
     zero_acc(acc);
     warp_gemm_reg(acc, fa, s.w3, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = 8 * j + 2 * t;
+        acc[j][0] += s.b3[c];
+        acc[j][1] += s.b3[c + 1];
+        acc[j][2] += s.b3[c];
+        acc[j][3] += s.b3[c + 1];
+    }
     float pl0 = 0.f, pl1 = 0.f, ph0 = 0.f, ph1 = 0.f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             const int c = 8 * j + 2 * t + e;
-            const float hl = bf16r(silu(acc[j][e] + s.b3[c])), hh = bf16r(silu(acc[j][2 + e] + s.b3[c]));
+            const float hl = bf16r(silu_h(acc[j][e])), hh = bf16r(silu_h(acc[j][2 + e]));
             pl0 = fmaf(s.w4[c], hl, pl0);
             pl1 = fmaf(s.w4[H + c], hl, pl1);
             ph0 = fmaf(s.w4[c], hh, ph0);
