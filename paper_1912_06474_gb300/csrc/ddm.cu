@@ -332,8 +332,15 @@ __global__ void __launch_bounds__(256, SDDM_SCATTER_MINB) k_scatter(KArgs a) {
                 r1[k] = src[1];
                 r2[k] = src[2];
                 cell[k] = ray_bin(a.g, __float_as_int(r2[k].w), __float_as_int(r2[k].z), r0[k], r1[k]);
-                rank[k] = atomicAdd(s_bin + cell[k], 1);
             }
+            // lanes of a warp with the same bin take consecutive ranks with one
+            // shared-memory atomic (neighbouring rays mostly share their bin)
+            const unsigned peers = __match_any_sync(0xffffffffu, cell[k]);
+            const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+            int r = 0;
+            if (lane == leader && cell[k] >= 0) r = atomicAdd(s_bin + cell[k], __popc(peers));
+            r = __shfl_sync(0xffffffffu, r, leader);
+            rank[k] = r + __popc(peers & ((1u << lane) - 1u));
         }
         __syncthreads();
         for (int c = threadIdx.x; c < n_cells; c += blockDim.x)
