@@ -162,3 +162,18 @@ def test_hotel_room_photon_map(sddm, hotel_pm, method, grid):
         assert e <= 1e-3
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("method,grid", [("megakernel", (1, 1, 1)), ("ddm", (2, 2, 2))])
+def test_coated_room_photon_map(oracle_mod, sddm, method, grid):
+    """Photons through the electrochromic pane (3-film stack on both faces):
+    the film code paths of the photon pass and of the camera pass."""
+    sc = scenes.tiny_room(L=16, coated=True)
+    glass = {m: 0.6 for m in sc.glass_materials()}
+    spec = scenes.RenderSpec(48, 32, 4, 5, seed=9, camera=sc.camera, glass_s=glass, nee=True)
+    n = 100000
+    img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.15, method, grid)
+    assert abs(pst["stored"] - n_ref) <= 1e-3 * n, (pst["stored"], n_ref)
+    err = rel_rmse(img, ref)
+    print(f"  coated room image rel-RMSE vs oracle {err:.2e}")
+    assert err <= 1e-3
