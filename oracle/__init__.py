@@ -67,7 +67,7 @@ class _RenderDesc(C.Structure):
                 ("seed", C.c_uint32), ("render_id", C.c_uint32), ("nee", C.c_int),
                 ("cam_pos", C.c_double * 3), ("cam_look", C.c_double * 3), ("cam_up", C.c_double * 3),
                 ("vfov_deg", C.c_double), ("ortho_height", C.c_double), ("s_override", C.c_void_p),
-                ("brute_force", C.c_int), ("photon_map", C.c_void_p)]
+                ("brute_force", C.c_int), ("photon_map", C.c_void_p), ("caustic_map", C.c_void_p)]
 
 
 def _load():
@@ -90,6 +90,8 @@ def _load():
         lib.orc_slab.argtypes = [C.c_double] * 5 + [P, P]
         lib.orc_photon_map_build.argtypes = [P, P, C.c_int64, C.c_double, C.c_int]
         lib.orc_photon_map_build.restype = C.c_void_p
+        lib.orc_photon_map_build_kind.argtypes = [P, P, C.c_int64, C.c_double, C.c_int, C.c_int]
+        lib.orc_photon_map_build_kind.restype = C.c_void_p
         lib.orc_photon_map_free.argtypes = [P]
         lib.orc_photon_map_get.argtypes = [P, P, P, P]
         lib.orc_photon_map_get.restype = C.c_int64
@@ -375,16 +377,19 @@ class Oracle:
         self.lib.orc_camera_ray(C.byref(r), float(px), float(py), _ptr(o), _ptr(d))
         return o, d
 
-    def photon_map(self, spec, n_photons, radius, n_threads=0):
+    def photon_map(self, spec, n_photons, radius, n_threads=0, kind="all"):
         """Photon map of this scene for the render ``spec`` (its seed, render id,
-        depth and coloration states): a handle for render_pixels."""
+        depth and coloration states): a handle for render_pixels. ``kind``:
+        "all" stored photons, or only the "global" or the "caustic" ones."""
         r, keep = self._render_desc(spec, False)
-        h = self.lib.orc_photon_map_build(self._h, C.byref(r), int(n_photons), float(radius), int(n_threads))
+        h = self.lib.orc_photon_map_build_kind(self._h, C.byref(r), int(n_photons), float(radius),
+                                               {"all": 0, "global": 1, "caustic": 2}[kind], int(n_threads))
         if not h:
             raise RuntimeError("orc_photon_map_build failed")
         return _PhotonMap(self.lib, h, self.scene.L)
 
-    def render_pixels(self, spec, pix=None, n_threads=0, per_sample=False, brute_force=False, photon_map=None):
+    def render_pixels(self, spec, pix=None, n_threads=0, per_sample=False, brute_force=False, photon_map=None,
+                      caustic_map=None):
         """Render the listed pixels (all if None). Returns a dict with ``xyz``
         [n,3]; with ``per_sample`` also ``sample_xyz`` [n,spp,3], ``first_prim``
         [n,spp], ``margin`` [n,spp] and ``cos_min`` [n,spp]; ``segments`` = (extension, shadow)."""
@@ -395,6 +400,8 @@ class Oracle:
         r, s_keep = self._render_desc(spec, brute_force)
         if photon_map is not None:
             r.photon_map = photon_map.h
+            if caustic_map is not None:
+                r.caustic_map = caustic_map.h
         xyz = np.zeros((n, 3), np.float64)
         sx = fp = mg = cm = None
         if per_sample:

@@ -350,7 +350,7 @@ static void trace_photon(const orc_ctx *c, const orc_render_desc *r, uint32_t i,
     const double *Le = c->a + (size_t)c->mat[lt] * L;
     for (int l = 0; l < L; ++l)
         Phi[l] = Le[l] * PI * c->light_area * phi0_scale;
-    int excl_prim = lt, excl_obj = -1, changed = 0;
+    int excl_prim = lt, excl_obj = -1, changed = 0, diffuse_seen = 0;
     for (int b = 1; b <= D - 1; ++b) {
         orc_hit h;
         if (!orc_trace_closest(c, o, d, excl_prim, excl_obj, r->brute_force, &h, NULL))
@@ -372,7 +372,7 @@ static void trace_photon(const orc_ctx *c, const orc_render_desc *r, uint32_t i,
                     q[a] = x[a];
                     q[3 + a] = d[a];
                 }
-                q[6] = 1.0;
+                q[6] = diffuse_seen ? 1.0 : 2.0;   /* 1: global, 2: caustic (only specular reflections so far) */
                 for (int l = 0; l < L; ++l)
                     pw[(size_t)(b - 1) * L + l] = Phi[l];
             }
@@ -388,6 +388,7 @@ static void trace_photon(const orc_ctx *c, const orc_render_desc *r, uint32_t i,
             excl_prim = tri;
             excl_obj = -1;
             changed = 1;
+            diffuse_seen = 1;
         } else if (kind == ORC_CONDUCTOR) {
             if (b == D - 1)
                 return;
@@ -481,8 +482,14 @@ static int64_t pm_cell(const orc_pmap *pm, const double *x)
 
 void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int n_threads)
 {
+    return orc_photon_map_build_kind(ctx, r, n_photons, radius, 0, n_threads);
+}
+
+void *orc_photon_map_build_kind(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int kind,
+                                int n_threads)
+{
     const orc_ctx *c = (const orc_ctx *)ctx;
-    if (!c || !r || n_photons < 0 || !(radius > 0.0) || r->max_depth < 2)
+    if (!c || !r || n_photons < 0 || !(radius > 0.0) || r->max_depth < 2 || kind < 0 || kind > 2)
         return NULL;
     const int L = c->L, D = r->max_depth;
     size_t slots = (size_t)n_photons * (size_t)(D - 1);
@@ -514,9 +521,11 @@ void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photon
     for (int t = 0; t < started; ++t)
         pthread_join(th[t], NULL);
     /* compact the stored photons in slot order */
+    /* kind 0: every stored photon; 1: global photons only; 2: caustic photons only */
+#define PM_KEEP(flag) ((flag) != 0.0 && (kind == 0 || (flag) == (double)kind))
     int64_t n = 0;
     for (size_t s = 0; s < slots; ++s)
-        n += rec[7 * s + 6] != 0.0;
+        n += PM_KEEP(rec[7 * s + 6]);
     pm->L = L;
     pm->n = n;
     pm->radius = radius;
@@ -530,7 +539,7 @@ void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photon
     }
     int64_t k = 0;
     for (size_t s = 0; s < slots; ++s) {
-        if (rec[7 * s + 6] == 0.0)
+        if (!PM_KEEP(rec[7 * s + 6]))
             continue;
         for (int a = 0; a < 3; ++a) {
             pm->pos[3 * k + a] = rec[7 * s + a];
@@ -742,8 +751,10 @@ static void trace_path(const orc_ctx *c, const orc_render_desc *r, int px, int p
                     }
                 }
             }
-            if (r->photon_map) {   /* photon mapping: indirect and caustic light from the map, then stop */
+            if (r->photon_map) {   /* photon mapping: indirect and caustic light from the map(s), then stop */
                 pm_gather((const orc_pmap *)r->photon_map, x, ns, rho, T, Ls);
+                if (r->caustic_map)
+                    pm_gather((const orc_pmap *)r->caustic_map, x, ns, rho, T, Ls);
                 break;
             }
             if (b == r->max_depth)

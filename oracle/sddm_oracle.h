@@ -78,6 +78,8 @@ typedef struct {
     const void *photon_map;   /* NULL, or a photon map (orc_photon_map_build): at the first diffuse
                                  vertex the path adds next-event light and the photons' radiance
                                  estimate, then stops */
+    const void *caustic_map;  /* NULL, or a second map gathered there too (with photon_map set): the
+                                 caustic photons when photon_map holds the global ones */
 } orc_render_desc;
 
 /* Photon map (Sec. 4, global illumination by photon mapping). Photons leave
@@ -89,6 +91,12 @@ typedef struct {
  * glass or not, is next-event light). Random numbers: Philox counter (photon,
  * 0xffffffff, hit, slot), key (seed, render id). */
 void *orc_photon_map_build(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int n_threads);
+/* The same photons split in two maps (Sec. 4 names global and caustic maps): a
+ * stored photon is caustic when only reflections (metal, glass), no diffuse
+ * bounce, changed its direction since the light; kind 0 keeps every stored
+ * photon, 1 the global ones, 2 the caustic ones. */
+void *orc_photon_map_build_kind(void *ctx, const orc_render_desc *r, int64_t n_photons, double radius, int kind,
+                                int n_threads);
 void orc_photon_map_free(void *pm);
 /* Stored photons: count, and optionally positions [n][3], directions [n][3], power [n][L]. */
 int64_t orc_photon_map_get(const void *pm, double *pos, double *dir, double *power);

@@ -67,3 +67,29 @@ def test_empty_map_leaves_emission_and_direct_light(oracle_mod):
     want = Le0 * (1 + rho0) * (sc.quad_w.astype(np.float64)[:, None] * sc.cmf.astype(np.float64)).sum(0)
     mean = img.mean((0, 1))
     assert np.all(np.abs(mean / want - 1) < 0.01), mean / want
+
+
+def test_global_and_caustic_maps_split_the_same_photons(oracle_mod):
+    """Global and caustic maps hold the same stored photons as the single map
+    (a photon is caustic when only reflections, no diffuse bounce, turned it):
+    counts and power add up, and with equal radii the two-map render equals the
+    one-map render. The closed furnace has no specular surface, so no caustics."""
+    sc = scenes.tiny_room(L=16)
+    spec = scenes.RenderSpec(24, 16, 2, 5, seed=4, camera=sc.camera, nee=True)
+    orc = oracle_mod.Oracle(sc)
+    n, r = 40000, 0.2
+    pa, pg, pc = (orc.photon_map(spec, n, r, kind=k) for k in ("all", "global", "caustic"))
+    (xa, _, wa), (xg, _, wg), (xc, _, wc) = pa.photons(), pg.photons(), pc.photons()
+    assert len(xc) > 0 and len(xg) > 0
+    assert len(xa) == len(xg) + len(xc)
+    assert np.allclose(wa.sum(0), wg.sum(0) + wc.sum(0), rtol=1e-12)
+    img_a = orc.render_pixels(spec, photon_map=pa)["xyz"]
+    img_s = orc.render_pixels(spec, photon_map=pg, caustic_map=pc)["xyz"]
+    assert np.allclose(img_a, img_s, rtol=1e-12, atol=1e-15)
+    # a smaller caustic radius changes the estimate only through the caustic photons
+    pc_small = orc.photon_map(spec, n, 0.05, kind="caustic")
+    img_c = orc.render_pixels(spec, photon_map=pg, caustic_map=pc_small)["xyz"]
+    img_g = orc.render_pixels(spec, photon_map=pg)["xyz"]
+    assert not np.allclose(img_c, img_s) and np.all(img_c >= img_g - 1e-15)
+    fsc, fspec, _, _ = _furnace(5)
+    assert len(oracle_mod.Oracle(fsc).photon_map(fspec, 20000, 0.1, kind="caustic").photons()[0]) == 0
