@@ -231,10 +231,11 @@ int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st
 typedef struct {
     int64_t photons;          /* photons emitted */
     int64_t photon_segments;  /* closest-hit queries of the photon pass */
-    int64_t stored;           /* photons stored in the map */
-    int64_t grid_cells;       /* cells of the uniform grid the map is sorted into */
+    int64_t stored;           /* photons stored in the map (the global map when caustic_radius > 0) */
+    int64_t grid_cells;       /* cells of the uniform grid(s) the map(s) are sorted into */
     double photon_ms;         /* device time of the photon pass and grid build */
     int64_t kernel_launches;  /* kernels of the photon pass and grid build */
+    int64_t stored_caustic;   /* photons in the caustic map (caustic_radius > 0), else 0 */
 } sddm_photon_stats;
 
 /* Render one image by photon mapping (Sec. 4: global illumination computed
@@ -256,15 +257,21 @@ typedef struct {
  * camera pass of sddm_render with the megakernel: emission and the shadow ray
  * at the first diffuse vertex as usual, plus rho/pi times the power of the
  * stored photons within `radius` whose direction points into the visible
- * side, over pi radius^2; the path stops there. The photon pass evaluates
+ * side, over pi radius^2; the path stops there. With caustic_radius > 0 the
+ * stored photons form two maps (Sec. 4 names a global and a caustic map): a
+ * photon that only reflections (metal, glass) have turned since the light,
+ * without a diffuse bounce, goes to the caustic map, gathered within
+ * caustic_radius; the others to the global map, gathered within radius; both
+ * are added. caustic_radius = 0 keeps one map of every stored photon. The photon pass evaluates
  * glass exactly; the camera pass follows d->bsdf_mode (the learned model runs
  * with the DDM method only). Needs d->nee 1, d->max_depth >= 2, radius > 0,
- * n_photons * (max_depth - 1) < 2^31 (else SDDM_ERR_INVALID_ARG). The map lives in library-owned device memory: 16
+ * caustic_radius >= 0, n_photons * (max_depth - 1) < 2^31 (else
+ * SDDM_ERR_INVALID_ARG). The map lives in library-owned device memory: 16
  * bytes x 2 + 4 L bytes per photon and bounce, reused by later calls; too
  * little device memory gives SDDM_ERR_OOM. Synchronous; outputs as
  * sddm_render (d->xyz_out DEVICE). st and pst may be NULL. */
 int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_photons, float radius,
-                           sddm_stats *st, sddm_photon_stats *pst);
+                           float caustic_radius, sddm_stats *st, sddm_photon_stats *pst);
 
 /* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}), the
  * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per

@@ -74,6 +74,7 @@ struct KArgs {
     const float2 *glass_res;
     int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
     PhotonGridView pm;    // photon map: gather at the first diffuse vertex, no continuation there
+    PhotonGridView pmc;   // caustic map gathered with it (pmc.on)
 };
 
 // Queue bin of a ray: its cell, its kind (extension / shadow) and, as far as
@@ -821,7 +822,8 @@ cudaError_t check_kernel_image() {
 // ------------------------------------------------------------- host side
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers &buf, cudaStream_t s);
+static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const PhotonGridView &pmcv, DDMBuffers &buf,
+                       cudaStream_t s);
 
 // Blocks for a grid-stride kernel: at most `want`, rounded down to whole waves
 // of the blocks that fit on the SMs at once, so that no partial last wave runs
@@ -836,14 +838,16 @@ static unsigned whole_waves(K kernel, int threads, size_t smem, int sm, unsigned
 }
 
 int ddm_trace_chunk(const DDMRun &run, DDMBuffers &buf, cudaStream_t s) {
-    return trace_chunk(run, PhotonGridView{}, buf, s);
+    return trace_chunk(run, PhotonGridView{}, PhotonGridView{}, buf, s);
 }
 
-int ddm_trace_chunk_pm(const DDMRun &run, const PhotonGridView &pm, DDMBuffers &buf, cudaStream_t s) {
-    return trace_chunk(run, pm, buf, s);
+int ddm_trace_chunk_pm(const DDMRun &run, const PhotonGridView &pm, const PhotonGridView &pmc, DDMBuffers &buf,
+                       cudaStream_t s) {
+    return trace_chunk(run, pm, pmc, buf, s);
 }
 
-static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers &buf, cudaStream_t s) {
+static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const PhotonGridView &pmcv, DDMBuffers &buf,
+                       cudaStream_t s) {
     const int64_t np = run.path_count;
     const int L = run.sc.L;
     const int nc = run.g.n_cells, nb = run.g.n_bins;
@@ -930,6 +934,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, DDMBuffers 
     a.glass_res = (const float2 *)(m + oRes);
     a.block_cnt = (int *)(m + oBc);
     a.pm = pmv;
+    a.pmc = pmcv;
     MlpRows mr{};
     if (use_queries) {
         mr.params = run.mlp_params;

@@ -17,6 +17,7 @@
 // k_shade_continue then issues the shadow ray but no continuation.
 
 constexpr int kFlPhotonTurned = 16;   // the photon's direction has changed (bounce or reflection)
+constexpr int kFlPhotonDiffuse = 32;  // ... by a diffuse bounce (else it is a caustic photon)
 
 struct PhotonPass {
     int64_t begin, n_total;
@@ -108,13 +109,14 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
                 const float cd = dot(d, ng);
                 const V3 ns = cd < 0.0f ? ng : (-1.0f) * ng;
                 const float *mA = sc.mat_a + (size_t)mat * L, *mB = sc.mat_b + (size_t)mat * L;
-                bool go = false, turn = true;   // a transmitted photon keeps its direction
+                bool go = false, turn = true, diffuse = false;   // a transmitted photon keeps its direction
                 V3 on = x, dn = d;
                 int excl = prim;
                 if (kind == kLambert || kind == kDiffuseEmitter) {
                     if (fl & kFlPhotonTurned) {
                         const size_t slot = (size_t)(pp.begin + q) * (D - 1) + (b - 1);
-                        pp.pos[slot] = make_float4(x.x, x.y, x.z, 1.0f);
+                        // w: 1 global photon, 2 caustic photon (only reflections turned it)
+                        pp.pos[slot] = make_float4(x.x, x.y, x.z, (fl & kFlPhotonDiffuse) ? 1.0f : 2.0f);
                         pp.dir[slot] = make_float4(d.x, d.y, d.z, 0.0f);
                         float *pw = pp.pow + slot * L;
                         for (int i = 0; i < L; ++i) pw[i] = a.ps.T[(size_t)i * np + q];
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
                         for (int i = 0; i < L; ++i) a.ps.T[(size_t)i * np + q] *= __ldg(rho + i);
                         on = x + kRayOffset * ns;
                         go = true;
+                        diffuse = true;
                     }
                 } else if (kind == kConductor) {
                     if (b < D - 1) {
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
                     }
                 }
                 if (go) {
-                    nfl = kFlExt | ((turn || (fl & kFlPhotonTurned)) ? kFlPhotonTurned : 0);
+                    nfl = kFlExt | ((turn || (fl & kFlPhotonTurned)) ? kFlPhotonTurned : 0) |
+                          ((diffuse || (fl & kFlPhotonDiffuse)) ? kFlPhotonDiffuse : 0);
                     ++n_ext;
                     a.ps.hit0[q] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
                     float t0;
@@ -188,7 +192,10 @@ __global__ void __launch_bounds__(256) k_ddm_gather(KArgs a) {
     const int L = sc.L, b = a.b;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const PathState &ps = a.ps;
-    const float norm = 1.0f / (3.14159265358979f * 3.14159265358979f * a.pm.radius * a.pm.radius);
+    // rho / pi times the power over pi r^2 of each map (global, caustic)
+    const float inv_g = 1.0f / (3.14159265358979f * a.pm.radius * a.pm.radius);
+    const float inv_c = a.pmc.on ? 1.0f / (3.14159265358979f * a.pmc.radius * a.pmc.radius) : 0.0f;
+    const float norm = 1.0f / 3.14159265358979f;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += stride) {
         const int fl = ps.flags[q];
         if (!(fl & kFlExt)) continue;
@@ -208,6 +215,12 @@ __global__ void __launch_bounds__(256) k_ddm_gather(KArgs a) {
             const float *pw = a.pm.pow + (size_t)slot * L;
             for (int i = 0; i < L; ++i) S[i] += __ldg(pw + i);
         });
+        for (int i = 0; i < L; ++i) S[i] *= inv_g;
+        if (a.pmc.on)
+            pm_gather_visit(a.pmc, xyz(h0), ns, [&](int slot) {
+                const float *pw = a.pmc.pow + (size_t)slot * L;
+                for (int i = 0; i < L; ++i) S[i] = fmaf(__ldg(pw + i), inv_c, S[i]);
+            });
         const float *rho = (kind == kLambert ? sc.mat_a : sc.mat_b) + (size_t)mat * L;
         Kahan X, Y, Z;
         for (int i = 0; i < L; ++i) {

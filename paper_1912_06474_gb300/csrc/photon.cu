@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(128) k_photon_trace(DevScene sc, PhotonTraceAr
     const float scale = 3.14159265358979f * sc.light_area / (float)a.n_photons;
     for (int l = 0; l < L; ++l) Phi[l] = __ldg(Le + l) * scale;
     int excl_prim = lt, excl_obj = -1;
-    bool changed = false;
+    bool changed = false, diffuse = false;   // turned at all / by a diffuse bounce
     unsigned long long segs = 0;
     for (int b = 1; b <= D - 1; ++b) {
         const Ray ray = make_ray(o, d);
@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(128) k_photon_trace(DevScene sc, PhotonTraceAr
         if (kind == kLambert || kind == kDiffuseEmitter) {
             if (changed) {
                 const size_t slot = (size_t)i * (D - 1) + (b - 1);
-                a.pos[slot] = make_float4(x.x, x.y, x.z, 1.0f);
+                // w: 1 global photon, 2 caustic photon (only reflections turned it)
+                a.pos[slot] = make_float4(x.x, x.y, x.z, diffuse ? 1.0f : 2.0f);
                 a.dir[slot] = make_float4(d.x, d.y, d.z, 0.0f);
                 float *pw = a.pow + slot * L;
                 for (int l = 0; l < L; ++l) pw[l] = Phi[l];
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(128) k_photon_trace(DevScene sc, PhotonTraceAr
             excl_prim = h.prim;
             excl_obj = -1;
             changed = true;
+            diffuse = true;
         } else if (kind == kConductor) {
             if (b == D - 1) break;
             const float c = fabsf(cd);
@@ -125,12 +127,15 @@ __device__ __forceinline__ int pm_cell_of(const PhotonGridView &g, float4 p) {
     return (c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
 }
 
-__global__ void k_pm_count(PhotonGridView g, int64_t slots, int *cnt, unsigned long long *stored) {
+// Stored photons of the wanted kind: 0 any, 1 global, 2 caustic.
+__device__ __forceinline__ bool pm_keep(float w, int kind) { return w != 0.0f && (kind == 0 || w == (float)kind); }
+
+__global__ void k_pm_count(PhotonGridView g, int64_t slots, int kind, int *cnt, unsigned long long *stored) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool ok = false;
     if (s < slots) {
         const float4 p = g.pos[s];
-        if (p.w != 0.0f) {
+        if (pm_keep(p.w, kind)) {
             atomicAdd(cnt + pm_cell_of(g, p), 1);
             ok = true;
         }
@@ -139,11 +144,11 @@ __global__ void k_pm_count(PhotonGridView g, int64_t slots, int *cnt, unsigned l
     if ((threadIdx.x & 31) == 0 && m) atomicAdd(stored, (unsigned long long)__popc(m));
 }
 
-__global__ void k_pm_scatter(PhotonGridView g, int64_t slots, const int *start, int *fill, int *order) {
+__global__ void k_pm_scatter(PhotonGridView g, int64_t slots, int kind, const int *start, int *fill, int *order) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= slots) return;
     const float4 p = g.pos[s];
-    if (p.w == 0.0f) return;
+    if (!pm_keep(p.w, kind)) return;
     const int c = pm_cell_of(g, p);
     order[start[c] + atomicAdd(fill + c, 1)] = (int)s;
 }
@@ -207,7 +212,7 @@ cudaError_t launch_photon_trace(const DevScene &sc, const PhotonTraceArgs &a, cu
     return cudaGetLastError();
 }
 
-cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int *cnt, int *start, int *fill, int *order,
+cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int kind, int *cnt, int *start, int *fill, int *order,
                               int *scan_sums, unsigned long long *stored, cudaStream_t s) {
     const int64_t cells = (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
     const unsigned ns = (unsigned)((slots + 255) / 256);
@@ -216,12 +221,12 @@ cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int *cnt, int *s
         (e = cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)cells, s)) ||
         (e = cudaMemsetAsync(stored, 0, sizeof(unsigned long long), s)))
         return e;
-    if (ns > 0) k_pm_count<<<ns, 256, 0, s>>>(g, slots, cnt, stored);
+    if (ns > 0) k_pm_count<<<ns, 256, 0, s>>>(g, slots, kind, cnt, stored);
     const int nb = (int)((cells + kScanTile - 1) / kScanTile);
     k_scan_sums<<<nb, 256, 0, s>>>(cnt, cells, scan_sums);
     k_scan_top<<<1, 32, 0, s>>>(scan_sums, nb, start + cells);
     k_scan_apply<<<nb, 256, 0, s>>>(cnt, cells, scan_sums, start);
-    if (ns > 0) k_pm_scatter<<<ns, 256, 0, s>>>(g, slots, start, fill, order);
+    if (ns > 0) k_pm_scatter<<<ns, 256, 0, s>>>(g, slots, kind, start, fill, order);
     return cudaGetLastError();
 }
 

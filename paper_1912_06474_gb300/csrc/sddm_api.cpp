@@ -140,7 +140,8 @@ struct sddm_ctx {
     // photon map (sddm_render_photon_map): slots, grid, and the view the
     // megakernel reads while pm_view.on
     DevBuf pm_state, pm_scratch, pm_pos, pm_dir, pm_pow, pm_cnt, pm_start, pm_fill, pm_order, pm_sums, pm_cntr;
-    PhotonGridView pm_view{};
+    DevBuf pmc_cnt, pmc_start, pmc_fill, pmc_order, pmc_sums;   // the caustic map's grid
+    PhotonGridView pm_view{}, pmc_view{};
     DDMBuffers pm_ddm_buf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int profile = 0;
@@ -831,6 +832,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
                 a.error_flag = ctx->d_err.as<int>();
                 a.count_traversal = count_trav;
                 a.pm = ctx->pm_view;
+                a.pmc = ctx->pmc_view;
                 cudaEvent_t t0 = nullptr, t1 = nullptr;
                 if (time_trace) {
                     if ((e = ctx->ddm_buf.event_pair(t0, t1)) || (e = cudaEventRecord(t0, s)))
@@ -863,7 +865,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
                 run.mlp_dmin = mlp_dmin;
                 run.mlp_dmax = mlp_dmax;
                 run.probe_key = d[0].seed ^ 0x9e3779b9u;
-                int rc2 = ctx->pm_view.on ? ddm_trace_chunk_pm(run, ctx->pm_view, ctx->ddm_buf, s)
+                int rc2 = ctx->pm_view.on ? ddm_trace_chunk_pm(run, ctx->pm_view, ctx->pmc_view, ctx->ddm_buf, s)
                                           : ddm_trace_chunk(run, ctx->ddm_buf, s);
                 if (rc2 != SDDM_OK) return rc2;
             }
@@ -974,7 +976,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
 }
 
 int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_photons, float radius,
-                           sddm_stats *st, sddm_photon_stats *pst) {
+                           float caustic_radius, sddm_stats *st, sddm_photon_stats *pst) {
     int rc = validate_desc(ctx, d, 1);
     if (rc != SDDM_OK) return rc;
     if (d->method == SDDM_METHOD_MEGAKERNEL && d->bsdf_mode != SDDM_BSDF_EXACT)
@@ -983,6 +985,9 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: needs nee = 1 and max_depth >= 2");
     if (!(radius > 0.0f) || !std::isfinite(radius))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: radius must be positive and finite");
+    if (!(caustic_radius >= 0.0f) || !std::isfinite(caustic_radius))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: caustic_radius must be finite and >= 0");
+    const bool two_maps = caustic_radius > 0.0f;
     const int64_t per = d->max_depth - 1;
     if (n_photons < 0 || n_photons > ((int64_t)1 << 31) / per - 1)
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: n_photons * (max_depth - 1) must stay below 2^31");
@@ -992,23 +997,28 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
     const int64_t slots = n_photons * per;
     std::vector<float> state(M);
     for (int m = 0; m < M; ++m) state[m] = material_state(ctx, *d, m);
-    // grid over the scene box, cells of side >= radius, at most ~2^24 cells
+    // grids over the scene box, cells of side >= the map's radius, at most ~2^24 cells
     const DDMScene &g = ctx->ddm;
-    PhotonGridView v{};
-    double ext[3], vol = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        ext[a] = std::max<double>(g.hi[a] - g.lo[a], 1e-6);
-        vol *= ext[a];
-    }
-    const double cell = std::max<double>(radius, std::cbrt(vol / (double)(1 << 24)) * 1.01);
-    int64_t cells = 1;
-    for (int a = 0; a < 3; ++a) {
-        v.lo[a] = g.lo[a];
-        v.dims[a] = (int)std::floor(ext[a] / cell) + 1;
-        cells *= v.dims[a];
-    }
-    v.cell = (float)cell;
-    v.radius = radius;
+    auto grid_for = [&](float r, PhotonGridView &v) {
+        double ext[3], vol = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            ext[a] = std::max<double>(g.hi[a] - g.lo[a], 1e-6);
+            vol *= ext[a];
+        }
+        const double cell = std::max<double>(r, std::cbrt(vol / (double)(1 << 24)) * 1.01);
+        int64_t n = 1;
+        for (int a = 0; a < 3; ++a) {
+            v.lo[a] = g.lo[a];
+            v.dims[a] = (int)std::floor(ext[a] / cell) + 1;
+            n *= v.dims[a];
+        }
+        v.cell = (float)cell;
+        v.radius = r;
+        return n;
+    };
+    PhotonGridView v{}, vc{};
+    const int64_t cells = grid_for(radius, v);
+    const int64_t cells_c = two_maps ? grid_for(caustic_radius, vc) : 1;
     const size_t sl = (size_t)std::max<int64_t>(slots, 1);
     cudaStream_t s = ctx->stream;
     if ((e = ctx->pm_state.upload(state, s)) ||
@@ -1018,7 +1028,12 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
         (e = ctx->pm_start.ensure(sizeof(int) * (size_t)(cells + 1))) ||
         (e = ctx->pm_fill.ensure(sizeof(int) * (size_t)cells)) || (e = ctx->pm_order.ensure(sizeof(int) * sl)) ||
         (e = ctx->pm_sums.ensure(sizeof(int) * (size_t)(cells / 1024 + 1))) ||
-        (e = ctx->pm_cntr.ensure(16 * sizeof(unsigned long long))))
+        (e = ctx->pm_cntr.ensure(16 * sizeof(unsigned long long))) ||
+        (two_maps && ((e = ctx->pmc_cnt.ensure(sizeof(int) * (size_t)cells_c)) ||
+                      (e = ctx->pmc_start.ensure(sizeof(int) * (size_t)(cells_c + 1))) ||
+                      (e = ctx->pmc_fill.ensure(sizeof(int) * (size_t)cells_c)) ||
+                      (e = ctx->pmc_order.ensure(sizeof(int) * sl)) ||
+                      (e = ctx->pmc_sums.ensure(sizeof(int) * (size_t)(cells_c / 1024 + 1))))))
         return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render_photon_map: device allocation failed")
                                               : cuda_fail(e, "sddm_render_photon_map: scratch");
     if ((e = cudaEventRecord(ctx->ev0, s)) || (e = cudaMemsetAsync(ctx->pm_pos.p, 0, sizeof(float4) * sl, s)) ||
@@ -1072,15 +1087,30 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
     v.pow = ctx->pm_pow.as<float>();
     v.cell_start = ctx->pm_start.as<int>();
     v.order = ctx->pm_order.as<int>();
-    if ((e = build_photon_grid(v, slots, ctx->pm_cnt.as<int>(), ctx->pm_start.as<int>(), ctx->pm_fill.as<int>(),
-                               ctx->pm_order.as<int>(), ctx->pm_sums.as<int>(), cntr + 1, s)) != cudaSuccess)
+    // one map of every stored photon, or the global photons (kind 1) and the caustic ones (kind 2) apart
+    if ((e = build_photon_grid(v, slots, two_maps ? 1 : 0, ctx->pm_cnt.as<int>(), ctx->pm_start.as<int>(),
+                               ctx->pm_fill.as<int>(), ctx->pm_order.as<int>(), ctx->pm_sums.as<int>(), cntr + 1, s)) !=
+        cudaSuccess)
         return cuda_fail(e, "sddm_render_photon_map: grid build");
     launches += slots > 0 ? 5 : 3;
+    if (two_maps) {
+        vc.pos = v.pos;
+        vc.dir = v.dir;
+        vc.pow = v.pow;
+        vc.cell_start = ctx->pmc_start.as<int>();
+        vc.order = ctx->pmc_order.as<int>();
+        if ((e = build_photon_grid(vc, slots, 2, ctx->pmc_cnt.as<int>(), ctx->pmc_start.as<int>(),
+                                   ctx->pmc_fill.as<int>(), ctx->pmc_order.as<int>(), ctx->pmc_sums.as<int>(),
+                                   cntr + 11, s)) != cudaSuccess)
+            return cuda_fail(e, "sddm_render_photon_map: caustic grid build");
+        launches += slots > 0 ? 5 : 3;
+    }
     unsigned long long hc[16];
     if ((e = cudaEventRecord(ctx->ev1, s)) ||
         (e = cudaMemcpyAsync(hc, cntr, sizeof(hc), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "sddm_render_photon_map: photon pass");
-    // counters: [0] megakernel photon segments, [1] stored, [2..9] DDM pass (segments at 2), int error word at [10]
+    // counters: [0] megakernel photon segments, [1] stored (global), [2..9] DDM pass (segments at 2), int error
+    // word at [10], [11] stored caustic
     int perr;
     std::memcpy(&perr, hc + 10, sizeof perr);
     if (perr != 0) {
@@ -1091,15 +1121,19 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
     float pms = 0.f;
     cudaEventElapsedTime(&pms, ctx->ev0, ctx->ev1);
     v.on = 1;
+    vc.on = two_maps ? 1 : 0;
     ctx->pm_view = v;
+    ctx->pmc_view = vc;
     rc = sddm_render(ctx, d, 1, st);
     ctx->pm_view = PhotonGridView{};
+    ctx->pmc_view = PhotonGridView{};
     if (rc != SDDM_OK) return rc;
     if (pst) {
         pst->photons = n_photons;
         pst->photon_segments = (int64_t)(hc[0] + hc[2]);
         pst->stored = (int64_t)hc[1];
-        pst->grid_cells = cells;
+        pst->stored_caustic = two_maps ? (int64_t)hc[11] : 0;
+        pst->grid_cells = cells + (two_maps ? cells_c : 0);
         pst->photon_ms = pms;
         pst->kernel_launches = launches;
     }

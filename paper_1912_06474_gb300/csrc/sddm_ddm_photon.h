@@ -29,7 +29,9 @@ struct DDMPhotonRun {
 
 // Trace one chunk of photons through the subdomain queues and store them.
 int ddm_photon_pass(const DDMPhotonRun &run, DDMBuffers &buf, cudaStream_t stream);
-// ddm_trace_chunk with a photon map gathered at each path's first diffuse vertex.
-int ddm_trace_chunk_pm(const DDMRun &run, const PhotonGridView &pm, DDMBuffers &buf, cudaStream_t stream);
+// ddm_trace_chunk with a photon map (and optionally a caustic map, pmc.on)
+// gathered at each path's first diffuse vertex.
+int ddm_trace_chunk_pm(const DDMRun &run, const PhotonGridView &pm, const PhotonGridView &pmc, DDMBuffers &buf,
+                       cudaStream_t stream);
 
 }  // namespace sddm

@@ -162,6 +162,7 @@ struct MegaArgs {
     int *error_flag;
     int count_traversal;
     PhotonGridView pm = {};            // photon map gathered at the first diffuse vertex (pm.on)
+    PhotonGridView pmc = {};           // caustic map gathered there too (pmc.on)
 };
 cudaError_t launch_megakernel(const MegaArgs &a, cudaStream_t stream);
 

@@ -19,9 +19,10 @@ struct PhotonTraceArgs {
     unsigned long long *segments;
 };
 cudaError_t launch_photon_trace(const DevScene &sc, const PhotonTraceArgs &a, cudaStream_t stream);
-// Sort the stored slots into the grid g (dims, lo, cell set by the caller);
-// fills g.cell_start / g.order from the given buffers ([cells + 1], [slots]).
-cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int *cnt, int *start, int *fill, int *order,
+// Sort the stored slots of one kind (0 any, 1 global, 2 caustic: pos.w) into
+// the grid g (dims, lo, cell set by the caller) from the given buffers
+// ([cells] counts and cursors, [cells + 1] starts, [slots] order).
+cudaError_t build_photon_grid(PhotonGridView &g, int64_t slots, int kind, int *cnt, int *start, int *fill, int *order,
                               int *scan_sums, unsigned long long *stored, cudaStream_t stream);
 
 }  // namespace sddm

@@ -85,7 +85,8 @@ class Stats(C.Structure):
 
 class PhotonStats(C.Structure):
     _fields_ = [("photons", C.c_int64), ("photon_segments", C.c_int64), ("stored", C.c_int64),
-                ("grid_cells", C.c_int64), ("photon_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("grid_cells", C.c_int64), ("photon_ms", C.c_double), ("kernel_launches", C.c_int64),
+                ("stored_caustic", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,7 +120,7 @@ def _load():
         "sddm_philox": ([P, I, P, C.c_uint32, C.c_uint32, P], I),
         "sddm_set_profiling": ([P, I], I),
         "sddm_render_noalloc": ([P, C.POINTER(RenderDesc), C.POINTER(Stats)], I),
-        "sddm_render_photon_map": ([P, C.POINTER(RenderDesc), C.c_int64, C.c_float, C.POINTER(Stats),
+        "sddm_render_photon_map": ([P, C.POINTER(RenderDesc), C.c_int64, C.c_float, C.c_float, C.POINTER(Stats),
                                     C.POINTER(PhotonStats)], I),
         "sddm_mlp_train": ([P, C.c_uint32, C.POINTER(MlpTrainOpts), C.POINTER(MlpReport)], I),
         "sddm_mlp_get_weights": ([P, C.c_uint32, P], I),
@@ -297,16 +298,18 @@ class Context:
         self.last_stats = st.as_dict()
         return self.last_stats
 
-    def render_photon_map(self, spec, n_photons, radius, method="ddm", bsdf="exact"):
+    def render_photon_map(self, spec, n_photons, radius, method="ddm", bsdf="exact", caustic_radius=0.0):
         """sddm_render_photon_map: photon pass of n_photons from the lights, then
         the camera pass gathering the map within ``radius`` at the first diffuse
-        vertex, both by ``method``. Returns (image [H,W,3] CUDA float32, stats,
-        photon stats)."""
+        vertex, both by ``method``; with ``caustic_radius`` > 0 the caustic
+        photons form a second map gathered within it. Returns (image [H,W,3]
+        CUDA float32, stats, photon stats)."""
         import torch
         img = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=torch.device("cuda", self.device))
         arr, _keep = self._descs([spec], method, bsdf, [img.data_ptr()], None, None)
         st, pst = Stats(), PhotonStats()
-        _check(lib.sddm_render_photon_map(self._h, arr, int(n_photons), float(radius), C.byref(st), C.byref(pst)))
+        _check(lib.sddm_render_photon_map(self._h, arr, int(n_photons), float(radius), float(caustic_radius),
+                                          C.byref(st), C.byref(pst)))
         self.last_stats = st.as_dict()
         return img, self.last_stats, pst.as_dict()
 

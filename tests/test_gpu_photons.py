@@ -118,6 +118,9 @@ def test_photon_map_argument_checks(sddm):
                            (scenes.RenderSpec(8, 8, 1, 64, camera=sc.camera), 1 << 26, 0.1)]:
             with pytest.raises(sddm.SddmError):
                 ctx.render_photon_map(spec, n, r)
+        for rc in (-0.1, float("inf")):
+            with pytest.raises(sddm.SddmError):
+                ctx.render_photon_map(scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 100, 0.1, caustic_radius=rc)
         # the context still renders afterwards
         img, st, pst = ctx.render_photon_map(scenes.RenderSpec(8, 8, 1, 4, camera=sc.camera), 1000, 0.1)
         assert pst["photons"] == 1000 and np.isfinite(img.cpu().numpy()).all()
@@ -177,3 +180,30 @@ def test_coated_room_photon_map(oracle_mod, sddm, method, grid):
     err = rel_rmse(img, ref)
     print(f"  coated room image rel-RMSE vs oracle {err:.2e}")
     assert err <= 1e-3
+
+
+@pytest.mark.parametrize("method,grid", [("megakernel", (1, 1, 1)), ("ddm", (2, 2, 2))])
+def test_global_and_caustic_maps(oracle_mod, sddm, method, grid):
+    """Two maps: global photons gathered within 0.15 m, caustic photons (turned
+    only by reflections) within 0.05 m; against the oracle's two maps."""
+    sc = scenes.tiny_room(L=16)
+    glass = {m: 0.3 for m in sc.glass_materials()}
+    spec = scenes.RenderSpec(64, 48, 4, 5, seed=11, camera=sc.camera, glass_s=glass, nee=True)
+    n, rg, rc = 200000, 0.15, 0.05
+    orc = oracle_mod.Oracle(sc)
+    pg, pc = orc.photon_map(spec, n, rg, kind="global"), orc.photon_map(spec, n, rc, kind="caustic")
+    ref = orc.render_pixels(spec, photon_map=pg, caustic_map=pc)["xyz"].reshape(48, 64, 3)
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        ctx.build(grid=grid)
+        img, st, pst = ctx.render_photon_map(spec, n, rg, method=method, caustic_radius=rc)
+        img = img.cpu().numpy()
+    finally:
+        ctx.close()
+    ng, nc = len(pg.photons()[0]), len(pc.photons()[0])
+    print(f"\n  {method}: global {pst['stored']} (oracle {ng}), caustic {pst['stored_caustic']} (oracle {nc}), "
+          f"rel-RMSE {rel_rmse(img, ref):.2e}")
+    assert nc > 0
+    assert abs(pst["stored"] - ng) <= 1e-3 * n and abs(pst["stored_caustic"] - nc) <= 1e-3 * n
+    assert rel_rmse(img, ref) <= 1e-3
