@@ -273,6 +273,21 @@ typedef struct {
 int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_photons, float radius,
                            float caustic_radius, sddm_stats *st, sddm_photon_stats *pst);
 
+/* Progressive photon mapping (Sec. 4 names photon mapping; the progressive
+ * form is the probabilistic one of Knaus and Zwicker, 2011): n_passes
+ * independent photon-mapping renders, pass j (1-based) with render id
+ * d->render_id + j - 1 (new photons and camera samples) and gather radii
+ * shrinking as r_{j+1}^2 = r_j^2 (j + alpha) / (j + 1) from r_1 = radius (and
+ * caustic_radius, 0 = one map), averaged into d->xyz_out (DEVICE). With
+ * 0 < alpha < 1 the radii go to zero slowly enough that the averaged estimate
+ * converges; alpha = 1 keeps them constant. Same requirements as
+ * sddm_render_photon_map, plus n_passes >= 1 and 0 < alpha <= 1 (else
+ * SDDM_ERR_INVALID_ARG). Statistics are sums over the passes (grid_cells: the
+ * last pass). Synchronous. */
+int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int n_passes, int64_t n_photons,
+                                       float radius, float caustic_radius, float alpha, sddm_stats *st,
+                                       sddm_photon_stats *pst);
+
 /* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}), the
  * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per
  * chunk ({2^21, 2^22, 2^23}; the ray queues are sized from it, two rays per

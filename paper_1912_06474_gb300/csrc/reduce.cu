@@ -97,6 +97,19 @@ cudaError_t launch_rgb_to_spectrum(int n, int L, const float *Q, const float *rg
     return cudaGetLastError();
 }
 
+// Running mean of images: out = a out + b in, elementwise (a = (j - 1) / j,
+// b = 1 / j for the j-th image).
+__global__ void k_blend(int64_t n, float a, float b, const float *in, float *out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = fmaf(a, out[t], b * in[t]);
+}
+
+cudaError_t launch_blend(int64_t n, float a, float b, const float *in, float *out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    k_blend<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(n, a, b, in, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_glass_eval(const DevScene &sc, uint32_t mat, int n, const float *cos_t, const int32_t *bin,
                               const float *s, const float *thick, float *R, float *T, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;

@@ -141,6 +141,7 @@ struct sddm_ctx {
     // megakernel reads while pm_view.on
     DevBuf pm_state, pm_scratch, pm_pos, pm_dir, pm_pow, pm_cnt, pm_start, pm_fill, pm_order, pm_sums, pm_cntr;
     DevBuf pmc_cnt, pmc_start, pmc_fill, pmc_order, pmc_sums;   // the caustic map's grid
+    DevBuf pm_img;                                               // one pass of a progressive render
     PhotonGridView pm_view{}, pmc_view{};
     DDMBuffers pm_ddm_buf;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1137,6 +1138,63 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
         pst->photon_ms = pms;
         pst->kernel_launches = launches;
     }
+    return SDDM_OK;
+}
+
+int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int n_passes, int64_t n_photons,
+                                       float radius, float caustic_radius, float alpha, sddm_stats *st,
+                                       sddm_photon_stats *pst) {
+    int rc = validate_desc(ctx, d, 1);
+    if (rc != SDDM_OK) return rc;
+    if (n_passes < 1 || !(alpha > 0.0f && alpha <= 1.0f))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_progressive_photon_map: needs n_passes >= 1 and 0 < alpha <= 1");
+    if (!d->xyz_out) return fail(SDDM_ERR_INVALID_ARG, "sddm_render_progressive_photon_map: xyz_out is NULL");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "sddm_render_progressive_photon_map: cudaSetDevice");
+    const int64_t nv = (int64_t)d->width * d->height * 3;
+    if ((e = ctx->pm_img.ensure(sizeof(float) * (size_t)nv)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SDDM_ERR_OOM, "sddm_render_progressive_photon_map: allocation failed")
+                                              : cuda_fail(e, "sddm_render_progressive_photon_map: scratch");
+    sddm_stats tot{};
+    sddm_photon_stats ptot{};
+    double r2 = (double)radius * radius, rc2 = (double)caustic_radius * caustic_radius;
+    for (int j = 1; j <= n_passes; ++j) {
+        sddm_render_desc dj = *d;
+        dj.render_id = d->render_id + (uint32_t)(j - 1);   // independent photons and camera samples per pass
+        dj.xyz_out = j == 1 ? d->xyz_out : ctx->pm_img.as<float>();
+        dj.aov_sample_xyz = nullptr;
+        dj.aov_first_prim = nullptr;
+        sddm_stats sj{};
+        sddm_photon_stats pj{};
+        rc = sddm_render_photon_map(ctx, &dj, n_photons, (float)std::sqrt(r2), (float)std::sqrt(rc2), &sj, &pj);
+        if (rc != SDDM_OK) return rc;
+        if (j > 1) {
+            if ((e = launch_blend(nv, (float)(j - 1) / (float)j, 1.0f / (float)j, ctx->pm_img.as<float>(), d->xyz_out,
+                                  ctx->stream)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+                return cuda_fail(e, "sddm_render_progressive_photon_map: blend");
+        }
+        tot.paths += sj.paths;
+        tot.segments_ext += sj.segments_ext;
+        tot.segments_shadow += sj.segments_shadow;
+        tot.crossings += sj.crossings;
+        tot.glass_queries += sj.glass_queries;
+        tot.mlp_fallbacks += sj.mlp_fallbacks;
+        tot.gpu_ms += sj.gpu_ms;
+        tot.kernel_launches += sj.kernel_launches + (j > 1 ? 1 : 0);
+        ptot.photons += pj.photons;
+        ptot.photon_segments += pj.photon_segments;
+        ptot.stored += pj.stored;
+        ptot.stored_caustic += pj.stored_caustic;
+        ptot.grid_cells = pj.grid_cells;
+        ptot.photon_ms += pj.photon_ms;
+        ptot.kernel_launches += pj.kernel_launches;
+        // radius of the next pass: r^2 (j + alpha) / (j + 1)
+        r2 *= ((double)j + alpha) / ((double)j + 1.0);
+        rc2 *= ((double)j + alpha) / ((double)j + 1.0);
+    }
+    if (st) *st = tot;
+    if (pst) *pst = ptot;
     return SDDM_OK;
 }
 

@@ -180,6 +180,7 @@ cudaError_t launch_reduce_pixels(const ReduceArgs &a, int64_t pixel_begin, int64
 
 cudaError_t launch_philox(int n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                           cudaStream_t stream);
+cudaError_t launch_blend(int64_t n, float a, float b, const float *in, float *out, cudaStream_t stream);
 cudaError_t launch_rgb_to_spectrum(int n, int L, const float *Q, const float *rgb, float *out, int clamp01,
                                    cudaStream_t stream);
 cudaError_t launch_glass_eval(const DevScene &sc, uint32_t mat, int n, const float *cos_t, const int32_t *bin,

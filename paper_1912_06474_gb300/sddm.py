@@ -28,6 +28,7 @@ BSDFS = {"exact": BSDF_EXACT, "mlp": BSDF_MLP, "mlp_raw": BSDF_MLP_RAW}
 EXPORTED = ["sddm_create", "sddm_destroy", "sddm_last_error", "sddm_version", "sddm_set_spectrum",
             "sddm_add_lambertian", "sddm_add_conductor", "sddm_add_glass_slab", "sddm_add_coated_glass",
             "sddm_rgb_to_spectrum", "sddm_render_photon_map",
+            "sddm_render_progressive_photon_map",
             "sddm_add_emitter",
             "sddm_add_diffuse_emitter", "sddm_set_mesh", "sddm_build", "sddm_render", "sddm_render_host",
             "sddm_autotune", "sddm_glass_eval", "sddm_philox", "sddm_set_profiling",
@@ -122,6 +123,8 @@ def _load():
         "sddm_render_noalloc": ([P, C.POINTER(RenderDesc), C.POINTER(Stats)], I),
         "sddm_render_photon_map": ([P, C.POINTER(RenderDesc), C.c_int64, C.c_float, C.c_float, C.POINTER(Stats),
                                     C.POINTER(PhotonStats)], I),
+        "sddm_render_progressive_photon_map": ([P, C.POINTER(RenderDesc), I, C.c_int64, C.c_float, C.c_float,
+                                                C.c_float, C.POINTER(Stats), C.POINTER(PhotonStats)], I),
         "sddm_mlp_train": ([P, C.c_uint32, C.POINTER(MlpTrainOpts), C.POINTER(MlpReport)], I),
         "sddm_mlp_get_weights": ([P, C.c_uint32, P], I),
         "sddm_mlp_set_weights": ([P, C.c_uint32, P, C.c_float, C.c_float], I),
@@ -310,6 +313,21 @@ class Context:
         st, pst = Stats(), PhotonStats()
         _check(lib.sddm_render_photon_map(self._h, arr, int(n_photons), float(radius), float(caustic_radius),
                                           C.byref(st), C.byref(pst)))
+        self.last_stats = st.as_dict()
+        return img, self.last_stats, pst.as_dict()
+
+    def render_progressive_photon_map(self, spec, n_passes, n_photons, radius, alpha=0.7, method="ddm",
+                                      bsdf="exact", caustic_radius=0.0):
+        """sddm_render_progressive_photon_map: the mean of n_passes photon-mapping
+        renders (render ids spec.render_id + j - 1) with gather radii shrinking
+        by (j + alpha) / (j + 1) in area per pass. Returns (image, stats, photon stats)."""
+        import torch
+        img = torch.empty((spec.height, spec.width, 3), dtype=torch.float32, device=torch.device("cuda", self.device))
+        arr, _keep = self._descs([spec], method, bsdf, [img.data_ptr()], None, None)
+        st, pst = Stats(), PhotonStats()
+        _check(lib.sddm_render_progressive_photon_map(self._h, arr, int(n_passes), int(n_photons), float(radius),
+                                                      float(caustic_radius), float(alpha), C.byref(st),
+                                                      C.byref(pst)))
         self.last_stats = st.as_dict()
         return img, self.last_stats, pst.as_dict()
 

@@ -207,3 +207,37 @@ def test_global_and_caustic_maps(oracle_mod, sddm, method, grid):
     assert nc > 0
     assert abs(pst["stored"] - ng) <= 1e-3 * n and abs(pst["stored_caustic"] - nc) <= 1e-3 * n
     assert rel_rmse(img, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("method,grid", [("megakernel", (1, 1, 1)), ("ddm", (2, 2, 2))])
+def test_progressive_photon_map(oracle_mod, sddm, method, grid):
+    """Progressive photon mapping: the mean of passes j = 1..3 with render ids
+    id + j - 1 and squared radii shrinking by (j + alpha) / (j + 1), against the
+    oracle renders of the same passes averaged here."""
+    import dataclasses
+    sc = scenes.tiny_room(L=16)
+    spec = scenes.RenderSpec(48, 32, 2, 5, seed=13, render_id=5, camera=sc.camera, nee=True)
+    n, r, rc, alpha, passes = 50000, 0.2, 0.08, 0.7, 3
+    orc = oracle_mod.Oracle(sc)
+    ref, r2, rc2 = None, r * r, rc * rc
+    for j in range(1, passes + 1):
+        sj = dataclasses.replace(spec, render_id=spec.render_id + j - 1)
+        pg = orc.photon_map(sj, n, float(np.float32(np.sqrt(r2))), kind="global")
+        pc = orc.photon_map(sj, n, float(np.float32(np.sqrt(rc2))), kind="caustic")
+        img = orc.render_pixels(sj, photon_map=pg, caustic_map=pc)["xyz"].reshape(32, 48, 3)
+        ref = img if ref is None else ref + (img - ref) / j
+        r2 *= (j + alpha) / (j + 1)
+        rc2 *= (j + alpha) / (j + 1)
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        ctx.build(grid=grid)
+        img, st, pst = ctx.render_progressive_photon_map(spec, passes, n, r, alpha=alpha, method=method,
+                                                          caustic_radius=rc)
+        img = img.cpu().numpy()
+    finally:
+        ctx.close()
+    err = rel_rmse(img, ref)
+    print(f"\n  progressive {method}: {passes} passes, {pst['photons']} photons, rel-RMSE {err:.2e}")
+    assert pst["photons"] == passes * n
+    assert err <= 1e-3
