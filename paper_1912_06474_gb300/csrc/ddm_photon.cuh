@@ -81,6 +81,14 @@ __global__ void __launch_bounds__(256) k_photon_emit(KArgs a, PhotonPass pp) {
     block_count3(a.counters + 0, n_ext, nullptr, 0, nullptr, 0);
 }
 
+// Power rows of the photons a warp stores are written row by row by the whole
+// warp (coalesced) through a [L][33] shared-memory tile per warp, for L up to
+// kStageMaxL; one lane per row otherwise.
+constexpr int kStageMaxL = 64;
+__host__ __device__ constexpr size_t photon_stage_bytes(int L) {
+    return L <= kStageMaxL ? (size_t)8 * L * 33 * sizeof(float) : 0;
+}
+
 template <bool FILMS>
 __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
     const int64_t np = a.ps.np;
@@ -90,6 +98,9 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
     unsigned long long n_ext = 0;
     __shared__ PushSmem psm;
     int *bins = block_bins_init(a.g.n_bins);
+    const bool staged = L <= kStageMaxL;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float *stage = reinterpret_cast<float *>(bins + ((a.g.n_bins + 3) & ~3)) + (size_t)w * L * 33;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += stride) {   // block-uniform trips
         const int64_t q = base + threadIdx.x;
         bool want = false;
@@ -97,6 +108,28 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
         float4 e0 = make_float4(0, 0, 0, 0), e1 = e0;
         int4 e2 = make_int4(0, 0, 0, 0);
         const int fl = q < np ? a.ps.flags[q] : 0;
+        if (staged) {
+            bool store = false;
+            if ((fl & kFlExt) && (fl & kFlPhotonTurned)) {
+                const int prim = __float_as_int(a.ps.hit0[q].w);
+                if (prim >= 0) {
+                    const int kind = __ldg(sc.mat_kind + __float_as_int(__ldg(sc.tri_n + prim).w));
+                    store = kind == kLambert || kind == kDiffuseEmitter;
+                }
+            }
+            const unsigned sm = __ballot_sync(0xffffffffu, store);
+            if (sm) {
+                if (store)
+                    for (int i = 0; i < L; ++i) stage[i * 33 + lane] = a.ps.T[(size_t)i * np + q];
+                __syncwarp();
+                for (unsigned m = sm; m; m &= m - 1) {
+                    const int src = __ffs(m) - 1;
+                    const size_t slot = (size_t)(pp.begin + base + 32 * w + src) * (D - 1) + (b - 1);
+                    for (int i = lane; i < L; i += 32) pp.pow[slot * L + i] = stage[i * 33 + src];
+                }
+                __syncwarp();
+            }
+        }
         if (fl & kFlExt) {
             int nfl = 0;
             const float4 h0 = a.ps.hit0[q], h1 = a.ps.hit1[q];
@@ -118,8 +151,10 @@ __global__ void __launch_bounds__(256) k_photon_shade(KArgs a, PhotonPass pp) {
                         // w: 1 global photon, 2 caustic photon (only reflections turned it)
                         pp.pos[slot] = make_float4(x.x, x.y, x.z, (fl & kFlPhotonDiffuse) ? 1.0f : 2.0f);
                         pp.dir[slot] = make_float4(d.x, d.y, d.z, 0.0f);
-                        float *pw = pp.pow + slot * L;
-                        for (int i = 0; i < L; ++i) pw[i] = a.ps.T[(size_t)i * np + q];
+                        if (!staged) {
+                            float *pw = pp.pow + slot * L;
+                            for (int i = 0; i < L; ++i) pw[i] = a.ps.T[(size_t)i * np + q];
+                        }
                     }
                     if (b < D - 1) {
                         const float *rho = kind == kLambert ? mA : mB;
@@ -337,10 +372,16 @@ int ddm_photon_pass(const DDMPhotonRun &run, DDMBuffers &buf, cudaStream_t s) {
             *run.launches += 2;
         }
         a.b = b;
-        if (run.sc.mat_nfilm)
-            k_photon_shade<true><<<path_blocks, 256, bins_smem, s>>>(a, pp);
-        else
-            k_photon_shade<false><<<path_blocks, 256, bins_smem, s>>>(a, pp);
+        const size_t shade_smem = sizeof(int) * (size_t)((nb + 3) & ~3) + photon_stage_bytes(L);
+        if (run.sc.mat_nfilm) {
+            PM_CHECK(cudaFuncSetAttribute(k_photon_shade<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shade_smem));
+            k_photon_shade<true><<<path_blocks, 256, shade_smem, s>>>(a, pp);
+        } else {
+            PM_CHECK(cudaFuncSetAttribute(k_photon_shade<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shade_smem));
+            k_photon_shade<false><<<path_blocks, 256, shade_smem, s>>>(a, pp);
+        }
         PM_CHECK(cudaGetLastError());
         *run.launches += 1;
     }
