@@ -1008,7 +1008,8 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
             k_shade_spectral<false><<<path_blocks, 256, 0, s>>>(a);
         DDM_CHECK(cudaGetLastError());
         if (a.pm.on) {
-            k_ddm_gather<<<path_blocks, 256, 0, s>>>(a);
+            // one path slot per thread: the gather is latency-bound and gains from the most blocks in flight
+            k_ddm_gather<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
             *run.launches += 1;
         }
