@@ -160,24 +160,7 @@ __global__ void __launch_bounds__(128) k_megakernel(MegaArgs a) {
                 }
             }
             if constexpr (PM) {
-                Spectrum<LT> S;
-                for_bins<LT>(L, [&](int i) { S.v[i] = 0.0f; });
-                pm_gather_visit(a.pm, xh, ns, [&](int slot) {
-                    const float *pw = a.pm.pow + (size_t)slot * L;
-                    for_bins<LT>(L, [&](int i) { S.v[i] += __ldg(pw + i); });
-                });
-                // rho / pi times the power over pi r^2 of each map (global, caustic)
-                const float inv_g = 1.0f / (3.14159265358979f * a.pm.radius * a.pm.radius);
-                for_bins<LT>(L, [&](int i) { S.v[i] *= inv_g; });
-                if (a.pmc.on) {
-                    const float inv_c = 1.0f / (3.14159265358979f * a.pmc.radius * a.pmc.radius);
-                    pm_gather_visit(a.pmc, xh, ns, [&](int slot) {
-                        const float *pw = a.pmc.pow + (size_t)slot * L;
-                        for_bins<LT>(L, [&](int i) { S.v[i] = fmaf(__ldg(pw + i), inv_c, S.v[i]); });
-                    });
-                }
-                const float norm = 1.0f / 3.14159265358979f;
-                add_xyz<LT>(sc, L, acc, [&](int i) { return T.v[i] * __ldg(rho + i) * S.v[i] * norm; });
+                pm_radiance_xyz(a.pm, a.pmc, xh, ns, L, rho, sc.wcmf, [&](int i) { return T.v[i]; }, acc);
                 break;
             }
             if (b == ri.max_depth) break;

@@ -40,4 +40,55 @@ __device__ __forceinline__ int pm_gather_visit(const PhotonGridView &pm, V3 x, V
     return n;
 }
 
+// Bins summed per walk over the gathered photons: their sums stay in registers.
+constexpr int kPmChunk = 32;
+
+// Photon-map radiance at a diffuse point (the megakernel's camera pass),
+// added to acc as XYZ: per bin i,
+// T(i) rho_i / pi times the power of the global map's photons within its radius
+// over pi r^2, plus the caustic map's (pmc.on) over its own pi r^2. The bins
+// are taken kPmChunk at a time, each chunk with its own walk over the photons,
+// so that the per-bin sums live in registers rather than in a local array.
+template <typename TF>
+__device__ __forceinline__ void pm_radiance_xyz(const PhotonGridView &pm, const PhotonGridView &pmc, V3 x, V3 ns,
+                                                int L, const float *rho, const float4 *wcmf, TF &&Tof, Kahan3 &acc) {
+    const float inv_g = 1.0f / (3.14159265358979f * pm.radius * pm.radius);
+    const float inv_c = pmc.on ? 1.0f / (3.14159265358979f * pmc.radius * pmc.radius) : 0.0f;
+    const float norm = 1.0f / 3.14159265358979f;
+    Kahan X, Y, Z;
+    for (int c0 = 0; c0 < L; c0 += kPmChunk) {
+        const int n = min(kPmChunk, L - c0);
+        float S[kPmChunk];
+#pragma unroll
+        for (int k = 0; k < kPmChunk; ++k) S[k] = 0.0f;
+        pm_gather_visit(pm, x, ns, [&](int slot) {
+            const float *pw = pm.pow + (size_t)slot * L + c0;
+#pragma unroll
+            for (int k = 0; k < kPmChunk; ++k)
+                if (k < n) S[k] += __ldg(pw + k);
+        });
+#pragma unroll
+        for (int k = 0; k < kPmChunk; ++k) S[k] *= inv_g;
+        if (pmc.on)
+            pm_gather_visit(pmc, x, ns, [&](int slot) {
+                const float *pw = pmc.pow + (size_t)slot * L + c0;
+#pragma unroll
+                for (int k = 0; k < kPmChunk; ++k)
+                    if (k < n) S[k] = fmaf(__ldg(pw + k), inv_c, S[k]);
+            });
+#pragma unroll
+        for (int k = 0; k < kPmChunk; ++k) {
+            if (k < n) {
+                const int i = c0 + k;
+                const float e = Tof(i) * __ldg(rho + i) * S[k] * norm;
+                const float4 w4 = __ldg(wcmf + i);
+                X.add(e * w4.x);
+                Y.add(e * w4.y);
+                Z.add(e * w4.z);
+            }
+        }
+    }
+    acc.add(X.s, Y.s, Z.s);
+}
+
 }  // namespace sddm
