@@ -150,13 +150,13 @@ int sddm_set_spectrum(sddm_ctx *ctx, int L, const float *lambda_nm, const float 
  * *mat receives the material id (ids count up from 0 in call order). */
 int sddm_add_lambertian(sddm_ctx *ctx, const float *rho, uint32_t *mat);
 
-/* Metal described by its optical constants n[L] + i k[L] (Eq. 1, Sec. 2:
- * "metallic surfaces ... described by means of optical constants"): a smooth
+/* Metal described by its optical constants n[L] + i k[L] (Eq. 1; Sec. 2
+ * characterises metals by these constants): a smooth
  * mirror weighted by the Fresnel reflectance. n > 0, k >= 0. */
 int sddm_add_conductor(sddm_ctx *ctx, const float *n, const float *k, uint32_t *mat);
 
-/* Glass pane as an absorbing plane-parallel slab (Sec. 2 glass samples,
- * Sec. 6 "the Fresnel definition", photochromic/electrochromic state):
+/* Glass pane as an absorbing plane-parallel slab (Sec. 2 glass samples; Sec. 6
+ * evaluates glass with the Fresnel equations; photochromic/electrochromic state):
  * real index n[L] >= 1, absorption alpha(s) = alpha_clear[L] + s * dalpha[L]
  * in 1/m (k = alpha * lambda / 4 pi), thickness in metres, default state
  * s_default in [0,1]. The slab's triangles must form one closed convex object
@@ -189,13 +189,13 @@ int sddm_add_diffuse_emitter(sddm_ctx *ctx, const float *rho, const float *Le, u
 
 /* Triangle mesh: vertices v[nv][3], triangles tri[nt][3] (vertex indices,
  * counter-clockwise about the outward normal), material mat_id[nt] and
- * object obj_id[nt] per triangle (Sec. 4 "polygons of objects"). nt >= 1,
+ * object obj_id[nt] per triangle (Sec. 4: objects are made of polygons). nt >= 1,
  * at most 2^26 triangles. Invalidates a previous build. */
 int sddm_set_mesh(sddm_ctx *ctx, const float *v, int nv, const uint32_t *tri, int nt,
                   const uint32_t *mat_id, const uint32_t *obj_id);
 
-/* Build the acceleration structures on the host and upload them (Sec. 5:
- * "splitting a global domain into several small sub-domains"): a global
+/* Build the acceleration structures on the host and upload them (Sec. 5: the
+ * scene domain is cut into small subdomains): a global
  * binned-SAH BVH for the megakernel and, for grid != {1,1,1}, a grid of
  * subdomains each with its own BVH over the triangles that overlap it
  * (duplicated by reference, node boxes clipped to the subdomain). o may be
@@ -299,7 +299,7 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
 
 /* ------------------------------------------------- learned glass surrogate
  * A small network stands in for the exact slab R, T of a glass material (the
- * paper evaluates glass "by the Fresnel definition", Sec. 6): inputs
+ * paper evaluates glass with the Fresnel equations, Sec. 6): inputs
  * (cos theta, lambda, s, thickness), each mapped to [-1, 1]: 2 cos - 1,
  * (lambda - 380)/200 - 1, 2 s - 1, and the thickness d through the normal-
  * incidence internal transmittance 2 exp(-alpha(lambda, s) d) - 1 with the
@@ -364,7 +364,7 @@ int sddm_set_profiling(sddm_ctx *ctx, int flags);
 
 /* ---------------------------------------------------------- test hooks */
 
-/* Glass slab R and T (Sec. 6 "Fresnel definition") for n queries of glass
+/* Glass slab R and T (Sec. 6, Fresnel equations) for n queries of glass
  * material `mat`: cos_theta[n] in [0,1], bin index bin[n] in [0,L), state
  * s[n], thickness_m[n]. All four inputs and R[n], T[n] are DEVICE arrays.
  * mode = sddm_bsdf_mode. */

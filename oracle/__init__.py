@@ -7,7 +7,7 @@ no code with the CUDA path: the two meet only in the seeded scene arrays.
 
 What each C function follows in the paper (arXiv:1912.06474):
   optics.c  -- Eq. 1 complex index, Fresnel for metals (Sec. 2) and the glass
-               slab "Fresnel definition" (Sec. 6) with multiple reflections.
+               slab from the Fresnel equations (Sec. 6) with multiple reflections.
   geom.c    -- ray/object interactions (Sec. 4-5): Moller-Trumbore, closest
                hit, shadow query through glass; brute force or median-split BVH.
   render.c  -- Eq. 2 by path tracing with Eq. 3's light sum as next-event

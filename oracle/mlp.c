@@ -2,8 +2,8 @@
  * FP64 reference of the glass-slab surrogate network -- TEST INFRASTRUCTURE ONLY
  * (see sddm_oracle.h).
  *
- * The network stands in for the exact absorbing-slab R, T of Sec. 6 ("the
- * Fresnel definition" of the glass) as a function of (cos theta, lambda, s,
+ * The network stands in for the exact absorbing-slab R, T of Sec. 6 (glass
+ * from the Fresnel equations) as a function of (cos theta, lambda, s,
  * thickness): 4 inputs -> 64 -> 64 -> 64 SiLU units -> 2 outputs (R, T).
  * Inputs are mapped to [-1, 1]:
  *   x0 = 2 cos - 1, x1 = 2 (lambda - 380) / 400 - 1, x2 = 2 s - 1,

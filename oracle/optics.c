@@ -4,7 +4,7 @@
  * TEST INFRASTRUCTURE ONLY (see sddm_oracle.h).
  *
  * Eq. 1 gives the complex index n~ = n + ik. Sec. 2 describes metals by their
- * optical constants and Sec. 6 evaluates glass "by the Fresnel definition";
+ * optical constants and Sec. 6 evaluates glass with the Fresnel equations;
  * the photochromic/electrochromic state is an absorption change. Fresnel's
  * amplitude coefficients for a wave arriving from vacuum:
  *     cos_t = sqrt(1 - sin^2(theta_i) / n~^2)   (principal root)

@@ -19,8 +19,8 @@
  *     cosine-distributed direction at a Lambertian vertex, the mirror
  *     direction weighted by Fresnel at a metal (Sec. 2, Eq. 1), and at a glass
  *     slab either the mirror direction weighted by R or straight transmission
- *     weighted by T (Sec. 6: "the Fresnel definition");
- *   - it stops after D vertices (the "predetermined number of bounces"), on a
+ *     weighted by T (Sec. 6: glass from the Fresnel equations);
+ *   - it stops after D vertices (the paper's fixed bounce limit), on a
  *     miss or on a black emitter.
  * XYZ = sum_i w_i L(lambda_i) cmf(lambda_i); a pixel is the mean of its spp.
  *

@@ -270,8 +270,8 @@ __device__ __forceinline__ float conductor_F(float c, float n, float k) {
     return 0.5f * (Rs + Rp);
 }
 
-// Absorbing plane-parallel slab (Sec. 6, "the Fresnel definition" of the
-// glass; Eq. 1 with k = alpha lambda / 4 pi): interface reflectance rho_j per
+// Absorbing plane-parallel slab (Sec. 6 evaluates glass with the Fresnel
+// equations; Eq. 1 with k = alpha lambda / 4 pi): interface reflectance rho_j per
 // polarisation, internal transmittance tau = exp(-alpha d / cos_t) with the
 // real-index refraction angle, and the multiple-reflection sums
 //   R_j = rho_j + (1 - rho_j)^2 rho_j tau^2 / (1 - rho_j^2 tau^2)

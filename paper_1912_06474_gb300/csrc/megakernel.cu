@@ -1,5 +1,5 @@
 // Plain baseline: one thread per camera path over the global BVH -- the
-// "classical" parallelisation of Sec. 5 (split the pixels, every worker sees
+// classical parallelisation of Sec. 5 (split the pixels, every worker sees
 // the whole scene) -- computing the same estimator as the DDM path.
 //
 // Per path (pixel p, sample j, render r), following Sec. 4's algorithm and

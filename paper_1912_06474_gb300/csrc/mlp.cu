@@ -1,5 +1,5 @@
 // Learned surrogate of the glass slab's R and T (a stand-in for the exact
-// "Fresnel definition" of the glass, Sec. 6): a 4 -> 64 -> 64 -> 64 -> 2 SiLU
+// Fresnel-equation glass of Sec. 6): a 4 -> 64 -> 64 -> 64 -> 2 SiLU
 // network evaluated and trained with BF16 tensor-core MMAs (m16n8k16, FP32
 // accumulation). The layers are 64 wide, so a warp carries a 16-row tile
 // through the whole network: the accumulator fragments of one layer, after
