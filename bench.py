@@ -129,11 +129,13 @@ def reduce_over_ranks(max_vals, sum_vals, device="cpu"):
     return [float(x) for x in t.tolist()], [int(x) for x in n.tolist()]
 
 
-def workload(method, width=512, height=512, spp=16, bsdf="exact"):
+def workload(method, width=512, height=512, spp=16, bsdf="exact", grid=None):
     from paper_1912_06474_gb300 import scenes
     scene = scenes.hotel_room(L=41, seed=0)
     spec = scenes.hotel_room_render(scene, width, height, spp, 5, seed=0)
-    grid = (4, 4, 2) if method == "ddm" else (1, 1, 1)
+    if grid is None:
+        grid = (4, 4, 2) if method == "ddm" else (1, 1, 1)
+    grid = tuple(int(g) for g in grid)
     cfg = {"workload": f"hotel_room_{width}x{height}_{spp}spp_d5_L41", "triangles": scene.n_tris,
            "width": width, "height": height, "spp": spp, "max_depth": 5, "lambda_bins": 41, "method": method,
            "grid": list(grid), "bsdf": bsdf, "l2": "flushed between steps (256 MiB write)",
@@ -176,7 +178,7 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    _, _, _, cfg = workload("ddm", args.width, args.height, args.spp, args.bsdf)
+    _, _, _, cfg = workload("ddm", args.width, args.height, args.spp, args.bsdf, args.grid)
     vals = []
     base = None
     for k in range(args.warmup + args.steps):
@@ -226,7 +228,7 @@ def run(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    scene, spec, grid, cfg = workload(args.method, args.width, args.height, args.spp, args.bsdf)
+    scene, spec, grid, cfg = workload(args.method, args.width, args.height, args.spp, args.bsdf, args.grid)
     spec.render_id = rank   # independent replicas: each rank renders its own stream of samples
     stream = torch.cuda.current_stream()
     ctx = sddm.Context(local, stream)
@@ -383,6 +385,8 @@ def main():
     ap.add_argument("--width", type=int, default=512)
     ap.add_argument("--height", type=int, default=512)
     ap.add_argument("--spp", type=int, default=16)
+    ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("GX", "GY", "GZ"),
+                    help="subdomain grid of the DDM arm (default 4 4 2, the hotel-room configuration)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
