@@ -501,7 +501,7 @@ void *orc_photon_map_build_kind(void *ctx, const orc_render_desc *r, int64_t n_p
         free(rec); free(pw); free(pm);
         return NULL;
     }
-    orc_pjob jb = {c, r, n_photons, n_photons ? 1.0 / (double)n_photons : 0.0, rec, pw};
+    orc_pjob jb = {c, r, n_photons, n_photons ? 1.0 / (double)n_photons : 0.0, rec, pw, 0};
     atomic_init(&jb.next, 0);
     if (n_threads <= 0) {
         long nc = sysconf(_SC_NPROCESSORS_ONLN);
