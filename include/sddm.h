@@ -138,8 +138,8 @@ const char *sddm_version(void);
 
 /* ---------------------------------------------------------------- scene */
 
-/* Spectral sampling of the rendering model (Sec. 1: "a model including
- * spectral properties"; Sec. 3). L bins (1..256) at lambda_nm[L], quadrature
+/* Spectral sampling of the rendering model (Sec. 1: the model carries
+ * spectral properties; Sec. 3). L bins (1..256) at lambda_nm[L], quadrature
  * weights quad_w[L] (nm), colour matching functions cmf_xyz[L][3]. Resets the
  * material list, which is defined per bin. */
 int sddm_set_spectrum(sddm_ctx *ctx, int L, const float *lambda_nm, const float *quad_w,

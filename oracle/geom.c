@@ -3,8 +3,8 @@
  *
  * TEST INFRASTRUCTURE ONLY (see sddm_oracle.h).
  *
- * Sec. 4 and Sec. 5 of the paper put the cost in "the interactions between
- * light rays and objects": finding the closest surface a ray meets and, for
+ * Sec. 4 and Sec. 5 of the paper place the cost in computing how rays interact
+ * with the objects: finding the closest surface a ray meets and, for
  * the rays shot toward the lights, whether anything lies in between. The
  * oracle answers both by the plain definition:
  *   - Moller-Trumbore intersection, double sided, a hit needs t > 0 and

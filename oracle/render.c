@@ -12,8 +12,8 @@
  *     its radiance (Eq. 2's L_i at that vertex); with next-event estimation
  *     off every emitter hit counts;
  *   - at a Lambertian vertex Eq. 3's light sum is estimated by one shadow ray
- *     toward a point drawn on the area lights (Sec. 4: "rays are shot from the
- *     hit point toward each light source"); the shadow ray passes through
+ *     toward a point drawn on the area lights (Sec. 4 casts a ray from each hit
+ *     point toward every light source); the shadow ray passes through
  *     glass slabs and is weighted by their transmittance;
  *   - the path continues by the reflection/refraction laws (Sec. 4): a
  *     cosine-distributed direction at a Lambertian vertex, the mirror

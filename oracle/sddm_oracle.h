@@ -13,7 +13,7 @@
  *     reflections; coloration state s sets the absorption alpha + s*dalpha.
  *   - Eq. 2 estimated by Monte Carlo path tracing (Sec. 4), Eq. 3's light sum
  *     as next-event estimation toward area lights, shadow rays to the light
- *     (Sec. 4, "Local illumination"), reflection/refraction continuation and a
+ *     (Sec. 4, local illumination), reflection/refraction continuation and a
  *     bounce limit (same passage).
  *   - The domain decomposition of Sec. 5 hands a ray on across interfaces with
  *     its properties unchanged, so its closest hit is that of a single global

@@ -1,6 +1,6 @@
 // Host construction of the acceleration structures.
 //
-// Sec. 5 splits "a global domain into several small sub-domains"; every
+// Sec. 5 cuts the scene domain into small subdomains; every
 // subdomain here gets its own bounding volume hierarchy over the triangles
 // that overlap it (duplicated by reference, bounds clipped to the subdomain),
 // so tracing inside a subdomain touches only that subdomain's data. A grid of

@@ -2,7 +2,7 @@
 //
 // Sec. 5 of the paper parallelises ray tracing by splitting the scene into
 // subdomains; a ray handed across an interface keeps its properties
-// ("direction, amplitude, angle") and the subdomain that receives it carries
+// (its direction, amplitude and angle) and the subdomain that receives it carries
 // on. Each processor works on the subdomains whose rays are waiting, keeping
 // their data loaded (Sec. 5, last paragraph). On one GB300 this becomes:
 //
