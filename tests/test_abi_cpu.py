@@ -31,3 +31,33 @@ def test_binding_has_no_cpu_fallback():
     for f in os.listdir(os.path.join(ROOT, "paper_1912_06474_gb300")):
         if f.endswith(".py"):
             assert "import oracle" not in open(os.path.join(ROOT, "paper_1912_06474_gb300", f)).read(), f
+
+
+def test_every_call_rejects_a_null_context():
+    """Argument checks run before any CUDA call: with a NULL context every entry
+    point returns a negative status and leaves a message (the library never
+    aborts), and sddm_create rejects a NULL output pointer."""
+    import ctypes as C
+    from paper_1912_06474_gb300 import build
+    build.build()
+    from paper_1912_06474_gb300 import sddm
+    lib = sddm.lib
+    skip = {"sddm_last_error", "sddm_version", "sddm_destroy"}
+    for name in sddm.EXPORTED:
+        if name in skip:
+            continue
+        f = getattr(lib, name)
+        args = []
+        for t in f.argtypes:
+            if t in (C.c_int, C.c_int64, C.c_uint32):
+                args.append(0)
+            elif t in (C.c_float, C.c_double):
+                args.append(0.0)
+            elif t is C.c_char_p:
+                args.append(None)
+            else:
+                args.append(None)
+        rc = f(*args)
+        assert rc < 0, name
+        assert lib.sddm_last_error(), name
+    assert lib.sddm_destroy(None) == 0
