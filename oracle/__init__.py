@@ -14,7 +14,7 @@ What each C function follows in the paper (arXiv:1912.06474):
                estimation (Sec. 3-4); spectral XYZ output.
   philox.c  -- the counter-based random stream both sides draw from.
 
-Parity unpinned: the bit-level Philox4x32-10 definition (pinned statistically).
+The random stream is pinned by Philox4x32-10's published known-answer vectors and statistically.
 """
 from __future__ import annotations
 

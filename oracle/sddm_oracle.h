@@ -25,8 +25,8 @@
  * kernel's precision (float, no contraction), and the inputs, which are the
  * caller's float32 arrays widened to double.
  *
- * Parity unpinned: the bit-level Philox4x32-10 definition (no known-answer
- * vectors are available offline; the stream is pinned statistically only).
+ * The random stream is pinned by Philox4x32-10's published known-answer
+ * vectors and statistically (tests/test_oracle_geometry.py).
  */
 #ifndef SDDM_ORACLE_H
 #define SDDM_ORACLE_H

@@ -2,8 +2,9 @@
 
 Independent formulations: plane intersection with area-ratio barycentrics for
 Moller-Trumbore, brute force for the BVH, moments of the cosine law for the
-direction sampler, the pinhole geometry for the camera, and statistics for the
-counter-based stream (its bit-level definition is unpinned).
+direction sampler, the pinhole geometry for the camera, and for the
+counter-based stream the published known-answer vectors of Philox4x32-10 plus
+statistics.
 """
 import math
 
@@ -11,6 +12,18 @@ import numpy as np
 import pytest
 
 from paper_1912_06474_gb300 import scenes
+
+
+def test_philox_known_answers(oracle_mod):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) against the known-answer
+    vectors published with the generator's reference implementation (Random123):
+    counter and key all zeros, all ones, and the digits of pi."""
+    cases = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+             ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+             ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+              (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in cases:
+        assert tuple(int(x) for x in oracle_mod.philox4x32_10(list(ctr), list(key))) == want
 
 
 def test_philox_statistics(oracle_mod):
