@@ -214,17 +214,22 @@ int sddm_render_host(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats
 
 /* Render one image with the plain megakernel without allocating any memory.
  * The paper has no counterpart: this serves callers that cannot call
- * cudaMalloc while rendering -- code inside a CUDA stream capture, or render
- * loops that must not stall on the allocator. All scratch (per-path results,
- * counters, the render record) lives in one fixed 16 MiB device array that the
- * library defines and every GPU that loads it holds until exit, so a call is
- * limited to width * height * spp <= 1,397,418 paths and 1920 materials;
- * larger renders return SDDM_ERR_INVALID_ARG with a message. d->method must be
- * SDDM_METHOD_MEGAKERNEL, d->bsdf_mode SDDM_BSDF_EXACT, and the per-sample
- * outputs NULL. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.
- * Every call shares the array: calls whose work overlaps on the GPU (several
- * streams or threads) race on it. Output: d->xyz_out, DEVICE, as sddm_render. */
+ * cudaMalloc while rendering -- an application whose own pool allocator owns
+ * the device memory (a library allocating beside it can run out even though
+ * the pool has room), or a render loop whose latency budget has no room for
+ * cudaMalloc / cudaFree, which may wait for the whole device. All scratch
+ * (per-path results, counters, the render record) lives in one fixed 16 MiB
+ * device array that the library defines and every GPU that loads it holds
+ * until exit, so a call is limited to width * height * spp <= 1,397,418 paths
+ * and 1920 materials; larger renders return SDDM_ERR_INVALID_ARG with a
+ * message. d->method must be SDDM_METHOD_MEGAKERNEL, d->bsdf_mode
+ * SDDM_BSDF_EXACT, and the per-sample outputs NULL. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it:
+ * make that first call before any stream capture, and do not use this entry
+ * point after cudaDeviceReset. Every call shares the array and finds the last
+ * call's contents there (each call rewrites what it reads); calls whose work
+ * overlaps on the GPU (several streams or threads) race on it. Returns when
+ * the device has finished. Output: d->xyz_out, DEVICE, as sddm_render. */
 int sddm_render_noalloc(sddm_ctx *ctx, const sddm_render_desc *d, sddm_stats *st);
 
 /* Photon pass of a photon-mapping render (filled by sddm_render_photon_map). */

@@ -4,13 +4,14 @@
 // accumulation). The layers are 64 wide, so a warp carries a 16-row tile
 // through the whole network: the accumulator fragments of one layer, after
 // SiLU and rounding to BF16, are exactly the A fragments of the next layer,
-// so activations move through a 2 KB per-warp staging tile and never leave
-// the SM. Layer 1 (K = 4) and the output layer (N = 2) run on the FP32 pipes.
+// so activations stay in registers from layer to layer and never leave the
+// SM. Layer 1 (K = 4) and the output layer (N = 2) run on the FP32 pipes.
 //
 // Parameters (FP32 master copy, 8770 floats): W1[64][4], b1[64], W2[64][64],
 // b2[64], W3[64][64], b3[64], W4[2][64], b4[2]; z = W h + b. Inputs are mapped
 // to [-1, 1] over the trained box: 2 cos - 1, (lambda - 380) / 200 - 1, 2 s - 1,
-// 2 (d - d_min) / (d_max - d_min) - 1.
+// and the thickness through the slab's internal transmittance at normal
+// incidence, 2 exp(-(alpha d + film absorbance)) - 1 (see features()).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

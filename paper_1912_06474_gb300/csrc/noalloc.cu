@@ -1,12 +1,15 @@
 // sddm_render_noalloc: a megakernel render that allocates no memory.
 //
-// Some callers cannot call cudaMalloc while they render: code running inside
-// a CUDA stream capture, where an allocation would break or serialise the
-// capture, and latency-bound render loops that must never stall on the
-// allocator or synchronise the device for it. sddm_render grows its scratch
-// buffers (per-sample results, counters, render tables) with cudaMalloc on
-// demand; this entry point instead keeps all of that scratch in one
-// file-scope device array of fixed size, so a call allocates nothing.
+// Some callers cannot call cudaMalloc while they render. A host application
+// that hands all device memory to its own pool allocator (a caching allocator
+// keeps freed blocks for itself, so a cudaMalloc from a library beside it can
+// fail for lack of memory the pool is holding) cannot let a library allocate
+// behind its back; and a render loop with a fixed latency budget cannot pay
+// for cudaMalloc / cudaFree, which may wait for the whole device.
+// sddm_render grows its scratch buffers (per-sample results, counters, render
+// tables) with cudaMalloc on demand; this entry point instead keeps all of
+// that scratch in one file-scope device array of fixed size, so a call
+// allocates nothing.
 //
 // The array is 16 MiB and lives on every GPU that loads the library until the
 // process exits. Its first 8 KiB hold the counters, the error word, the render
@@ -16,6 +19,13 @@
 // call's contents; each call overwrites everything it reads (the header is
 // re-uploaded, counters included), but calls whose work overlaps on the GPU --
 // two streams, or two host threads -- race on it.
+//
+// The first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (that device current) and keeps it for the process;
+// make that first call before any stream capture. The address is not looked
+// up again, so the entry point must not be used after cudaDeviceReset. A call
+// returns once the device has finished its work: it reads the counters and
+// the error word back and synchronises the stream.
 #include <cuda_runtime.h>
 
 #include <cstdio>

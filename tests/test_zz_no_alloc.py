@@ -1,11 +1,13 @@
 """sddm_render_noalloc, the render entry point that allocates no memory.
 
-It is for callers that cannot call cudaMalloc while they render (inside a CUDA
-stream capture, or in a loop that must never stall on the allocator); its
-scratch is a fixed device array inside the library. Two calls in a row, of
+It is for callers that cannot call cudaMalloc while they render (an
+application whose own pool allocator owns the device memory, or a render loop
+that has no time for the allocator); its scratch is a fixed device array
+inside the library. Two calls in a row, of
 different sizes, must each match what sddm_render produces for the same
 render, so nothing left in the shared array from a previous call leaks into
-the next. This file is collected last on purpose.
+the next, and the second call must leave the device's free memory exactly
+as it was. This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -27,10 +29,17 @@ def test_noalloc_matches_render_twice():
     g = sc.glass_materials()[0]
     specs = [scenes.RenderSpec(64, 48, 4, 3, seed=5, camera=sc.camera, glass_s={g: 0.8}),
              scenes.RenderSpec(40, 40, 2, 5, seed=6, camera=sc.camera)]
-    for spec in specs:
+    for i, spec in enumerate(specs):
         ref, _ = ctx.render([spec], method="megakernel")
         out = torch.full((spec.height, spec.width, 3), float("nan"), device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = ctx.render_noalloc(spec, out)
+        torch.cuda.synchronize()
+        if i > 0:
+            # after the first call (which loads the kernels and looks up the
+            # scratch address), a call of another size allocates nothing
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy().reshape(-1, 3)
         want = ref[0].cpu().numpy().reshape(-1, 3)
         assert np.isfinite(got).all()
