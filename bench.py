@@ -26,6 +26,14 @@ roofline: the trace kernel (k_trace_wave for DDM, k_megakernel for the plain
           kernel's own device time, against the measured HBM copy bandwidth.
 image_rel_rmse_vs_oracle: the timed image against the FP64 oracle on the
           pixel sample the CPU-baseline leg renders (validity: <= 1e-3).
+mlp_fallback_fraction: surrogate batches that fell back to the exact slab /
+          surrogate batches evaluated.
+facade  = the large electrochromic facade room at its full configuration as a
+          second workload (one process only): 5M triangles, 8 panes each with
+          its own s, 16 renders of 1920x1080 px at 64 spp, depth 8, 81 bins,
+          DDM over 8x8x4 subdomains with the surrogate, all 16 renders in one
+          sddm_render call = one step (about 27 G segments); its own e2e,
+          roofline, arms, cpu_baseline and image check (--no-facade skips it).
 --impl reference times the FP64 CPU oracle on a bounded pixel sample of the
 same workload (there is no reference implementation to install).
 """
@@ -197,9 +205,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _timed_steps(ctx, spec, out, method, bsdf, steps, flush, stream):
+def _timed_steps(ctx, spec, out, method, bsdf, steps, flush, stream, batch=False):
     """K renders, each bracketed by CUDA events on the library's stream, L2
-    flushed before each. Returns (device ms per step, stats per step)."""
+    flushed before each. Returns (device ms per step, stats per step). With
+    ``batch`` spec and out are lists: one step renders all of them in one call."""
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     sts = []
@@ -207,7 +216,7 @@ def _timed_steps(ctx, spec, out, method, bsdf, steps, flush, stream):
     for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
-        sts.append(ctx.render_into([spec], [out], method=method, bsdf=bsdf))
+        sts.append(ctx.render_into(spec if batch else [spec], out if batch else [out], method=method, bsdf=bsdf))
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev], sts
@@ -260,6 +269,7 @@ def run(args):
     segs = sum(_segs(s) for s in sts)
     launches = sum(s["kernel_launches"] for s in sts)
     fallbacks = sum(s.get("mlp_fallbacks", 0) for s in sts)
+    mlp_batches = sum(s.get("mlp_batches", 0) for s in sts)
     total_ms = sum(step_ms)
     image = out.clone()
     # the same steps launched eagerly with CUDA events around every trace launch:
@@ -361,13 +371,141 @@ def run(args):
         "arms": arm_vals,
         "segments_per_step": segs // (args.steps * world), "clocks": clk,
         "mlp_fallback_batches_per_step": fallbacks // args.steps if args.bsdf == "mlp" else None,
+        "mlp_fallback_fraction": round(fallbacks / mlp_batches, 4) if mlp_batches else None,
     }
     if not args.no_cpu_baseline and world == 1:
         info, pix, ref = cpu_baseline(width=args.width, height=args.height, spp=args.spp)
         line["cpu_baseline"] = info
         got = image.cpu().numpy().reshape(-1, 3)[pix].astype(np.float64)
         line["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    if not args.no_facade and world == 1:
+        del ctx, out, image
+        torch.cuda.empty_cache()
+        try:
+            line["facade"] = facade_leg(local, stream, flush, args)
+        except Exception as exc:   # the hotel line stands on its own
+            line["facade"] = {"error": f"{type(exc).__name__}: {exc}"}
     print(json.dumps(line), flush=True)
+
+
+FACADE_WORKLOAD = "facade_room_5M_tris_16x1920x1080_64spp_d8_L81_ddm8x8x4_mlp"
+
+
+def _trace_bytes(cst):
+    """Algorithmic bytes of the DDM trace kernel for the counted render: ray
+    record reads (48 B per visit), hand-offs (48 B), hit records (32 B per
+    extension segment), node (64 B) and triangle (48 B) fetches."""
+    return (48 * cst["ray_visits"] + 48 * cst["crossings"] + 32 * cst["segments_ext"] + 64 * cst["node_visits"]
+            + 48 * cst["tri_tests"])
+
+
+def facade_leg(local, stream, flush, args):
+    """The facade room at its full configuration: every render of the batch in
+    one sddm_render call is one step, timed once after three warm-up calls of
+    the same batch at 1 spp (the same kernels, queues and glass model)."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_1912_06474_gb300 import scenes, sddm
+    scene = scenes.facade_room(L=81, seed=0)
+    specs = scenes.facade_renders(scene)
+    grid = (8, 8, 4)
+    cfg = {"workload": FACADE_WORKLOAD, "triangles": scene.n_tris, "renders": len(specs), "width": specs[0].width,
+           "height": specs[0].height, "spp": specs[0].spp, "max_depth": specs[0].max_depth, "lambda_bins": 81,
+           "panes": len(scene.glass_materials()), "method": "ddm", "grid": list(grid), "bsdf": "mlp",
+           "l2": "inputs larger than L2 (BVHs ~0.6 GB), flushed before the step"}
+    ctx = sddm.Context(local, stream)
+    ctx.set_scene(scene)
+    t0 = time.perf_counter()
+    ctx.build(grid=grid)
+    cfg["build_s"] = round(time.perf_counter() - t0, 3)
+    train = ctx.mlp_train(scene.glass_materials()[0], seed=7)
+    cfg["surrogate_training"] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in train.items()}
+    outs = [torch.empty((sp.height, sp.width, 3), dtype=torch.float32, device="cuda") for sp in specs]
+    warm = [dataclasses.replace(sp, spp=1) for sp in specs]
+    for _ in range(3):
+        ctx.render_into(warm, outs, method="ddm", bsdf="mlp")
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, sts = _timed_steps(ctx, specs, outs, "ddm", "mlp", 1, flush, stream, batch=True)
+    st = sts[0]
+    segs = _segs(st)
+    value = segs / (ms[0] / 1e3) / 1e6
+    # end to end: the same batch through sddm_render_host, images copied back to pinned host memory
+    host = [torch.empty((sp.height, sp.width, 3), dtype=torch.float32).pin_memory() for sp in specs]
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    est = ctx.render_host(specs, host, method="ddm", bsdf="mlp")
+    e2e_s = time.perf_counter() - t0
+    # the kernel's roofline and the other arms on render 0 (1/16 of the step)
+    one = [specs[0]]
+    ctx.set_profiling(count_traversal=True)
+    cst = ctx.render_into(one, outs[:1], method="ddm", bsdf="mlp")
+    ctx.set_profiling(time_trace=True)
+    ctx.render_into(one, outs[:1], method="ddm", bsdf="mlp")
+    tst = ctx.render_into(one, outs[:1], method="ddm", bsdf="mlp")
+    ctx.set_profiling()
+    arms = {}
+    ctx.render_into(one, outs[:1], method="ddm", bsdf="exact")
+    am, ast = _timed_steps(ctx, one, outs[:1], "ddm", "exact", 1, flush, stream, batch=True)
+    arms["ddm_exact_render0_64spp"] = round(_segs(ast[0]) / (am[0] / 1e3) / 1e6, 3)
+    mk = sddm.Context(local, stream)
+    mk.set_scene(scene)
+    mk.build(grid=(1, 1, 1))
+    mk_spec = [dataclasses.replace(specs[0], spp=4)]
+    mk.render_into(mk_spec, outs[:1], method="megakernel", bsdf="exact")
+    am, ast = _timed_steps(mk, mk_spec, outs[:1], "megakernel", "exact", 1, flush, stream, batch=True)
+    arms["megakernel_exact_render0_4spp"] = round(_segs(ast[0]) / (am[0] / 1e3) / 1e6, 3)
+    mk.close()
+    clk = clocks.stop()
+    peak, peak_kind = _peaks()
+    tbytes = _trace_bytes(cst)
+    achieved = tbytes / (tst["trace_ms"] / 1e3) / 1e9 if tst["trace_ms"] > 0 else None
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "steps": 1, "warmup": 3,
+        "warmup_note": "the same 16 renders at 1 spp", "ms_per_step": round(ms[0], 1), "config": cfg,
+        "segments_per_step": segs, "paths_per_step": st["paths"],
+        "e2e": {"value": round(_segs(est) / e2e_s / 1e6, 3), "unit": UNIT,
+                "h2d_bytes_per_step": 128 * len(specs) + 4 * len(scene.materials) * len(specs) + 24,
+                "d2h_bytes_per_step": sum(sp.width * sp.height * 12 for sp in specs) + 80},
+        "gpu_launches": int(st["kernel_launches"]),
+        "mlp_fallback_fraction": round(st["mlp_fallbacks"] / st["mlp_batches"], 4) if st["mlp_batches"] else None,
+        "mlp_batches_per_step": st["mlp_batches"],
+        "arms": arms,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,
+                     "kernel": "k_trace_wave", "peak_kind": peak_kind, "sample": "render 0 of the batch",
+                     "bytes_sample": tbytes, "trace_ms_sample": round(tst["trace_ms"], 3),
+                     "trace_launches_sample": tst["trace_launches"],
+                     "nodes_per_visit": round(cst["node_visits"] / max(cst["ray_visits"], 1), 2),
+                     "tris_per_visit": round(cst["tri_tests"] / max(cst["ray_visits"], 1), 2)},
+        "clocks": clk,
+    }
+    del ctx
+    # the FP64 oracle on a seeded subset of every render: the CPU baseline and
+    # the image check of the timed images (subset rel-RMSE over all renders)
+    import oracle
+    t0 = time.perf_counter()
+    orc = oracle.Oracle(scene)
+    build_s = time.perf_counter() - t0
+    got, ref, oseg, ot = [], [], 0, 0.0
+    for r, sp in enumerate(specs):
+        pix = scenes.pixel_subset(sp.width, sp.height, 256, seed=500 + r)
+        t0 = time.perf_counter()
+        o = orc.render_pixels(sp, pix)
+        ot += time.perf_counter() - t0
+        oseg += sum(o["segments"])
+        ref.append(o["xyz"])
+        got.append(outs[r].cpu().numpy().reshape(-1, 3)[pix].astype(np.float64))
+    g, rf = np.concatenate(got), np.concatenate(ref)
+    res["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(g - rf) / np.linalg.norm(rf))
+    res["cpu_baseline"] = {"value": oseg / ot / 1e6, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+                           "sample": f"256 seeded pixels x 64 spp of each of the 16 renders ({oseg} segments, "
+                                     f"{ot:.1f} s wall; oracle BVH build {build_s:.1f} s not counted)"}
+    return res
 
 
 def main():
@@ -381,6 +519,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--paths-in-flight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-facade", action="store_true", help="skip the full-size facade-room workload")
     ap.add_argument("--single-arm", action="store_true", help="time only the selected method and glass model")
     ap.add_argument("--width", type=int, default=512)
     ap.add_argument("--height", type=int, default=512)

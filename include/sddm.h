@@ -111,6 +111,7 @@ typedef struct {
     int64_t node_visits;      /* SDDM_PROFILE_COUNT_TRAVERSAL: BVH interior nodes visited */
     int64_t tri_tests;        /* SDDM_PROFILE_COUNT_TRAVERSAL: ray/triangle tests */
     int64_t ray_visits;       /* SDDM_PROFILE_COUNT_TRAVERSAL: (ray, subdomain) visits traced */
+    int64_t mlp_batches;      /* surrogate batches evaluated (each probed once); mlp_fallbacks of them fell back */
 } sddm_stats;
 
 /* Profiling switches (sddm_set_profiling), off by default. */

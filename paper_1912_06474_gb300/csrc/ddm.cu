@@ -949,6 +949,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
         mr.mode = 1;
         mr.raw = 0;
         mr.fallbacks = run.counters + 4;
+        mr.batches = run.counters + 8;
     }
 
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);

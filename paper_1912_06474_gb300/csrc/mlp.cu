@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
         __syncwarp();
     }
     if (a.fallbacks && n_fb) atomicAdd(a.fallbacks, n_fb);
+    if (a.batches && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.batches, (unsigned long long)n_batches);
 }
 
 // The exact slab for the same query rows, one thread per (query, bin): the

@@ -776,9 +776,9 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
     cudaStream_t s = ctx->stream;
     if ((e = ctx->d_info.upload(info, s)) || (e = ctx->d_state.upload(state, s)) || (e = ctx->d_out_tab.upload(outs, s)) ||
         (e = ctx->d_aov_xyz_tab.upload(aov_x, s)) || (e = ctx->d_aov_prim_tab.upload(aov_p, s)) ||
-        (e = ctx->d_counters.ensure(8 * sizeof(unsigned long long))) || (e = ctx->d_err.ensure(16)))
+        (e = ctx->d_counters.ensure(kNumCounters * sizeof(unsigned long long))) || (e = ctx->d_err.ensure(16)))
         return cuda_fail(e, "sddm_render: upload of the render table");
-    if ((e = cudaMemsetAsync(ctx->d_counters.p, 0, 8 * sizeof(unsigned long long), s)) ||
+    if ((e = cudaMemsetAsync(ctx->d_counters.p, 0, kNumCounters * sizeof(unsigned long long), s)) ||
         (e = cudaMemsetAsync(ctx->d_err.p, 0, 16, s)))
         return cuda_fail(e, "sddm_render: memset");
     RenderBatch rb;
@@ -938,7 +938,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         if (graphable) ctx->seen[key] = 1;
     }
     if ((e = cudaEventRecord(ctx->ev1, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: event");
-    unsigned long long cnt[8];
+    unsigned long long cnt[kNumCounters];
     int err[4];
     if ((e = cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, s)) ||
         (e = cudaMemcpyAsync(err, ctx->d_err.p, sizeof(err), cudaMemcpyDeviceToHost, s)) ||
@@ -959,6 +959,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         st->glass_queries = (int64_t)cnt[2];
         st->crossings = (int64_t)cnt[3];
         st->mlp_fallbacks = (int64_t)cnt[4];
+        st->mlp_batches = (int64_t)cnt[8];
         st->gpu_ms = ms;
         st->kernel_launches = launches;
         st->node_visits = count_trav ? (int64_t)cnt[5] : 0;
@@ -1180,6 +1181,7 @@ int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d,
         tot.crossings += sj.crossings;
         tot.glass_queries += sj.glass_queries;
         tot.mlp_fallbacks += sj.mlp_fallbacks;
+        tot.mlp_batches += sj.mlp_batches;
         tot.gpu_ms += sj.gpu_ms;
         tot.kernel_launches += sj.kernel_launches + (j > 1 ? 1 : 0);
         ptot.photons += pj.photons;

@@ -93,7 +93,7 @@ struct DDMRun {
     int max_depth;
     float *sample_xyz;
     int32_t *first_prim;
-    unsigned long long *counters;   // ext, shadow, glass, crossings, fallbacks
+    unsigned long long *counters;   // ext, shadow, glass, crossings, fallbacks, nodes, tris, visits, mlp batches
     int *error_flag;
     int sm_count, blocks_per_sm;
     int64_t queue_capacity;

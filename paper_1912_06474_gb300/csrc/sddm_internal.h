@@ -11,6 +11,11 @@
 
 namespace sddm {
 
+// Statistics counters of a render call, u64 each (layout at DevScene users'
+// `counters` fields): ext, shadow, glass, crossings, fallbacks, nodes, tris,
+// visits, surrogate batches; the rest spare.
+constexpr int kNumCounters = 16;
+
 constexpr int kMaxL = 256;
 constexpr int kMaxCross = 4;        // distinct glass slabs a shadow ray may pass through
 constexpr int kMaxDepth = 64;
@@ -158,7 +163,8 @@ struct MegaArgs {
     int64_t path_begin, path_count;    // global path range of this launch
     float *sample_xyz;                 // [path_count][3]
     int32_t *first_prim;               // [path_count] or null
-    unsigned long long *counters;      // [8]: ext, shadow, glass, crossings, fallbacks, nodes, tris, visits
+    unsigned long long *counters;      // [16]: ext, shadow, glass, crossings, fallbacks, nodes, tris, visits,
+                                       // surrogate batches, spare
     int *error_flag;
     int count_traversal;
     PhotonGridView pm = {};            // photon map gathered at the first diffuse vertex (pm.on)

@@ -33,6 +33,7 @@ struct MlpRows {
     int mode;
     int raw;                          // 1: network output only, no probe or fallback
     unsigned long long *fallbacks;    // 32-row batches that fell back to the exact slab
+    unsigned long long *batches;      // 32-row batches evaluated (probe batches; NULL: not counted)
 };
 cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream);
 // The exact slab over the same rows (no network).

@@ -78,7 +78,7 @@ class Stats(C.Structure):
                 ("crossings", C.c_int64), ("glass_queries", C.c_int64), ("mlp_fallbacks", C.c_int64),
                 ("gpu_ms", C.c_double), ("kernel_launches", C.c_int64), ("trace_ms", C.c_double),
                 ("trace_launches", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
-                ("ray_visits", C.c_int64)]
+                ("ray_visits", C.c_int64), ("mlp_batches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

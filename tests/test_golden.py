@@ -60,11 +60,18 @@ def test_c1_golden_on_gpu(method, grid):
     imgs, _ = ctx.render([spec], method=method)
     got = imgs[0].cpu().numpy().reshape(-1, 3)[pix].astype(np.float64)
     rel = np.abs(got - ref).max(1) / np.maximum(np.abs(ref).max(1), 1e-12)
-    # depth-2 paths (a diffuse bounce and a second shadow ray after the first
-    # hit) carry a few more float roundings than the first-hit pass's 1e-5
     safe = (margin > 1e-5) & (cmin >= 0.02)
     assert safe.sum() > 0.9 * len(pix)
-    assert rel[safe].max() <= 1e-4, rel[safe].max()
+    # 1e-5 relative where every shadow-ray cosine of the path is >= 0.05. A
+    # grazing cosine c carries the float rounding of the unit vectors it is
+    # made of (an absolute error of a few 1e-8 per ulp) into the radiance as
+    # a relative error of about that over c: between 0.02 and 0.05 the error
+    # times c stays below 1e-6 (measured: 1.7e-5 at c = 0.026, 1.5e-5 at
+    # c = 0.022, the same in all three methods).
+    well = safe & (cmin >= 0.05)
+    assert well.sum() > 0.8 * len(pix)
+    assert rel[well].max() <= 1e-5, rel[well].max()
+    assert (rel[safe] * cmin[safe]).max() <= 1e-6, (rel[safe] * cmin[safe]).max()
     assert rel.max() <= 1e-3, rel.max()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
     ctx.close()
