@@ -71,7 +71,8 @@ def test_c1_golden_on_gpu(method, grid):
     well = safe & (cmin >= 0.05)
     assert well.sum() > 0.8 * len(pix)
     assert rel[well].max() <= 1e-5, rel[well].max()
-    assert (rel[safe] * cmin[safe]).max() <= 1e-6, (rel[safe] * cmin[safe]).max()
+    cond = rel[safe] * np.minimum(cmin[safe], 1.0)   # cmin is inf on paths without a shadow ray
+    assert cond.max() <= 1e-6, cond.max()
     assert rel.max() <= 1e-3, rel.max()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
     ctx.close()
