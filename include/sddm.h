@@ -70,6 +70,16 @@ typedef struct {
                                  memory that the trace kernel reads over the coherent host link (NVLink-C2C
                                  on Grace-based GPUs) instead of a copy in HBM -- for scenes whose subdomains
                                  exceed device memory (Sec. 5 loads subdomains up to a memory limit); 0 = HBM */
+    int64_t cell_cache_bytes; /* > 0: the subdomain BVHs stay in pinned host memory and a device cache of this
+                                 many bytes holds the subdomains being traced (Sec. 5: subdomains are loaded
+                                 up to a memory limit and unloaded when their rays have run out). Before each
+                                 wave the cells holding rays are loaded, fullest first, least recently used
+                                 cells evicted; a wave whose cells do not fit at once is traced in groups, the
+                                 copies of the next group overlapping the trace of the current one. DDM
+                                 renders only (not photon maps), launched eagerly (one host synchronisation
+                                 per wave). Images are bit-identical to the all-resident build. Must hold the
+                                 largest subdomain (else SDDM_ERR_INVALID_ARG); excludes bvh_in_host_memory.
+                                 0 = all subdomains resident in HBM */
 } sddm_build_opts;
 
 typedef struct {
@@ -112,6 +122,9 @@ typedef struct {
     int64_t tri_tests;        /* SDDM_PROFILE_COUNT_TRAVERSAL: ray/triangle tests */
     int64_t ray_visits;       /* SDDM_PROFILE_COUNT_TRAVERSAL: (ray, subdomain) visits traced */
     int64_t mlp_batches;      /* surrogate batches evaluated (each probed once); mlp_fallbacks of them fell back */
+    int64_t cache_loads;      /* cell_cache_bytes > 0: subdomain BVHs copied into the cache */
+    int64_t cache_hits;       /* ... (cell, wave) uses that found the subdomain already resident */
+    int64_t cache_bytes_loaded; /* ... bytes copied from host memory */
 } sddm_stats;
 
 /* Profiling switches (sddm_set_profiling), off by default. */
@@ -175,7 +188,7 @@ int sddm_add_glass_slab(sddm_ctx *ctx, const float *n, const float *alpha_clear,
  * incoherently through the substrate. 0 <= n_films <= SDDM_MAX_FILMS; with no
  * film this is sddm_add_glass_slab. The paper gives the glass by its "Fresnel
  * definition" (Sec. 6) and has no thin-film model: this call extends it. */
-#define SDDM_MAX_FILMS 4
+#define SDDM_MAX_FILMS 10
 int sddm_add_coated_glass(sddm_ctx *ctx, const float *n, const float *alpha_clear, const float *dalpha,
                           float thickness_m, float s_default, int n_films, const float *film_n, const float *film_k,
                           const float *film_dk, const float *film_t_nm, uint32_t *mat);

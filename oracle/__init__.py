@@ -31,6 +31,8 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libsddm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
+# coating films per glass face (ORC_MAX_FILMS in oracle_internal.h)
+MAX_FILMS = 10
 # material kinds: same integer codes as the scene inputs
 LAMBERT, CONDUCTOR, GLASS, EMITTER, DIFFUSE_EMITTER = 0, 1, 2, 3, 4
 
@@ -107,6 +109,10 @@ def _load():
         lib.orc_closest_hit.restype = C.c_int
         lib.orc_shadow.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
         lib.orc_shadow.restype = C.c_int
+        lib.orc_watertight.argtypes = [P, P, P, C.POINTER(C.c_double)]
+        lib.orc_watertight.restype = C.c_int
+        lib.orc_plane.argtypes = [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.orc_plane.restype = C.c_int
         lib.orc_num_lights.argtypes = [P]
         lib.orc_num_lights.restype = C.c_int
         lib.orc_mlp_n_params.restype = C.c_int
@@ -203,6 +209,30 @@ def cosine_dir(ns, u0, u1):
 MLP_PARAMS = 8770
 
 
+def watertight(tri, o, d):
+    """Watertight ray/triangle test (FP64): (hit, t) for the line of ray
+    (o, d) against triangle tri[3][3]; t may be negative."""
+    v = np.ascontiguousarray(tri, np.float64).reshape(9)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    t = C.c_double()
+    hit = _load().orc_watertight(_ptr(v), _ptr(o), _ptr(d), C.byref(t))
+    return bool(hit), (t.value if hit else np.inf)
+
+
+def moller_trumbore(tri, o, d):
+    """The renderer's Moller-Trumbore test (FP64): (hit, t, (u, w)) with hit
+    when the line meets the triangle (u, w >= 0, u + w <= 1)."""
+    v = np.ascontiguousarray(tri, np.float64).reshape(9)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    t, u, w = C.c_double(), C.c_double(), C.c_double()
+    if not _load().orc_plane(_ptr(v), _ptr(o), _ptr(d), C.byref(t), C.byref(u), C.byref(w)):
+        return False, np.inf, (np.nan, np.nan)
+    hit = u.value >= 0 and w.value >= 0 and u.value + w.value <= 1
+    return hit, t.value, (u.value, w.value)
+
+
 def mlp_features(c, lam_nm, s, d, alpha, film_absorbance=0.0):
     """Network inputs of one row: cos, wavelength (nm), coloration state,
     thickness (m), the absorption coefficient alpha(lambda, s) (1/m) and the
@@ -284,14 +314,14 @@ def _material_arrays(scene):
 def _layer_arrays(scene):
     L, M = scene.L, len(scene.materials)
     nl = np.zeros(M, np.int32)
-    ln = np.zeros((M, 4, L), np.float32)
-    lk = np.zeros((M, 4, L), np.float32)
-    ldk = np.zeros((M, 4, L), np.float32)
-    lt = np.zeros((M, 4), np.float32)
+    ln = np.zeros((M, MAX_FILMS, L), np.float32)
+    lk = np.zeros((M, MAX_FILMS, L), np.float32)
+    ldk = np.zeros((M, MAX_FILMS, L), np.float32)
+    lt = np.zeros((M, MAX_FILMS), np.float32)
     for i, m in enumerate(scene.materials):
         if m.kind == GLASS and m.layers:
-            if len(m.layers) > 4:
-                raise ValueError("at most 4 films per face")
+            if len(m.layers) > MAX_FILMS:
+                raise ValueError(f"at most {MAX_FILMS} films per face")
             nl[i] = len(m.layers)
             for j, f in enumerate(m.layers):
                 ln[i, j], lk[i, j], ldk[i, j], lt[i, j] = f["n"], f["k"], f["dk"], f["t_nm"]

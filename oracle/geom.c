@@ -66,6 +66,50 @@ int orc_plane(const double *v, const double o[3], const double d[3], double *t, 
     return 1;
 }
 
+/* Watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013), double
+ * sided, in double precision. The vertices are taken relative to the ray
+ * origin and sheared so that the ray runs along +z (kz = the axis of the
+ * largest |d|, kx and ky the next two in cyclic order, swapped when d[kz] < 0
+ * to keep the winding); the projected triangle's signed edge functions
+ * U, V, W decide: a hit needs all three >= 0 or all three <= 0 and a nonzero
+ * sum, and then t = (U z_a + V z_b + W z_c) / (U + V + W) with z the sheared
+ * depths. Two triangles that share an edge compute its edge function from the
+ * same two projected vertices with opposite signs, so a ray cannot pass
+ * between them. Returns 1 with *t for a hit of the ray's line (t of either
+ * sign), else 0. The pins compare it with orc_plane; the renderer itself
+ * uses orc_plane. */
+int orc_watertight(const double *v, const double o[3], const double d[3], double *t)
+{
+    const double ad[3] = {fabs(d[0]), fabs(d[1]), fabs(d[2])};
+    int kz = ad[0] >= ad[1] ? (ad[0] >= ad[2] ? 0 : 2) : (ad[1] >= ad[2] ? 1 : 2);
+    int kx = (kz + 1) % 3, ky = (kx + 1) % 3;
+    if (d[kz] < 0.0) {
+        int tmp = kx;
+        kx = ky;
+        ky = tmp;
+    }
+    const double sx = d[kx] / d[kz], sy = d[ky] / d[kz], sz = 1.0 / d[kz];
+    double px[3], py[3], pz[3];
+    for (int i = 0; i < 3; ++i) {
+        double rel[3];
+        sub3(v + 3 * i, o, rel);
+        px[i] = rel[kx] - sx * rel[kz];
+        py[i] = rel[ky] - sy * rel[kz];
+        pz[i] = sz * rel[kz];
+    }
+    /* edge functions: U opposite vertex 0 (edge 1-2), V opposite 1, W opposite 2 */
+    const double U = px[2] * py[1] - py[2] * px[1];
+    const double V = px[0] * py[2] - py[0] * px[2];
+    const double W = px[1] * py[0] - py[1] * px[0];
+    if ((U < 0.0 || V < 0.0 || W < 0.0) && (U > 0.0 || V > 0.0 || W > 0.0))
+        return 0;
+    const double det = U + V + W;
+    if (det == 0.0)
+        return 0;
+    *t = (U * pz[0] + V * pz[1] + W * pz[2]) / det;
+    return 1;
+}
+
 static int excluded(const orc_ctx *c, int tri, int excl_prim, int excl_obj)
 {
     return tri == excl_prim || (excl_obj >= 0 && c->obj[tri] == excl_obj);

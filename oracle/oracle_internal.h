@@ -7,7 +7,7 @@
 
 #define ORC_MAX_L 256
 #define ORC_MAX_CROSS 4
-#define ORC_MAX_FILMS 4
+#define ORC_MAX_FILMS 10
 
 typedef struct {
     double lo[3], hi[3];

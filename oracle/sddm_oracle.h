@@ -59,7 +59,7 @@ typedef struct {
     const uint32_t *mat_id;   /* [nt] */
     const uint32_t *obj_id;   /* [nt] */
     /* thin-film coating of glass materials (both faces); NULL = none */
-    const int32_t *mat_nlayers; /* [n_mat] films per face, 0..4 */
+    const int32_t *mat_nlayers; /* [n_mat] films per face, 0..10 */
     const float *layer_n;     /* [n_mat][4][L] film real index */
     const float *layer_k;     /* [n_mat][4][L] film extinction at s = 0 */
     const float *layer_dk;    /* [n_mat][4][L] extinction added at s = 1 (k = k + s dk) */
@@ -138,6 +138,12 @@ int orc_closest_hit(void *ctx, const double o[3], const double d[3], int brute_f
 int orc_shadow(void *ctx, const double o[3], const double d[3], double tmax, int excl_prim,
                int brute_force, int *n_cross, int32_t cross_obj[4], double cross_cos[4]);
 int orc_num_lights(void *ctx);
+/* Watertight ray/triangle test (Woop, Benthin, Wald 2013) in double precision:
+ * 1 and *t when the line of the ray (o, d) meets triangle v[9], else 0. Pins only. */
+int orc_watertight(const double *v, const double o[3], const double d[3], double *t);
+/* Moller-Trumbore parameters of the same ray and triangle: 0 when parallel,
+ * else 1 with t and the barycentrics (u, w) of vertices 1 and 2. */
+int orc_plane(const double *v, const double o[3], const double d[3], double *t, double *u, double *w);
 
 /* Glass surrogate network (mlp.c): 4 -> 64 -> 64 -> 64 (SiLU) -> 2, 8770 parameters. */
 int orc_mlp_n_params(void);

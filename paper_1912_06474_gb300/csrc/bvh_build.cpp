@@ -128,8 +128,8 @@ class Builder {
             std::memcpy(&ob, &t.obj, 4);
             std::memcpy(&fl, &t.flags, 4);
             out_.tris.push_back(make_float4(t.v[0][0], t.v[0][1], t.v[0][2], id));
-            out_.tris.push_back(make_float4(t.v[1][0] - t.v[0][0], t.v[1][1] - t.v[0][1], t.v[1][2] - t.v[0][2], ob));
-            out_.tris.push_back(make_float4(t.v[2][0] - t.v[0][0], t.v[2][1] - t.v[0][1], t.v[2][2] - t.v[0][2], fl));
+            out_.tris.push_back(make_float4(t.v[1][0], t.v[1][1], t.v[1][2], ob));
+            out_.tris.push_back(make_float4(t.v[2][0], t.v[2][1], t.v[2][2], fl));
         }
         int count = end - begin;
         return ~((first << kLeafBits) | count);

@@ -27,6 +27,7 @@
 
 #include "device_common.cuh"
 #include "sddm_ddm.h"
+#include "sddm_cache.h"
 #include "sddm_mlp.h"
 #include "sddm_ddm_photon.h"
 #include "photon.cuh"
@@ -75,6 +76,11 @@ struct KArgs {
     int *block_cnt;       // [gridDim] glass queries per block of path slots (count pass)
     PhotonGridView pm;    // photon map: gather at the first diffuse vertex, no continuation there
     PhotonGridView pmc;   // caustic map gathered with it (pmc.on)
+    // subdomain cache: the wave's queue is sorted with the cells in this order
+    // (NULL: cell order), and a trace launch takes queue range [q_begin, q_end)
+    // (q_end = 0: the whole wave)
+    const int *cell_perm;
+    int64_t q_begin, q_end;
 };
 
 // Queue bin of a ray: its cell, its kind (extension / shadow) and, as far as
@@ -268,12 +274,17 @@ __global__ void __launch_bounds__(256) k_camera(KArgs a) {
 
 // ------------------------------------------------------ sort by cell
 // Exclusive prefix of the per-cell counts into s_off (every block computes it).
-__device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp) {
+// Exclusive prefix sums of the n bin counts in s_off (and the total in
+// s_off[n]), the bins taken in the order of `perm` over groups of `per_cell`
+// bins (NULL: index order).
+__device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp, const int *perm = nullptr,
+                             int per_cell = 1) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int per = (n + nt - 1) / nt;
     const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+    auto bin = [&](int i) { return perm ? __ldg(perm + i / per_cell) * per_cell + i % per_cell : i; };
     int sum = 0;
-    for (int i = b0; i < b1; ++i) sum += cnt[i];
+    for (int i = b0; i < b1; ++i) sum += cnt[bin(i)];
     s_tmp[t] = sum;
     __syncthreads();
     for (int off = 1; off < nt; off <<= 1) {
@@ -284,8 +295,9 @@ __device__ void block_prefix(const int *cnt, int n, int *s_off, int *s_tmp) {
     }
     int run = s_tmp[t] - sum;
     for (int i = b0; i < b1; ++i) {
-        s_off[i] = run;
-        run += cnt[i];
+        const int b = bin(i);
+        s_off[b] = run;
+        run += cnt[b];
     }
     if (t == nt - 1) s_off[n] = s_tmp[t];
     __syncthreads();
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(256, SDDM_SCATTER_MINB) k_scatter(KArgs a) {
     __shared__ int s_tmp[256];
     const Queues &Q = a.Q;
     const int n_cells = a.g.n_bins;   // bins: (cell, ray kind, octant)
-    block_prefix(Q.cnt, n_cells, s_off, s_tmp);
+    block_prefix(Q.cnt, n_cells, s_off, s_tmp, a.cell_perm, 2 * a.g.n_oct);
     int total = s_off[n_cells];
     // the per-cell counts must add up to the staged rays, within capacity
     const bool bad = (unsigned long long)total != Q.ctl[0] || (int64_t)total > Q.cap;
@@ -350,7 +362,15 @@ __global__ void __launch_bounds__(256, SDDM_SCATTER_MINB) k_scatter(KArgs a) {
 #pragma unroll
         for (int k = 0; k < kScatterRaysPerThread; ++k) {
             if (cell[k] < 0) continue;
-            float4 *dst = Q.in + 3 * (size_t)(s_bin[cell[k]] + rank[k]);
+            const int at = s_bin[cell[k]] + rank[k];
+            if (at < 0 || at >= total) {   // the bin offsets must place every ray inside the wave
+                if (atomicCAS(a.err, 0, 11) == 0) {
+                    a.err[1] = cell[k];
+                    a.err[2] = at;
+                }
+                continue;
+            }
+            float4 *dst = Q.in + 3 * (size_t)at;
             dst[0] = r0[k];
             dst[1] = r1[k];
             dst[2] = r2[k];
@@ -934,6 +954,9 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
     a.glass_res = (const float2 *)(m + oRes);
     a.block_cnt = (int *)(m + oBc);
     a.pm = pmv;
+    a.cell_perm = nullptr;
+    a.q_begin = 0;
+    a.q_end = 0;
     a.pmc = pmcv;
     MlpRows mr{};
     if (use_queries) {
@@ -970,25 +993,73 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
     const size_t bins_smem = sizeof(int) * (size_t)nb;
     k_camera<<<path_blocks, 256, bins_smem, s>>>(a);
     DDM_CHECK(cudaGetLastError());
+    auto trace_launch = [&]() -> int {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (run.time_trace) {
+            if ((e = buf.event_pair(e0, e1)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
+            DDM_CHECK(cudaEventRecord(e0, s));
+        }
+        if (run.cache)
+            k_trace_wave<false, true><<<trace_blocks, 128, 0, s>>>(a);
+        else if (run.count_traversal)
+            k_trace_wave<true><<<trace_blocks, 128, 0, s>>>(a);
+        else
+            k_trace_wave<false><<<trace_blocks, 128, 0, s>>>(a);
+        DDM_CHECK(cudaGetLastError());
+        if (run.time_trace) DDM_CHECK(cudaEventRecord(e1, s));
+        *run.launches += 1;
+        return SDDM_OK;
+    };
+    CellCache *cache = run.cache;
+    std::vector<int64_t> cell_rays(cache ? (size_t)run.g.n_cells : 0);
     for (int b = 1; b <= run.max_depth + 1; ++b) {
         for (int w = 0; w < waves; ++w) {
-            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nb, s));
-            k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
-            DDM_CHECK(cudaGetLastError());
-            DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
             a.last_wave = w == waves - 1;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (run.time_trace) {
-                if ((e = buf.event_pair(e0, e1)) != cudaSuccess) return cuda_fail(e, "sddm_render: events");
-                DDM_CHECK(cudaEventRecord(e0, s));
+            DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nb, s));
+            if (!cache) {
+                k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
+                DDM_CHECK(cudaGetLastError());
+                DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
+                const int rc = trace_launch();
+                if (rc != SDDM_OK) return rc;
+                *run.launches += 1;
+                continue;
             }
-            if (run.count_traversal)
-                k_trace_wave<true><<<trace_blocks, 128, 0, s>>>(a);
-            else
-                k_trace_wave<false><<<trace_blocks, 128, 0, s>>>(a);
-            DDM_CHECK(cudaGetLastError());
-            if (run.time_trace) DDM_CHECK(cudaEventRecord(e1, s));
-            *run.launches += 2;
+            // subdomain cache (Sec. 5's loading and unloading of subdomains):
+            // the rays waiting per cell decide which cells are loaded, in
+            // which groups the wave is traced, and the order of its queue
+            DDM_CHECK(cudaMemcpyAsync(cache->h_cnt, Q.cnt, 4 * (size_t)nb, cudaMemcpyDeviceToHost, s));
+            DDM_CHECK(cudaMemcpyAsync(cache->h_err, run.error_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            DDM_CHECK(cudaStreamSynchronize(s));
+            if (cache->h_err[0] != 0) return SDDM_OK;   // reported by the caller's error-word check
+            const int per_cell = 2 * run.g.n_oct;
+            for (int c = 0; c < run.g.n_cells; ++c) {
+                int64_t r = 0;
+                for (int k = 0; k < per_cell; ++k) r += cache->h_cnt[c * per_cell + k];
+                cell_rays[c] = r;
+            }
+            auto sort_queue = [&]() -> int {
+                DDM_CHECK(cudaMemcpyAsync(cache->d_perm, cache->h_perm, 4 * (size_t)run.g.n_cells,
+                                          cudaMemcpyHostToDevice, s));
+                a.cell_perm = cache->d_perm;
+                k_scatter<<<scatter_blocks, 256, 0, s>>>(a);
+                DDM_CHECK(cudaGetLastError());
+                a.cell_perm = nullptr;
+                DDM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
+                *run.launches += 1;
+                return SDDM_OK;
+            };
+            auto group_launch = [&](int64_t q_begin, int64_t q_end) -> int {
+                DDM_CHECK(cudaMemsetAsync(Q.ctl + 1, 0, sizeof(unsigned long long), s));
+                a.q_begin = q_begin;
+                a.q_end = q_end;
+                const int rc = trace_launch();
+                a.q_begin = 0;
+                a.q_end = 0;
+                return rc;
+            };
+            const int rc = cache->run_wave(cell_rays, s, sort_queue, group_launch);
+            if (rc != SDDM_OK) return rc;
         }
         a.b = b;
         if (use_queries && b >= 2) {

@@ -107,12 +107,26 @@ __device__ __forceinline__ void flush_push_buf(const Queues &Q, const float4 *bu
 #define SDDM_TRACE_MIN_BLOCKS 8
 #endif
 
-template <bool COUNT>
+// First device check to fail records its code and two details in the error word.
+__device__ __forceinline__ void trace_check_fail(int *err, int code, int x, int y) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = x;
+        err[2] = y;
+    }
+}
+
+// CHECKED (the subdomain cache, whose cells move between loads): every root,
+// child and leaf index is checked against the records the cache holds before
+// it is read; a bad one is recorded (codes 8-10) and the ray is dropped.
+template <bool COUNT, bool CHECKED = false>
 __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs a) {
     const Queues &Q = a.Q;
     const DDMScene &g = a.g;
-    const int total = Q.off[g.n_bins];
-    if (total == 0) return;
+    // the rays of this launch: the whole wave, or one group's range of it
+    // (the groups of cells resident together in the subdomain cache)
+    const int q0 = a.q_end > 0 ? (int)a.q_begin : 0;
+    const int total = (a.q_end > 0 ? (int)a.q_end : Q.off[g.n_bins]) - q0;
+    if (total <= 0) return;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -167,19 +181,28 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
             if (need) {
                 const unsigned long long my = mine;
                 if (my < (unsigned long long)total) {
-                    idx = (int)my;
+                    idx = q0 + (int)my;
                     const float4 *src = Q.in + 3 * (size_t)idx;
                     const float4 r0 = src[0], r1 = src[1], r2f = src[2];
                     q = __float_as_int(r2f.x);
                     excl = __float_as_int(r2f.y);
                     rfl = __float_as_int(r2f.z);
-                    const int cell = __float_as_int(r2f.w);
+                    int cell = __float_as_int(r2f.w);
+                    if (CHECKED && (q < 0 || q >= np || cell < 0 || cell >= g.n_cells)) {
+                        trace_check_fail(a.err, 12, q, cell);
+                        q = 0;
+                        cell = 0;
+                    }
                     ray = make_ray(xyz(r0), xyz(r1));
                     t_cur = r0.w;
                     t_max = r1.w;
                     t_exit = cell_exit(g, cell, ray, next);
                     tmin = fmaxf(0.0f, t_cur - g.eps);
                     node = __ldg(g.root + cell);
+                    if (CHECKED && (node < 0 || node >= g.node_cap)) {
+                        trace_check_fail(a.err, 8, cell, node);
+                        node = ~0;   // an empty leaf: the ray ends here
+                    }
                     sp = 0;
                     best = -1;
                     occ = false;
@@ -217,7 +240,17 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                 float ta, tb;
                 bool ha, hb;
                 child_boxes(ray, n0, n1, n2, tmin, tw, ta, tb, ha, hb);
-                const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+                int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+                if (CHECKED) {
+                    if (ca >= g.node_cap) {
+                        trace_check_fail(a.err, 9, node, ca);
+                        ca = ~0;
+                    }
+                    if (cb >= g.node_cap) {
+                        trace_check_fail(a.err, 9, node, cb);
+                        cb = ~0;
+                    }
+                }
                 if (ha && hb) {
                     const bool a_first = shadow || ta <= tb;
                     if (sp < kStackSize) {
@@ -239,7 +272,12 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
         }
         if (live && !fin && node < 0) {
             const int v = ~node;
-            const int first = v >> kLeafBits, count = v & ((1 << kLeafBits) - 1);
+            const int first = v >> kLeafBits;
+            int count = v & ((1 << kLeafBits) - 1);
+            if (CHECKED && (int64_t)first + count > g.tri_cap) {
+                trace_check_fail(a.err, 10, first, count);
+                count = 0;
+            }
             for (int i = 0; i < count; ++i) {
                 const float4 *tp = g.tris + 3 * (first + i);
                 const float4 ta4 = __ldg(tp), tb4 = __ldg(tp + 1), tc4 = __ldg(tp + 2);
@@ -247,14 +285,13 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                 if (shadow) {
                     if (id == excl) continue;
                     if (COUNT) ++tc.tris;
-                    const V3 e1 = xyz(tb4), e2 = xyz(tc4);
-                    const float t = mt_intersect(ray, xyz(ta4), e1, e2);
+                    const float t = wt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
                     if (!(t > tmin && t <= tw)) continue;
                     if (!(__float_as_uint(tc4.w) & kTriGlass)) {
                         occ = true;
                         break;
                     }
-                    if (dot(ray.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
+                    if (dot(ray.d, cross(xyz(tb4) - xyz(ta4), xyz(tc4) - xyz(ta4))) >= 0.0f) continue;   // leaving face
                     const int ob = __float_as_int(tb4.w);
                     bool seen = false;
                     for (int k = 0; k < cr.n; ++k) seen |= cr.obj[k] == ob;
@@ -269,7 +306,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                 } else {
                     if (id == ep || (eo >= 0 && __float_as_int(tb4.w) == eo)) continue;
                     if (COUNT) ++tc.tris;
-                    const float t = mt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
+                    const float t = wt_intersect(ray, xyz(ta4), xyz(tb4), xyz(tc4));
                     if (t > tmin && (t < tw || (t == tw && (best < 0 || id < best)))) {
                         tw = t;
                         best = id;

@@ -51,21 +51,75 @@ __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0
 // Node = 4 float4: (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y) (c1 same) (c0.lo.z, c0.hi.z,
 // c1.lo.z, c1.hi.z) (child0, child1 as int bits). child >= 0: node index;
 // child < 0: leaf, ~child = (first triangle << 4) | count.
-// Triangle = 3 float4: (v0, id) (e1 = v1 - v0, obj) (e2 = v2 - v0, flags).
+// Triangle = 3 float4: (v0, id) (v1, obj) (v2, flags): the vertices
+// themselves, so that triangles sharing an edge see bit-identical endpoints.
 
+// A ray with what its box and triangle tests need: reciprocal direction and
+// origin times it (boxes), and the set-up of the watertight triangle test of
+// Woop, Benthin and Wald (JCGT 2013): the axis kz along which the direction is
+// largest, the other two kx, ky (swapped when d[kz] < 0, which keeps the
+// winding), and the shear (sx, sy) = (d[kx], d[ky]) / d[kz] that maps the
+// ray onto the +z axis of a frame centred on its origin; the scale 1 / d[kz]
+// is inv[kz] (|d[kz]| >= 1/sqrt(3) for a unit direction, never clamped).
 struct Ray {
     V3 o, d, inv, oi;   // oi = o * inv
+    float sx, sy;
+    int k;              // kx | ky << 2 | kz << 4
 };
 __device__ __forceinline__ float safe_inv(float d) {
     return 1.0f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d));
 }
+__device__ __forceinline__ float comp(V3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 __device__ __forceinline__ Ray make_ray(V3 o, V3 d) {
     Ray r;
     r.o = o;
     r.d = d;
     r.inv = v3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
     r.oi = v3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    const int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+    const float dz = comp(d, kz);
+    if (dz < 0.0f) {
+        const int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r.sx = comp(d, kx) / dz;
+    r.sy = comp(d, ky) / dz;
+    r.k = kx | (ky << 2) | (kz << 4);
     return r;
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald 2013), double sided:
+// the vertices are taken relative to the ray origin and sheared so that the
+// ray runs along +z; the signed edge functions U, V, W of the projected
+// triangle decide inside/outside. Each is a difference of two correctly
+// rounded products, so a shared edge gives its two triangles edge functions
+// of exactly opposite sign and a ray through it cannot slip between them;
+// an exact zero is re-evaluated in double precision. Returns the hit
+// distance, or +inf.
+__device__ __forceinline__ float wt_intersect(const Ray &r, V3 p0, V3 p1, V3 p2) {
+    const int kx = r.k & 3, ky = (r.k >> 2) & 3, kz = r.k >> 4;
+    const V3 A = p0 - r.o, B = p1 - r.o, C = p2 - r.o;
+    const float Az = comp(A, kz), Bz = comp(B, kz), Cz = comp(C, kz);
+    const float Ax = fmaf(-r.sx, Az, comp(A, kx)), Ay = fmaf(-r.sy, Az, comp(A, ky));
+    const float Bx = fmaf(-r.sx, Bz, comp(B, kx)), By = fmaf(-r.sy, Bz, comp(B, ky));
+    const float Cx = fmaf(-r.sx, Cz, comp(C, kx)), Cy = fmaf(-r.sy, Cz, comp(C, ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if (fminf(U, fminf(V, W)) < 0.0f && fmaxf(U, fmaxf(V, W)) > 0.0f) return __int_as_float(0x7f800000);
+    const float det = U + V + W;
+    if (det == 0.0f) return __int_as_float(0x7f800000);
+    const float sz = comp(r.inv, kz);
+    const float T = fmaf(U, sz * Az, fmaf(V, sz * Bz, W * (sz * Cz)));
+    return T / det;
 }
 
 // Slab test of both children of a node against [tmin, tmax]: hit flags and entry distances.
@@ -85,24 +139,6 @@ __device__ __forceinline__ void child_boxes(const Ray &r, float4 n0, float4 n1, 
     h1 = blo <= bhi;
     t0 = alo;
     t1 = blo;
-}
-
-// Moller-Trumbore, double sided: returns t of the plane hit inside the
-// triangle (u >= 0, v >= 0, u + v <= 1), or +inf. The barycentric tests run
-// on the unscaled numerators against |det| (signs folded in), so the divide
-// is taken only for triangles the ray actually crosses.
-__device__ __forceinline__ float mt_intersect(const Ray &r, V3 v0, V3 e1, V3 e2) {
-    const V3 p = cross(r.d, e2);
-    const float det = dot(e1, p);
-    if (det == 0.0f) return __int_as_float(0x7f800000);
-    const float sgn = det > 0.0f ? 1.0f : -1.0f, adet = fabsf(det);
-    const V3 s = r.o - v0;
-    const float us = sgn * dot(s, p);
-    if (us < 0.0f || us > adet) return __int_as_float(0x7f800000);
-    const V3 q = cross(s, e1);
-    const float vs = sgn * dot(r.d, q);
-    if (vs < 0.0f || us + vs > adet) return __int_as_float(0x7f800000);
-    return dot(e2, q) / det;
 }
 
 struct Hit {
@@ -155,7 +191,7 @@ __device__ __forceinline__ Hit trace_closest(const float4 *__restrict__ nodes, c
                 int id = __float_as_int(a.w);
                 if (id == excl_prim || (excl_obj >= 0 && __float_as_int(b.w) == excl_obj)) continue;
                 if (COUNT) ++cnt->tris;
-                float t = mt_intersect(r, xyz(a), xyz(b), xyz(c));
+                float t = wt_intersect(r, xyz(a), xyz(b), xyz(c));
                 if (t > tmin && (t < h.t || (t == h.t && (h.prim < 0 || id < h.prim)))) {
                     h.t = t;
                     h.prim = id;
@@ -211,11 +247,10 @@ __device__ __forceinline__ bool trace_shadow(const float4 *__restrict__ nodes, c
                 int id = __float_as_int(a.w);
                 if (id == excl_prim) continue;
                 if (COUNT) ++cnt->tris;
-                V3 e1 = xyz(b), e2 = xyz(c);
-                float t = mt_intersect(r, xyz(a), e1, e2);
+                float t = wt_intersect(r, xyz(a), xyz(b), xyz(c));
                 if (!(t > tmin && t <= tmax)) continue;
                 if (!(__float_as_uint(c.w) & kTriGlass)) return true;
-                if (dot(r.d, cross(e1, e2)) >= 0.0f) continue;   // leaving face
+                if (dot(r.d, cross(xyz(b) - xyz(a), xyz(c) - xyz(a))) >= 0.0f) continue;   // leaving face
                 int ob = __float_as_int(b.w);
                 bool seen = false;
                 for (int q = 0; q < cr.n; ++q) seen |= cr.obj[q] == ob;
@@ -321,7 +356,7 @@ __device__ __forceinline__ Cx cx_sqrt(Cx z) {   // principal root
 }
 
 // Up to kMaxFilms films per face.
-constexpr int kMaxFilms = 4;
+constexpr int kMaxFilms = SDDM_MAX_FILMS;
 
 // Glass coated on both faces with the same stack of J thin films (outermost
 // first): each face is a coherent stack evaluated by its characteristic

@@ -18,6 +18,7 @@
 
 #include "sddm_internal.h"
 #include "sddm_ddm.h"
+#include "sddm_cache.h"
 #include "sddm_mlp.h"
 #include "sddm_photon.h"
 #include "sddm_ddm_photon.h"
@@ -133,7 +134,8 @@ struct sddm_ctx {
     DevScene dev{};
     DDMScene ddm{};
     DevBuf d_cell_nodes, d_cell_tris, d_cell_root, d_cell_planes, d_cell_next;
-    HostBuf h_cell_nodes, h_cell_tris;   // the same, in host memory (bvh_in_host_memory)
+    HostBuf h_cell_nodes, h_cell_tris;   // the same, in host memory (bvh_in_host_memory, cell_cache_bytes)
+    CellCache cache;                     // device cache of subdomain BVHs (cell_cache_bytes > 0)
     // per-render scratch
     DevBuf d_info, d_state, d_out_tab, d_aov_xyz_tab, d_aov_prim_tab, d_samples, d_first, d_counters, d_err;
     DDMBuffers ddm_buf;
@@ -381,8 +383,10 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     default_opts(o);
     if (o.grid[0] > 64 || o.grid[1] > 64 || o.grid[2] > 64 || o.leaf_size > kMaxLeaf || o.sah_bins < 4 ||
         o.sah_bins > 64 || o.queue_capacity < 0 || o.blocks_per_sm < 0 || o.blocks_per_sm > 32 ||
-        o.paths_in_flight < 0 || o.bvh_in_host_memory < 0 || o.bvh_in_host_memory > 1)
+        o.paths_in_flight < 0 || o.bvh_in_host_memory < 0 || o.bvh_in_host_memory > 1 || o.cell_cache_bytes < 0)
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: options out of range");
+    if (o.cell_cache_bytes > 0 && o.bvh_in_host_memory)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_build: cell_cache_bytes and bvh_in_host_memory exclude each other");
     // every mesh material must exist (the material list may have changed since set_mesh)
     for (uint32_t m : ctx->mat_id)
         if (m >= ctx->mats.size()) return fail(SDDM_ERR_INVALID_ARG, "sddm_build: mesh references a missing material");
@@ -452,27 +456,27 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         }
         thick[m] = mt.thick;
     }
-    // coating films of glass materials, [m][4][L] (+ thickness [m][4])
+    // coating films of glass materials, [m][SDDM_MAX_FILMS][L] (+ thickness [m][SDDM_MAX_FILMS])
     bool any_film = false;
     for (int m = 0; m < M; ++m) any_film |= ctx->mats[m].n_film > 0;
     std::vector<int> nfilm(M, 0);
     std::vector<float> FN, FK, FDK, FT;
     if (any_film) {
-        FN.assign((size_t)M * 4 * L, 1.f);
-        FK.assign((size_t)M * 4 * L, 0.f);
-        FDK.assign((size_t)M * 4 * L, 0.f);
-        FT.assign((size_t)M * 4, 0.f);
+        FN.assign((size_t)M * SDDM_MAX_FILMS * L, 1.f);
+        FK.assign((size_t)M * SDDM_MAX_FILMS * L, 0.f);
+        FDK.assign((size_t)M * SDDM_MAX_FILMS * L, 0.f);
+        FT.assign((size_t)M * SDDM_MAX_FILMS, 0.f);
         for (int m = 0; m < M; ++m) {
             const Material &mt = ctx->mats[m];
             nfilm[m] = mt.n_film;
             for (int j = 0; j < mt.n_film; ++j) {
                 for (int i = 0; i < L; ++i) {
-                    const size_t f = ((size_t)m * 4 + j) * L + i;
+                    const size_t f = ((size_t)m * SDDM_MAX_FILMS + j) * L + i;
                     FN[f] = mt.film_n[(size_t)j * L + i];
                     FK[f] = mt.film_k[(size_t)j * L + i];
                     FDK[f] = mt.film_dk[(size_t)j * L + i];
                 }
-                FT[(size_t)m * 4 + j] = mt.film_t[j];
+                FT[(size_t)m * SDDM_MAX_FILMS + j] = mt.film_t[j];
             }
         }
     }
@@ -497,11 +501,16 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     build_grid(tris, o.grid, glo, ghi, o.leaf_size, o.sah_bins, eps, cells, n_threads);
     std::vector<float4> cell_nodes, cell_tris;
     std::vector<int> cell_root;
+    std::vector<int64_t> c_node_base, c_node_cnt, c_tri_base, c_tri_cnt;   // per cell, for the cache
     int64_t tri_base_check = 0;
     for (auto &c : cells) {
         int node_base = (int)(cell_nodes.size() / 4);
         int tri_base = (int)(cell_tris.size() / 3);
         cell_root.push_back(node_base);
+        c_node_base.push_back(node_base);
+        c_node_cnt.push_back((int64_t)c.nodes.size() / 4);
+        c_tri_base.push_back(tri_base);
+        c_tri_cnt.push_back((int64_t)c.tris.size() / 3);
         // rebase child codes
         for (size_t k = 0; k < c.nodes.size(); k += 4) {
             float4 n3 = c.nodes[k + 3];
@@ -536,7 +545,8 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         (e = ctx->d_tri_obj.upload(tri_obj, s)) || (e = ctx->d_light_v.upload(light_v, s)) ||
         (e = ctx->d_light_cdf.upload(light_cdf, s)) || (e = ctx->d_gnodes.upload(global.nodes, s)) ||
         (e = ctx->d_gtris.upload(global.tris, s)) ||
-        (o.bvh_in_host_memory ? ((e = ctx->h_cell_nodes.upload(cell_nodes)) || (e = ctx->h_cell_tris.upload(cell_tris)))
+        ((o.bvh_in_host_memory || o.cell_cache_bytes > 0)
+             ? ((e = ctx->h_cell_nodes.upload(cell_nodes)) || (e = ctx->h_cell_tris.upload(cell_tris)))
                               : ((e = ctx->d_cell_nodes.upload(cell_nodes, s)) || (e = ctx->d_cell_tris.upload(cell_tris, s)))) ||
         (e = ctx->d_cell_root.upload(cell_root, s)) ||
         (any_film && ((e = ctx->d_nfilm.upload(nfilm, s)) || (e = ctx->d_film_n.upload(FN, s)) ||
@@ -585,12 +595,34 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
 #endif
     g.n_oct = (SDDM_MAX_SUBBINS >= 64 && 128 * g.n_cells <= kMaxBins) ? 64 : (SDDM_MAX_SUBBINS >= 8 && 16 * g.n_cells <= kMaxBins) ? 8 : 1;
     g.n_bins = 2 * g.n_cells * g.n_oct;
-    if (o.bvh_in_host_memory) {
+    ctx->cache.release();
+    if (o.cell_cache_bytes > 0) {
+        // subdomains loaded into a device cache of that many bytes as their queues fill
+        ctx->d_cell_nodes.release();
+        ctx->d_cell_tris.release();
+        const int rc = ctx->cache.init(static_cast<const float4 *>(ctx->h_cell_nodes.h),
+                                       static_cast<const float4 *>(ctx->h_cell_tris.h), c_node_base, c_node_cnt,
+                                       c_tri_base, c_tri_cnt, o.cell_cache_bytes, ctx->d_cell_root.as<int>(),
+                                       g.n_bins);
+        if (rc != SDDM_OK) {
+            ctx->cache.release();
+            ctx->built = false;
+            return rc;
+        }
+        g.nodes = ctx->cache.d_cache;
+        g.tris = ctx->cache.d_cache;
+        g.node_cap = ctx->cache.plan.budget / 64;
+        g.tri_cap = ctx->cache.plan.budget / 48;
+    } else if (o.bvh_in_host_memory) {
+        g.node_cap = (int64_t)cell_nodes.size() / 4;
+        g.tri_cap = (int64_t)cell_tris.size() / 3;
         g.nodes = ctx->h_cell_nodes.as<float4>();
         g.tris = ctx->h_cell_tris.as<float4>();
         ctx->d_cell_nodes.release();
         ctx->d_cell_tris.release();
     } else {
+        g.node_cap = (int64_t)cell_nodes.size() / 4;
+        g.tri_cap = (int64_t)cell_tris.size() / 3;
         g.nodes = ctx->d_cell_nodes.as<float4>();
         g.tris = ctx->d_cell_tris.as<float4>();
         ctx->h_cell_nodes.release();
@@ -866,6 +898,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
                 run.mlp_dmin = mlp_dmin;
                 run.mlp_dmax = mlp_dmax;
                 run.probe_key = d[0].seed ^ 0x9e3779b9u;
+                run.cache = ctx->opts.cell_cache_bytes > 0 ? &ctx->cache : nullptr;
                 int rc2 = ctx->pm_view.on ? ddm_trace_chunk_pm(run, ctx->pm_view, ctx->pmc_view, ctx->ddm_buf, s)
                                           : ddm_trace_chunk(run, ctx->ddm_buf, s);
                 if (rc2 != SDDM_OK) return rc2;
@@ -888,7 +921,10 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         }
         return SDDM_OK;
     };
-    const bool graphable = ctx->graphs_enabled && !count_trav && !time_trace && !ctx->pm_view.on;
+    // the subdomain cache plans each wave on the host from the rays waiting per cell: not capturable
+    const bool graphable = ctx->graphs_enabled && !count_trav && !time_trace && !ctx->pm_view.on &&
+                           ctx->opts.cell_cache_bytes == 0;
+    ctx->cache.loads = ctx->cache.plan.hits = ctx->cache.bytes_loaded = ctx->cache.groups = 0;
     std::string key;
     if (graphable) {
         char buf[256];
@@ -960,6 +996,9 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         st->crossings = (int64_t)cnt[3];
         st->mlp_fallbacks = (int64_t)cnt[4];
         st->mlp_batches = (int64_t)cnt[8];
+        st->cache_loads = ctx->cache.loads;
+        st->cache_hits = ctx->cache.plan.hits;
+        st->cache_bytes_loaded = ctx->cache.bytes_loaded;
         st->gpu_ms = ms;
         st->kernel_launches = launches;
         st->node_visits = count_trav ? (int64_t)cnt[5] : 0;
@@ -989,6 +1028,8 @@ int sddm_render_photon_map(sddm_ctx *ctx, const sddm_render_desc *d, int64_t n_p
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: radius must be positive and finite");
     if (!(caustic_radius >= 0.0f) || !std::isfinite(caustic_radius))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: caustic_radius must be finite and >= 0");
+    if (ctx->opts.cell_cache_bytes > 0 && d->method == SDDM_METHOD_DDM)
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_render_photon_map: not with the subdomain cache (cell_cache_bytes)");
     const bool two_maps = caustic_radius > 0.0f;
     const int64_t per = d->max_depth - 1;
     if (n_photons < 0 || n_photons > ((int64_t)1 << 31) / per - 1)
@@ -1182,6 +1223,9 @@ int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d,
         tot.glass_queries += sj.glass_queries;
         tot.mlp_fallbacks += sj.mlp_fallbacks;
         tot.mlp_batches += sj.mlp_batches;
+        tot.cache_loads += sj.cache_loads;
+        tot.cache_hits += sj.cache_hits;
+        tot.cache_bytes_loaded += sj.cache_bytes_loaded;
         tot.gpu_ms += sj.gpu_ms;
         tot.kernel_launches += sj.kernel_launches + (j > 1 ? 1 : 0);
         ptot.photons += pj.photons;

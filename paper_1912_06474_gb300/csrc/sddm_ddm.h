@@ -18,6 +18,8 @@
 
 namespace sddm {
 
+struct CellCache;
+
 constexpr int kMaxCells = 2048;
 constexpr int kMaxBins = 2 * kMaxCells;   // queue sort key: (cell, ray kind[, direction octant])
 
@@ -32,6 +34,7 @@ struct DDMScene {
     const float4 *nodes;  // all cells' BVH nodes
     const float4 *tris;   // all cells' triangle references
     const int *root;      // [n_cells] root node of each cell
+    int64_t node_cap, tri_cap;   // node and triangle records addressable from nodes / tris
     // per cell: bounding planes (x-, x+, y-, y+), (z-, z+, -, -) and the
     // neighbours across those faces (-1 outside the grid), 2 entries each
     const float4 *cell_planes;
@@ -104,6 +107,8 @@ struct DDMRun {
     const float *mlp_params;
     float mlp_dmin, mlp_dmax;
     uint32_t probe_key;
+    // subdomain BVHs cached in device memory under a byte budget (NULL: all resident)
+    CellCache *cache = nullptr;
 };
 
 // Run every bounce of one chunk of paths (asynchronous on `stream`).

@@ -51,7 +51,7 @@ struct DevScene {
     const float *mat_c;       // [n_mat][L] -   | - | dalpha
     const float *mat_thick;   // [n_mat]
     // thin-film coatings of glass materials (both faces; NULL when no material has one)
-    const int *mat_nfilm;     // [n_mat] films per face, 0..4
+    const int *mat_nfilm;     // [n_mat] films per face, 0..SDDM_MAX_FILMS
     const float *film_n;      // [n_mat][4][L] real index
     const float *film_k;      // [n_mat][4][L] extinction at s = 0
     const float *film_dk;     // [n_mat][4][L] extinction added at s = 1

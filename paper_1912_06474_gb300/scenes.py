@@ -154,7 +154,7 @@ class Material:
     s_default: float = 0.0
     Le: Optional[np.ndarray] = None           # emitted radiance [L]
     name: str = ""
-    # glass coated on both faces with thin films (up to 4 per face), outermost
+    # glass coated on both faces with thin films (up to 10 per face), outermost
     # first: each a dict n [L], k [L] (extinction at s = 0), dk [L] (added at
     # s = 1), t_nm (thickness, nm)
     layers: Optional[list] = None
@@ -323,12 +323,14 @@ def _glass(rng, lam, thickness_m, s, name):
                     thickness_m=thickness_m, s_default=s, name=name)
 
 
-def electrochromic_glass(rng, lam, thickness_m=0.006, s=0.5, name="electrochromic") -> Material:
-    """Clear glass substrate coated on both faces with a 3-film electrochromic
-    stack, outermost first: transparent conductor (~150 nm, n ~ 1.9), the
-    electrochromic film (~350 nm, n ~ 2.1) whose extinction rises with the
-    coloration state s mostly toward the red, transparent conductor (~150 nm).
-    Seeded smooth curves; the substrate's own absorption does not depend on s."""
+def electrochromic_glass(rng, lam, thickness_m=0.006, s=0.5, name="electrochromic", n_films=3) -> Material:
+    """Clear glass substrate coated on both faces with an electrochromic stack
+    of n_films films, outermost first, alternating transparent conductor
+    (~150 nm, n ~ 1.9) and electrochromic film (~350 nm, n ~ 2.1, extinction
+    rising with the coloration state s mostly toward the red); the default 3
+    films are conductor, electrochromic film, conductor, and a single film is
+    the electrochromic one. Seeded smooth curves; the substrate's own
+    absorption does not depend on s."""
     lam = np.asarray(lam, np.float64)
     x = (lam - 380.0) / 400.0
     tco_n = (1.95 - 0.15 * x + rng.uniform(-0.03, 0.03)).astype(np.float32)
@@ -338,9 +340,12 @@ def electrochromic_glass(rng, lam, thickness_m=0.006, s=0.5, name="electrochromi
     mu, sig = rng.uniform(650.0, 780.0), rng.uniform(120.0, 200.0)
     ec_dk = (rng.uniform(0.08, 0.15) * np.exp(-0.5 * ((lam - mu) / sig) ** 2)).astype(np.float32)
     zero = np.zeros_like(x, dtype=np.float32)
-    layers = [dict(n=tco_n, k=tco_k, dk=zero, t_nm=float(rng.uniform(130, 170))),
-              dict(n=ec_n, k=ec_k, dk=ec_dk, t_nm=float(rng.uniform(300, 400))),
-              dict(n=tco_n, k=tco_k, dk=zero, t_nm=float(rng.uniform(130, 170)))]
+    layers = []
+    for j in range(n_films):
+        if n_films > 1 and j % 2 == 0:
+            layers.append(dict(n=tco_n, k=tco_k, dk=zero, t_nm=float(rng.uniform(130, 170))))
+        else:
+            layers.append(dict(n=ec_n, k=ec_k, dk=ec_dk, t_nm=float(rng.uniform(300, 400))))
     return Material(GLASS, n=cauchy_index(lam), alpha_clear=absorption_curve(rng, lam, 0.0, 5.0),
                     dalpha=np.zeros(len(lam), np.float32), thickness_m=thickness_m, s_default=s, name=name,
                     layers=layers)
@@ -355,7 +360,8 @@ def _metal(rng, lam, name):
 # Scenes
 # --------------------------------------------------------------------------
 def tiny_room(L: int = 16, seed: int = 0, s: float = 0.5, light_scale: float = 10.0,
-              with_pane: bool = True, pane_override: Optional[Material] = None, coated: bool = False) -> Scene:
+              with_pane: bool = True, pane_override: Optional[Material] = None, coated: bool = False,
+              n_films: int = 3) -> Scene:
     """5x4x3 m room, freestanding 1x1 m pane 4 mm thick, 0.8 m cube, ceiling light.
 
     36 triangles of geometry plus the 2-triangle light quad. z is up, the
@@ -368,7 +374,7 @@ def tiny_room(L: int = 16, seed: int = 0, s: float = 0.5, light_scale: float = 1
         Material(LAMBERT, rho=smooth_curve(rng, lam, 0.05, 0.9), name="floor"),
         Material(LAMBERT, rho=smooth_curve(rng, lam, 0.05, 0.9), name="cube"),
         pane_override if pane_override is not None else (
-            electrochromic_glass(np.random.default_rng(seed + 77), lam, 0.004, s, "pane") if coated
+            electrochromic_glass(np.random.default_rng(seed + 77), lam, 0.004, s, "pane", n_films) if coated
             else _glass(rng, lam, 0.004, s, "pane")),
         Material(EMITTER, Le=planck_normalised(lam, 5800.0, light_scale), name="light"),
     ]

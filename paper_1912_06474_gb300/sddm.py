@@ -45,7 +45,7 @@ class SddmError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("grid", C.c_int * 3), ("leaf_size", C.c_int), ("sah_bins", C.c_int),
                 ("queue_capacity", C.c_int64), ("blocks_per_sm", C.c_int), ("paths_in_flight", C.c_int64),
-                ("bvh_in_host_memory", C.c_int)]
+                ("bvh_in_host_memory", C.c_int), ("cell_cache_bytes", C.c_int64)]
 
 
 class MlpTrainOpts(C.Structure):
@@ -78,7 +78,8 @@ class Stats(C.Structure):
                 ("crossings", C.c_int64), ("glass_queries", C.c_int64), ("mlp_fallbacks", C.c_int64),
                 ("gpu_ms", C.c_double), ("kernel_launches", C.c_int64), ("trace_ms", C.c_double),
                 ("trace_launches", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
-                ("ray_visits", C.c_int64), ("mlp_batches", C.c_int64)]
+                ("ray_visits", C.c_int64), ("mlp_batches", C.c_int64), ("cache_loads", C.c_int64),
+                ("cache_hits", C.c_int64), ("cache_bytes_loaded", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -229,9 +230,9 @@ class Context:
         self.n_mat = len(scene.materials)
 
     def build(self, grid=(1, 1, 1), leaf_size=4, sah_bins=16, queue_capacity=0, blocks_per_sm=0,
-              paths_in_flight=0, bvh_in_host_memory=False):
+              paths_in_flight=0, bvh_in_host_memory=False, cell_cache_bytes=0):
         o = BuildOpts((C.c_int * 3)(*grid), leaf_size, sah_bins, queue_capacity, blocks_per_sm,
-                      paths_in_flight, 1 if bvh_in_host_memory else 0)
+                      paths_in_flight, 1 if bvh_in_host_memory else 0, int(cell_cache_bytes))
         _check(lib.sddm_build(self._h, C.byref(o)))
         self.build_opts = o
 

@@ -94,6 +94,18 @@ int main() {
     for (int i = 0; i < nt; ++i) wrong += seen[i] != 1;
     std::printf("triangles referenced once: %d of %d wrong, oversized leaves %d\n", wrong, nt, bad_leaf);
     if (wrong || bad_leaf) return 1;
+    // packed triangles carry their three vertices bit for bit (the watertight
+    // test needs the endpoints a shared edge has in both of its triangles)
+    int moved = 0;
+    for (size_t k = 0; k < b.tris.size(); k += 3) {
+        const BuildTri &t = tris[as_int(b.tris[k].w)];
+        for (int v = 0; v < 3; ++v) {
+            const float4 &p = b.tris[k + v];
+            moved += p.x != t.v[v][0] || p.y != t.v[v][1] || p.z != t.v[v][2];
+        }
+    }
+    std::printf("packed vertices differing from the input: %d\n", moved);
+    if (moved) return 1;
 
     // 2. closest hits through the packed BVH equal brute force
     int mism = 0;

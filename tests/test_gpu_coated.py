@@ -121,3 +121,54 @@ def test_surrogate_on_coated_glass(oracle_mod, sddm, room):
     print("tiny room coated, 512^2 x 16 spp: exact stack %.2f ms, surrogate %.2f ms (%.2fx)"
           % (ms["exact"], ms["mlp"], ms["exact"] / ms["mlp"]))
     ctx.close()
+
+
+def test_surrogate_gain_against_film_count(sddm):
+    """What the trained network gains over the exact stack as the stack grows:
+    4M (cos, bin, s) rows of a pane coated with 1, 3, 6 and 10 films, device
+    time of the exact transfer-matrix stack against the network (alone, and
+    with its probe and exact fallback), the network retrained on each stack.
+    The exact model's cost grows with the films and the network's does not;
+    the film count where the network first wins is printed and checked against
+    the count this GPU gives (none up to 10: the exact stack stays cheaper)."""
+    films = (1, 3, 6, 10)
+    res = {}
+    for J in films:
+        room = scenes.tiny_room(L=41, seed=0, coated=True, n_films=J)
+        ctx = sddm.Context(0)
+        try:
+            ctx.set_scene(room)
+            ctx.build(grid=(1, 1, 1))
+            g = room.glass_materials()[0]
+            rep = ctx.mlp_train(g, seed=7)
+            c, b, s, d = _rows(room, g, 1 << 22, 2)
+            args = [torch.from_numpy(a).cuda() for a in (c, b, s, d)]
+            t = {}
+            out = {}
+            for mode in ("exact", "mlp_raw", "mlp"):
+                ctx.glass_eval(g, *args, mode=mode)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record()
+                for _ in range(5):
+                    out[mode] = ctx.glass_eval(g, *args, mode=mode)
+                ev[1].record()
+                torch.cuda.synchronize()
+                t[mode] = ev[0].elapsed_time(ev[1]) / 5
+            dT = (out["mlp"][1] - out["exact"][1]).abs()
+            res[J] = t
+            print(f"{J:2d} films: exact {t['exact']:.3f} ms, network {t['mlp_raw']:.3f} ms, network with probe and "
+                  f"fallback {t['mlp']:.3f} ms; served |dT| mean {dT.mean().item():.2e} max {dT.max().item():.2e}; "
+                  f"training loss {rep['final_loss']:.1e}")
+            assert dT.mean().item() <= 1e-3
+        finally:
+            ctx.close()
+    # the exact stack's cost grows with the films, the network's stays flat
+    assert res[10]["exact"] > 3.0 * res[1]["exact"]
+    assert res[10]["mlp_raw"] < 1.5 * res[1]["mlp_raw"]
+    wins = [J for J in films if res[J]["mlp"] < res[J]["exact"]]
+    slope = (res[10]["exact"] - res[1]["exact"]) / 9.0
+    cross = 1 + (res[1]["mlp"] - res[1]["exact"]) / slope
+    print(f"network wins first at {wins[0] if wins else 'none of'} {films if not wins else ''} films; "
+          f"linear extrapolation of the exact cost reaches the network's at {cross:.1f} films")
+    assert not wins

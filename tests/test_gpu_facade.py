@@ -50,14 +50,20 @@ def test_facade_full_configuration_batched_surrogate(oracle_mod):
     """The facade workload at its full size, in one call: 16 renders of
     1920x1080 px at 64 spp, depth 8, 81 bins, DDM over 8x8x4 subdomains, the
     glass of all 8 panes (one set of curves, each pane its own s) served by one
-    trained surrogate with probe and exact fallback. Checked against the FP64
-    oracle on a seeded subset of 1024 pixels of every render: the relative
-    RMSE over all 16 subsets (16,384 pixels) estimates the batch's image
-    error and must be <= 1e-3. Per render the subset is a coarser estimate: a
-    rare sample that FP32 and FP64 route differently at some bounce (seen at
-    about one pixel in 10^4 here, in both the DDM and the megakernel, e.g. a
-    grazing hit among the furniture's thin triangles) weighs 1/1024 in a
-    subset but 1/2M in the image, so a render's subset may reach 2e-3."""
+    trained surrogate with probe and exact fallback; the same batch once more
+    with the exact slab. Both are checked against the FP64 oracle on a seeded
+    subset of 4096 pixels of every render (65,536 pixels):
+
+    * over all subsets the surrogate batch is within 1e-3 relative RMSE;
+    * the surrogate's own contribution, measured on every full image against
+      the exact-slab images (the two trace the same paths: the branch
+      probability does not depend on the glass model), is within 1e-3 per
+      render;
+    * per render, the subset error of the surrogate images exceeds 1e-3 only
+      where the exact-slab images' error on the same pixels does too: the
+      excess comes from a rare sample that FP32 and FP64 route differently,
+      which weighs 1/4096 in a subset and 1/2M in the image, not from the
+      surrogate."""
     from paper_1912_06474_gb300 import sddm
     sc = scenes.facade_room(L=81, seed=0)
     ctx = sddm.Context(0)
@@ -66,26 +72,35 @@ def test_facade_full_configuration_batched_surrogate(oracle_mod):
     rep = ctx.mlp_train(sc.glass_materials()[0], seed=7)
     specs = scenes.facade_renders(sc)   # 16 x 1920x1080 x 64 spp, depth 8
     assert len(specs) == 16 and specs[0].n_paths == 1920 * 1080 * 64
-    t0 = time.perf_counter()
-    imgs, st = ctx.render(specs, method="ddm", bsdf="mlp")
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    seg = st["segments_ext"] + st["segments_shadow"]
-    print(f"facade full: surrogate loss {rep['final_loss']:.2e}; {st['paths']} paths, {seg} segments, "
-          f"{st['gpu_ms']:.0f} ms device ({seg / (st['gpu_ms'] * 1e3):.0f} Mseg/s), {wall:.1f} s wall, "
-          f"{st['mlp_fallbacks']} fallback batches of {st['glass_queries']} glass queries")
+    imgs = {}
+    for bsdf in ("mlp", "exact"):
+        t0 = time.perf_counter()
+        out, st = ctx.render(specs, method="ddm", bsdf=bsdf)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        seg = st["segments_ext"] + st["segments_shadow"]
+        print(f"facade full, {bsdf}: {st['paths']} paths, {seg} segments, {st['gpu_ms']:.0f} ms device "
+              f"({seg / (st['gpu_ms'] * 1e3):.0f} Mseg/s), {wall:.1f} s wall; surrogate batches "
+              f"{st['mlp_batches']}, fallbacks {st['mlp_fallbacks']}")
+        imgs[bsdf] = [im.cpu().numpy().reshape(-1, 3) for im in out]
+        del out
+    print(f"surrogate loss {rep['final_loss']:.2e}")
     orc = oracle_mod.Oracle(sc)
-    errs, got_all, ref_all = [], [], []
+    surr_full, e_mlp, e_exact, got_all, ref_all = [], [], [], [], []
     for r, sp in enumerate(specs):
-        pix = scenes.pixel_subset(sp.width, sp.height, 1024, seed=100 + r)
+        surr_full.append(rel_rmse(imgs["mlp"][r], imgs["exact"][r]))
+        pix = scenes.pixel_subset(sp.width, sp.height, 4096, seed=100 + r)
         ref = orc.render_pixels(sp, pix)["xyz"]
-        got = imgs[r].cpu().numpy().reshape(-1, 3)[pix]
-        errs.append(rel_rmse(got, ref))
-        got_all.append(got)
+        e_mlp.append(rel_rmse(imgs["mlp"][r][pix], ref))
+        e_exact.append(rel_rmse(imgs["exact"][r][pix], ref))
+        got_all.append(imgs["mlp"][r][pix])
         ref_all.append(ref)
+        print(f"render {r}: surrogate vs exact (full image) {surr_full[-1]:.2e}; vs oracle on 4096 px: "
+              f"surrogate {e_mlp[-1]:.2e}, exact slab {e_exact[-1]:.2e}")
     pooled = rel_rmse(np.concatenate(got_all), np.concatenate(ref_all))
-    print("rel-RMSE over all subsets %.2e; per render max %.2e mean %.2e" % (pooled, max(errs),
-                                                                           sum(errs) / len(errs)))
+    print(f"surrogate batch vs oracle over all 65,536 sampled pixels: {pooled:.2e}")
     assert pooled <= 1e-3
-    assert max(errs) <= 2e-3
+    assert max(surr_full) <= 1e-3
+    for r in range(len(specs)):
+        assert e_mlp[r] <= 1e-3 or e_exact[r] >= 0.9 * e_mlp[r], (r, e_mlp[r], e_exact[r])
     ctx.close()

@@ -74,7 +74,10 @@ def test_furnace_photon_map(oracle_mod, sddm, method, grid):
     n = 200000
     img, ref, pst, n_ref = _both(oracle_mod, sddm, sc, spec, n, 0.1, method, grid)
     # every photon is stored once per hit from its second hit on, none escapes
-    # (in FP64; an FP32 ray may slip through a box corner now and then)
+    # in FP64; in FP32 two of the 600,000 deposits go missing. The triangle
+    # test is watertight (no ray passes between the triangles of a shared
+    # edge), and the count did not change when it replaced Moller-Trumbore, so
+    # these two are not rays slipping through an edge of the box
     assert n_ref == n * (D - 2)
     assert n * (D - 2) - 1e-4 * n <= pst["stored"] <= n * (D - 2)
     assert rel_rmse(img, ref) <= 1e-3

@@ -180,3 +180,96 @@ def test_shadow_glass_crossings(oracle_mod, brute):
     orc = oracle_mod.Oracle(_glass_slabs_scene(2))
     occ, cr = orc.shadow([5, 0, 0], -d, 20.0, brute_force=brute)
     assert not occ and len(cr) == 2
+
+
+def test_watertight_equals_moller_trumbore_away_from_edges(oracle_mod):
+    """The FP64 watertight test (Woop, Benthin, Wald 2013) agrees with the
+    Moller-Trumbore test the oracle renders with wherever the ray is clearly
+    inside or clearly outside the triangle: the same hit decision, and the
+    same distance to 1e-12."""
+    rng = np.random.default_rng(31)
+    agree = hits = 0
+    for _ in range(20000):
+        tri = rng.uniform(-1, 1, (3, 3))
+        o = rng.uniform(-2, 2, 3)
+        d = tri.mean(0) + rng.normal(0, 0.6, 3) - o
+        d /= np.linalg.norm(d)
+        mh, mt, (u, w) = oracle_mod.moller_trumbore(tri, o, d)
+        if not np.isfinite(mt) or min(abs(u), abs(w), abs(1 - u - w)) < 1e-9:
+            continue
+        wh, wt = oracle_mod.watertight(tri, o, d)
+        assert wh == mh, (tri, o, d)
+        if wh:
+            hits += 1
+            assert abs(wt - mt) <= 1e-12 * max(1.0, abs(mt))
+        agree += 1
+    assert agree > 19000 and hits > 2000
+
+
+def _icosphere(levels):
+    """Closed triangle mesh of the unit sphere with shared vertices."""
+    t = (1 + 5 ** 0.5) / 2
+    V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    V = [np.array(v, float) / np.linalg.norm(v) for v in V]
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11),
+         (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(levels):
+        mid = {}
+
+        def m(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                p = V[a] + V[b]
+                V.append(p / np.linalg.norm(p))
+                mid[k] = len(V) - 1
+            return mid[k]
+        F = [f for a, b, c in F for f in ((a, m(a, b), m(c, a)), (b, m(b, c), m(a, b)), (c, m(c, a), m(b, c)),
+                                            (m(a, b), m(b, c), m(c, a)))]
+    return np.array(V), np.array(F)
+
+
+def test_watertight_closed_mesh_has_no_cracks(oracle_mod):
+    """Rays from inside a closed mesh aimed exactly at its vertices, at points
+    on its edges and at random points never miss every triangle with the
+    watertight test: a shared edge or vertex belongs to at least one of the
+    triangles around it."""
+    V, F = _icosphere(2)
+    rng = np.random.default_rng(5)
+    E = {tuple(sorted((f[i], f[(i + 1) % 3]))) for f in F for i in range(3)}
+    targets = [V[i] for i in range(len(V))]
+    for a, b in sorted(E):
+        for s in (0.5, rng.uniform(0.01, 0.99)):
+            targets.append(V[a] + s * (V[b] - V[a]))
+    targets += list(rng.normal(0, 1, (200, 3)))
+    mt_missed = 0
+    for origin in (np.zeros(3), np.array([0.1, -0.2, 0.15]), np.array([1e-3, 3e-3, -2e-3])):
+        for x in targets:
+            d = x - origin
+            d /= np.linalg.norm(d)
+            n_wt = sum(oracle_mod.watertight(V[f], origin, d)[1] > 0 for f in F)
+            assert n_wt >= 1, (origin, x)
+            n_mt = sum(oracle_mod.moller_trumbore(V[f], origin, d)[0] and
+                       oracle_mod.moller_trumbore(V[f], origin, d)[1] > 0 for f in F)
+            mt_missed += n_mt == 0
+    print(f"rays through vertices and edges that Moller-Trumbore lets through: {mt_missed}")
+
+
+def test_watertight_exact_shared_edge(oracle_mod):
+    """A unit square split along its diagonal into two triangles, rays along
+    +z and -z through points of the diagonal (and through the shared corners):
+    the edge functions vanish exactly there, and the watertight test must
+    count the point as inside both triangles (a boundary point belongs to
+    the triangle), so the ray is never lost between them."""
+    t1 = np.array([[0, 0, 1], [1, 0, 1], [1, 1, 1]], float)
+    t2 = np.array([[0, 0, 1], [1, 1, 1], [0, 1, 1]], float)
+    for k in range(0, 9):
+        p = k / 8.0
+        for dz in (1.0, -1.0):
+            o = np.array([p, p, 1.0 - 2.0 * dz])
+            d = np.array([0.0, 0.0, dz])
+            h1, ta = oracle_mod.watertight(t1, o, d)
+            h2, tb = oracle_mod.watertight(t2, o, d)
+            assert h1 and h2, (p, dz)
+            assert ta == tb == 2.0
