@@ -80,6 +80,11 @@ typedef struct {
                                  per wave). Images are bit-identical to the all-resident build. Must hold the
                                  largest subdomain (else SDDM_ERR_INVALID_ARG); excludes bvh_in_host_memory.
                                  0 = all subdomains resident in HBM */
+    int continue_cells;       /* 1: a ray that leaves its subdomain without a hit is carried on by the same
+                                 thread into the neighbour's BVH within the wave (one wave per bounce, no
+                                 hand-off through the neighbour's queue); results are identical. 0 = the
+                                 ray record is handed to the neighbour's queue for the next wave (Sec. 5's
+                                 interface exchange). Not with cell_cache_bytes */
 } sddm_build_opts;
 
 typedef struct {

@@ -60,10 +60,10 @@ typedef struct {
     const uint32_t *obj_id;   /* [nt] */
     /* thin-film coating of glass materials (both faces); NULL = none */
     const int32_t *mat_nlayers; /* [n_mat] films per face, 0..10 */
-    const float *layer_n;     /* [n_mat][4][L] film real index */
-    const float *layer_k;     /* [n_mat][4][L] film extinction at s = 0 */
-    const float *layer_dk;    /* [n_mat][4][L] extinction added at s = 1 (k = k + s dk) */
-    const float *layer_t;     /* [n_mat][4] film thickness, nm */
+    const float *layer_n;     /* [n_mat][ORC_MAX_FILMS][L] film real index */
+    const float *layer_k;     /* [n_mat][ORC_MAX_FILMS][L] film extinction at s = 0 */
+    const float *layer_dk;    /* [n_mat][ORC_MAX_FILMS][L] extinction added at s = 1 (k = k + s dk) */
+    const float *layer_t;     /* [n_mat][ORC_MAX_FILMS] film thickness, nm */
 } orc_scene_desc;
 
 typedef struct {

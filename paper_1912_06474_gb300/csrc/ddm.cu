@@ -977,7 +977,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
 
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
     const unsigned scatter_blocks = whole_waves(k_scatter, 256, 0, sm, (unsigned)sm * 4);
-    const int waves = std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
+    const int waves = run.g.continue_cells ? 1 : std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
     const size_t ctl_bytes = 32 + 4 * (size_t)nb;
     const unsigned cont_blocks = whole_waves(k_shade_continue, 256, sizeof(int) * (size_t)nb, sm, path_blocks);
     // the glass count and gather passes share one partition of the path slots

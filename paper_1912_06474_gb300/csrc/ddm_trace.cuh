@@ -354,14 +354,34 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                     done = true;
                 }
             }
-            if (!done) {
-                want = true;
-                o0 = make_float4(ray.o.x, ray.o.y, ray.o.z, fmaxf(t_cur, t_exit));
-                o1 = make_float4(ray.d.x, ray.d.y, ray.d.z, t_max);
-                o2 = make_int4(q, excl, rfl_next, next);
+            if (!done && a.g.continue_cells) {
+                // the lane carries the ray on into the neighbouring cell's
+                // BVH, with the same record it would have handed over
+                const int cell = next;
+                t_cur = fmaxf(t_cur, t_exit);
+                t_exit = cell_exit(g, cell, ray, next);
+                tmin = fmaxf(0.0f, t_cur - g.eps);
+                node = __ldg(g.root + cell);
+                sp = 0;
+                best = -1;
+                occ = false;
+                rfl = rfl_next;
+                n_prev = cr.n;
+                tw = (rfl & kRayShadow) ? fminf(t_exit + g.eps, t_max) : t_exit + g.eps;
                 ++n_cross;
+                ++n_vis;
+                done = true;
+                fin = false;
+            } else {
+                if (!done) {
+                    want = true;
+                    o0 = make_float4(ray.o.x, ray.o.y, ray.o.z, fmaxf(t_cur, t_exit));
+                    o1 = make_float4(ray.d.x, ray.d.y, ray.d.z, t_max);
+                    o2 = make_int4(q, excl, rfl_next, next);
+                    ++n_cross;
+                }
+                idx = -1;
             }
-            idx = -1;
         }
         if (want && a.last_wave) {   // cannot happen: each wave moves a ray forward along one axis
             atomicCAS(a.err, 0, 4);

@@ -80,22 +80,6 @@ __device__ __forceinline__ void warp_gemm(float acc[8][4], const __nv_bfloat16 *
     }
 }
 
-// acc (16 x 64) += A (16 x 64) * W^T with A already in registers as mma
-// A fragments: fa[kk] holds rows g, g + 8 and columns 16 kk + 2t + {0, 1, 8, 9}
-// -- exactly the accumulator layout of the previous layer (see pack_afrag).
-__device__ __forceinline__ void warp_gemm_reg(float acc[8][4], const uint32_t fa[4][4], const __nv_bfloat16 *W,
-                                              int lane) {
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t *bp = reinterpret_cast<const uint32_t *>(W + (8 * j + g) * LD + 16 * kk + 2 * t);
-            mma16816(acc[j], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], bp[0], bp[4]);
-        }
-    }
-}
-
 // Activations h (accumulator layout: h[j][0..1] row g, cols 8j + 2t + {0,1};
 // h[j][2..3] row g + 8) as BF16 A fragments of the next layer's mma.
 __device__ __forceinline__ void pack_afrag(const float h[8][4], uint32_t fa[4][4]) {
@@ -138,10 +122,23 @@ __device__ __forceinline__ void features(float c, float lam, float s, float alph
 // produces h = z / 2 directly (halving is exact in binary floating point, so
 // the activations are bit for bit those of the unscaled layer), and
 // SiLU(z) = h + h tanh(h) costs one SFU operation and one FMA.
-struct InferSmem {
+//
+// All four layers run on the tensor cores (m16n8k16, BF16 operands, FP32
+// accumulation):
+//  * layer 1 (K = 4) as one K = 16 step whose A row is [x_hi(4) | x_lo(4) |
+//    1 | 1 | 0 ...] and whose B row for output n is [W1n(4) | W1n(4) | b_hi |
+//    b_lo | 0 ...]: each input split into two BF16 parts and the bias into two,
+//    so the products keep 16 bits of the FP32 inputs and bias;
+//  * layers 2 and 3 (64 x 64) as four K steps;
+//  * layer 4 (N = 2) as an N = 8 tile whose rows 2..7 are zero.
+// B fragments come from shared memory by ldmatrix, four 8x8 blocks at a time.
+constexpr int LD1 = 24;   // layer-1 B rows: 16 used, stride 48 B (16-byte aligned, conflict-free)
+struct alignas(16) InferSmem {   // 16-byte rows for ldmatrix
+    __nv_bfloat16 w1[H * LD1];              // [64][16]: W1 / 2 twice, b1 / 2 as hi + lo
     __nv_bfloat16 w2[H * LD], w3[H * LD];   // W / 2
-    float w1[H * 4], b1[H], b2[H], b3[H];   // W1 / 2, b / 2
-    float w4[2 * H], b4[2];
+    __nv_bfloat16 w4[8 * LD];               // rows 0, 1: W4; rows 2..7: 0
+    float b2[H], b3[H];                     // b / 2
+    float b4[2];
 };
 
 __device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
@@ -150,90 +147,136 @@ __device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
         s.w2[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W2 + i]);
         s.w3[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W3 + i]);
     }
-    for (int i = threadIdx.x; i < H * 4; i += blockDim.x) s.w1[i] = 0.5f * bf16r(p[OFF_W1 + i]);
-    for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) s.w4[i] = bf16r(p[OFF_W4 + i]);
+    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+        const int n = i >> 4, k = i & 15;
+        float v = 0.0f;
+        if (k < 8) {
+            v = 0.5f * bf16r(p[OFF_W1 + 4 * n + (k & 3)]);
+        } else if (k < 10) {
+            const float b = 0.5f * p[OFF_B1 + n];
+            const float hi = bf16r(b);
+            v = k == 8 ? hi : b - hi;
+        }
+        s.w1[n * LD1 + k] = __float2bfloat16_rn(v);
+    }
+    for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
+        const int n = i >> 6, k = i & 63;
+        s.w4[n * LD + k] = __float2bfloat16_rn(n < 2 ? p[OFF_W4 + H * n + k] : 0.0f);
+    }
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        s.b1[i] = 0.5f * p[OFF_B1 + i];
         s.b2[i] = 0.5f * p[OFF_B2 + i];
         s.b3[i] = 0.5f * p[OFF_B3 + i];
     }
     if (threadIdx.x < 2) s.b4[threadIdx.x] = p[OFF_B4 + threadIdx.x];
 }
 
+// Four 8x8 BF16 blocks from shared memory (ldmatrix): lane l gives the
+// address of row l & 7 of block l >> 3 and receives, of every block, row
+// (l >> 2), elements 2 (l & 3) and 2 (l & 3) + 1.
+__device__ __forceinline__ void ldmatrix_x4(const void *row_addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                            uint32_t &r3) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row_addr);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+// acc (16 x 64) += A (16 x 16 kk_steps) W^T, A in registers as mma A
+// fragments, W [64][ld] bf16 in shared memory (row n = output n). The B
+// fragments of output tiles j, j + 1 for one K step are one ldmatrix.x4.
+template <int KSTEPS>
+__device__ __forceinline__ void warp_gemm_ldm(float acc[8][4], const uint32_t fa[][4], const __nv_bfloat16 *W,
+                                              int ld, int lane) {
+    const int q = lane >> 3, r = lane & 7;
+#pragma unroll
+    for (int kk = 0; kk < KSTEPS; ++kk) {
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            uint32_t b0, b1, c0, c1;
+            ldmatrix_x4(W + (8 * (j + (q >> 1)) + r) * ld + 16 * kk + 8 * (q & 1), b0, b1, c0, c1);
+            mma16816(acc[j], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
+            mma16816(acc[j + 1], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], c0, c1);
+        }
+    }
+}
+
 // SiLU of z given h = z / 2.
 __device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
 
+// Layer-1 A fragment of rows g (xl) and g + 8 (xh): this lane's K columns
+// 2t, 2t + 1 (t = 0, 1: high parts of inputs 2t, 2t + 1; t = 2, 3: low parts
+// of inputs 2t - 4, 2t - 3) and 2t + 8, 2t + 9 (t = 0: the two bias ones).
+__device__ __forceinline__ void layer1_afrag(const float xl[4], const float xh[4], int t, uint32_t fa[4]) {
+    const int i = 2 * (t & 1);
+    const bool lo = t >= 2;
+    auto part = [&](float v) {
+        const float hi = bf16r(v);
+        return lo ? v - hi : hi;
+    };
+    fa[0] = pack_bf16x2(part(xl[i]), part(xl[i + 1]));
+    fa[1] = pack_bf16x2(part(xh[i]), part(xh[i + 1]));
+    const uint32_t ones = pack_bf16x2(1.0f, 1.0f);
+    fa[2] = t == 0 ? ones : 0u;
+    fa[3] = t == 0 ? ones : 0u;
+}
+
 // The network on the 16 rows of a warp tile; this thread supplies the inputs
-// of rows g and g + 8 and receives their outputs (the same on the 4 lanes of
-// a group). Activations stay in registers: each layer's accumulators are
-// packed into the next layer's BF16 A fragments.
+// of rows g and g + 8 and receives their outputs (on the lanes with t = 0).
+// Activations stay in registers: each layer's accumulators are packed into
+// the next layer's BF16 A fragments.
 __device__ void tile_forward(const InferSmem &s, const float xl[4], const float xh[4], int lane, float yl[2],
                              float yh[2]) {
     const int t = lane & 3;
-    float h[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int c = 8 * j + 2 * t + e;
-            float zl = s.b1[c], zh = s.b1[c];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                zl = fmaf(s.w1[4 * c + k], xl[k], zl);
-                zh = fmaf(s.w1[4 * c + k], xh[k], zh);
-            }
-            h[j][e] = silu_h(zl);
-            h[j][2 + e] = silu_h(zh);
-        }
-    }
-    uint32_t fa[4][4];
-    pack_afrag(h, fa);
     float acc[8][4];
+    uint32_t fa[4][4];
+    layer1_afrag(xl, xh, t, fa[0]);
     zero_acc(acc);
-    warp_gemm_reg(acc, fa, s.w2, lane);
+    warp_gemm_ldm<1>(acc, fa, s.w1, LD1, lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[j][e] = silu_h(acc[j][e]);
+    pack_afrag(acc, fa);
+    zero_acc(acc);
+    warp_gemm_ldm<4>(acc, fa, s.w2, LD, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
-        h[j][0] = silu_h(acc[j][0] + s.b2[c]);
-        h[j][1] = silu_h(acc[j][1] + s.b2[c + 1]);
-        h[j][2] = silu_h(acc[j][2] + s.b2[c]);
-        h[j][3] = silu_h(acc[j][3] + s.b2[c + 1]);
+        const float2 bb = *reinterpret_cast<const float2 *>(s.b2 + c);
+        acc[j][0] = silu_h(acc[j][0] + bb.x);
+        acc[j][1] = silu_h(acc[j][1] + bb.y);
+        acc[j][2] = silu_h(acc[j][2] + bb.x);
+        acc[j][3] = silu_h(acc[j][3] + bb.y);
     }
-    pack_afrag(h, fa);
+    pack_afrag(acc, fa);
     zero_acc(acc);
-    warp_gemm_reg(acc, fa, s.w3, lane);
+    warp_gemm_ldm<4>(acc, fa, s.w3, LD, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
-        acc[j][0] += s.b3[c];
-        acc[j][1] += s.b3[c + 1];
-        acc[j][2] += s.b3[c];
-        acc[j][3] += s.b3[c + 1];
+        const float2 bb = *reinterpret_cast<const float2 *>(s.b3 + c);
+        acc[j][0] = silu_h(acc[j][0] + bb.x);
+        acc[j][1] = silu_h(acc[j][1] + bb.y);
+        acc[j][2] = silu_h(acc[j][2] + bb.x);
+        acc[j][3] = silu_h(acc[j][3] + bb.y);
     }
-    float pl0 = 0.f, pl1 = 0.f, ph0 = 0.f, ph1 = 0.f;
+    pack_afrag(acc, fa);
+    // layer 4: one N = 8 tile, K = 64 in four steps (two ldmatrix.x4, each
+    // the B fragments of two K steps)
+    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int q = lane >> 3, r = lane & 7;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int c = 8 * j + 2 * t + e;
-            const float hl = bf16r(silu_h(acc[j][e])), hh = bf16r(silu_h(acc[j][2 + e]));
-            pl0 = fmaf(s.w4[c], hl, pl0);
-            pl1 = fmaf(s.w4[H + c], hl, pl1);
-            ph0 = fmaf(s.w4[c], hh, ph0);
-            ph1 = fmaf(s.w4[H + c], hh, ph1);
-        }
+    for (int kk = 0; kk < 4; kk += 2) {
+        uint32_t b0, b1, c0, c1;
+        ldmatrix_x4(s.w4 + r * LD + 16 * (kk + (q >> 1)) + 8 * (q & 1), b0, b1, c0, c1);
+        mma16816(o, fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
+        mma16816(o, fa[kk + 1][0], fa[kk + 1][1], fa[kk + 1][2], fa[kk + 1][3], c0, c1);
     }
-#pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {
-        pl0 += __shfl_xor_sync(kFull, pl0, o);
-        pl1 += __shfl_xor_sync(kFull, pl1, o);
-        ph0 += __shfl_xor_sync(kFull, ph0, o);
-        ph1 += __shfl_xor_sync(kFull, ph1, o);
-    }
-    yl[0] = pl0 + s.b4[0];
-    yl[1] = pl1 + s.b4[1];
-    yh[0] = ph0 + s.b4[0];
-    yh[1] = ph1 + s.b4[1];
+    // o[0..1]: row g, outputs 2t, 2t + 1; o[2..3]: row g + 8 (outputs 0, 1 on t = 0)
+    yl[0] = o[0] + s.b4[0];
+    yl[1] = o[1] + s.b4[1];
+    yh[0] = o[2] + s.b4[0];
+    yh[1] = o[3] + s.b4[1];
 }
 
 struct RowIn {
@@ -301,16 +344,22 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
 // Rows are taken 32 at a time by a warp (two 16-row tiles). One row of each
 // batch, chosen by Philox, is also evaluated exactly; if it is off by more
 // than 1e-3 in R or T, or if any row lies outside the trained box, the whole
-// batch is evaluated exactly instead.
+// batch is evaluated exactly instead. The probes of 32 batches run together,
+// one per lane, so that a probe costs one lane's share of an exact evaluation
+// rather than a whole warp's.
 #ifndef SDDM_MLP_MINB
 #define SDDM_MLP_MINB 4   // resident inference blocks per SM asked of the register allocator: 64 registers
                           // with ~100 B of spills, 32 warps per SM (+3% on the hotel bench against 80
                           // registers and 24 warps)
 #endif
+#ifndef SDDM_MLP_UNROLL_HALVES
+#define SDDM_MLP_UNROLL_HALVES 1   // the two 16-row tiles of a batch as one unrolled sequence
+#endif
 template <bool FILMS>
 __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
     __shared__ InferSmem s;
     __shared__ float2 out[8][32];
+    __shared__ float4 xin[8][32];   // per warp: the encoded inputs of its 32 rows
     load_infer_weights(s, a.params);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
@@ -328,10 +377,9 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
         n_batches = nq * nb;
     }
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t b_first = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;   // this warp's batches: b_first + k nwarps
     unsigned long long n_fb = 0;
-    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b < n_batches; b += nwarps) {
-        int64_t r0;
-        int nvalid;
+    auto batch_rows = [&](int64_t b, int64_t &r0, int &nvalid) {
         if (a.mode == 1) {
             const int64_t qi = b / nb;
             const int j = (int)(b - qi * nb);
@@ -341,49 +389,93 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
             r0 = b * 32;
             nvalid = total - r0 < 32 ? (int)(total - r0) : 32;
         }
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            if (half == 1 && nvalid <= 16) break;   // warp-uniform: no valid row in the second tile
-            RowIn il, ih;
-            const int kl = 16 * half + g, kh = kl + 8;
-            row_input(a, kl < nvalid ? r0 + kl : total, total, il);
-            row_input(a, kh < nvalid ? r0 + kh : total, total, ih);
-            float xl[4], xh[4], yl[2], yh[2];
-            features(il.c, il.lam, il.s, row_alpha_d<FILMS>(a.sc, il), xl);
-            features(ih.c, ih.lam, ih.s, row_alpha_d<FILMS>(a.sc, ih), xh);
-            tile_forward(s, xl, xh, lane, yl, yh);
-            if (t == 0) {
-                out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
-                out[w][kh] = make_float2(out_to_rt(yh[0]), out_to_rt(yh[1]));
-            }
+    };
+    auto store = [&](int64_t r, float2 y) {
+        if (a.mode == 0) {
+            a.R[r] = y.x;
+            a.T[r] = y.y;
+        } else {
+            a.results[r] = y;
         }
-        __syncwarp();
-        RowIn in;
-        const bool valid = row_input(a, lane < nvalid ? r0 + lane : total, total, in);
-        float2 y = out[w][lane];
-        const bool in_box = in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f &&
-                            in.s >= 0.0f && in.s <= 1.0f && in.d >= a.thick_min && in.d <= a.thick_max;
-        const bool box_ok = __all_sync(kFull, !valid || in_box);
-        const uint4 pr = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, kSlotProbe), a.probe_key,
-                                       0x50524f42u);
-        const int pick = (int)(pr.x % (uint32_t)nvalid);
+    };
+    // Rounds of up to 32 of the warp's batches: the network serves every row
+    // of them, then lane k probes batch k (one exact row each, all lanes at
+    // once), then every batch whose probe or trained box failed is evaluated
+    // exactly, row per lane.
+    for (int64_t k0 = 0; b_first + k0 * nwarps < n_batches; k0 += 32) {
+        unsigned box_bad = 0;
+        int n_round = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int64_t b = b_first + (k0 + k) * nwarps;
+            if (b >= n_batches) break;
+            ++n_round;
+            int64_t r0;
+            int nvalid;
+            batch_rows(b, r0, nvalid);
+            // each lane encodes the row of its own index once (the coating
+            // films' absorbance loop included); the tiles read their rows'
+            // inputs from the warp's staging row
+            {
+                RowIn in;
+                row_input(a, lane < nvalid ? r0 + lane : total, total, in);
+                float xr[4];
+                features(in.c, in.lam, in.s, row_alpha_d<FILMS>(a.sc, in), xr);
+                xin[w][lane] = make_float4(xr[0], xr[1], xr[2], xr[3]);
+            }
+            __syncwarp();
+#if SDDM_MLP_UNROLL_HALVES
+#pragma unroll
+#else
+#pragma unroll 1
+#endif
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && nvalid <= 16) break;   // warp-uniform: no valid row in the second tile
+                const int kl = 16 * half + g, kh = kl + 8;
+                float yl[2], yh[2];
+                const float4 ql = xin[w][kl], qh = xin[w][kh];
+                const float xl[4] = {ql.x, ql.y, ql.z, ql.w}, xh[4] = {qh.x, qh.y, qh.z, qh.w};
+                tile_forward(s, xl, xh, lane, yl, yh);
+                if (t == 0) {
+                    out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
+                    out[w][kh] = make_float2(out_to_rt(yh[0]), out_to_rt(yh[1]));
+                }
+            }
+            __syncwarp();
+            RowIn in;
+            const bool valid = row_input(a, lane < nvalid ? r0 + lane : total, total, in);
+            const bool in_box = in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f &&
+                                in.s >= 0.0f && in.s <= 1.0f && in.d >= a.thick_min && in.d <= a.thick_max;
+            if (!__all_sync(kFull, !valid || in_box)) box_bad |= 1u << k;
+            if (valid) store(r0 + lane, out[w][lane]);
+            __syncwarp();
+        }
+        if (a.raw) continue;
+        // probes: lane k takes the Philox-chosen row of batch k of the round
         int bad = 0;
-        if (lane == pick) {
+        if (lane < n_round) {
+            const int64_t b = b_first + (k0 + lane) * nwarps;
+            int64_t r0;
+            int nvalid;
+            batch_rows(b, r0, nvalid);
+            const uint4 pr = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, kSlotProbe),
+                                           a.probe_key, 0x50524f42u);
+            const int64_t r = r0 + (int)(pr.x % (uint32_t)nvalid);
+            RowIn in;
+            row_input(a, r, total, in);
             const float2 e = exact_row<FILMS>(a, in);
+            const float2 y = a.mode == 0 ? make_float2(a.R[r], a.T[r]) : a.results[r];
             bad = fabsf(e.x - y.x) > kMlpProbeTol || fabsf(e.y - y.y) > kMlpProbeTol;
         }
-        bad = __shfl_sync(kFull, bad, pick);
-        if (!a.raw && (!box_ok || bad)) {
-            if (valid) y = exact_row<FILMS>(a, in);
+        unsigned fall = __ballot_sync(kFull, bad) | box_bad;
+        while (fall) {
+            const int k = __ffs(fall) - 1;
+            fall &= fall - 1;
+            int64_t r0;
+            int nvalid;
+            batch_rows(b_first + (k0 + k) * nwarps, r0, nvalid);
+            RowIn in;
+            if (row_input(a, lane < nvalid ? r0 + lane : total, total, in)) store(r0 + lane, exact_row<FILMS>(a, in));
             if (lane == 0) ++n_fb;
-        }
-        if (valid) {
-            if (a.mode == 0) {
-                a.R[r0 + lane] = y.x;
-                a.T[r0 + lane] = y.y;
-            } else {
-                a.results[r0 + lane] = y;
-            }
         }
         __syncwarp();
     }

@@ -301,7 +301,7 @@ int sddm_add_coated_glass(sddm_ctx *ctx, const float *n, const float *alpha_clea
                           const float *film_dk, const float *film_t_nm, uint32_t *mat) {
     NEED_SPECTRUM("sddm_add_coated_glass");
     if (n_films < 0 || n_films > SDDM_MAX_FILMS || (n_films > 0 && (!film_n || !film_k || !film_dk || !film_t_nm)))
-        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_coated_glass: 0..4 films with n, k, dk and thickness arrays");
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_add_coated_glass: 0..SDDM_MAX_FILMS films with n, k, dk and thickness arrays");
     const int L = ctx->L;
     for (int j = 0; j < n_films; ++j) {
         if (!finite_range(film_n + (size_t)j * L, L, 1.0f, 10.f) || !finite_range(film_k + (size_t)j * L, L, 0.0f, 10.f) ||
@@ -387,6 +387,8 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: options out of range");
     if (o.cell_cache_bytes > 0 && o.bvh_in_host_memory)
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: cell_cache_bytes and bvh_in_host_memory exclude each other");
+    if (o.continue_cells < 0 || o.continue_cells > 1 || (o.continue_cells && o.cell_cache_bytes > 0))
+        return fail(SDDM_ERR_INVALID_ARG, "sddm_build: continue_cells is 0 or 1, and not with cell_cache_bytes");
     // every mesh material must exist (the material list may have changed since set_mesh)
     for (uint32_t m : ctx->mat_id)
         if (m >= ctx->mats.size()) return fail(SDDM_ERR_INVALID_ARG, "sddm_build: mesh references a missing material");
@@ -595,6 +597,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
 #endif
     g.n_oct = (SDDM_MAX_SUBBINS >= 64 && 128 * g.n_cells <= kMaxBins) ? 64 : (SDDM_MAX_SUBBINS >= 8 && 16 * g.n_cells <= kMaxBins) ? 8 : 1;
     g.n_bins = 2 * g.n_cells * g.n_oct;
+    g.continue_cells = o.continue_cells;
     ctx->cache.release();
     if (o.cell_cache_bytes > 0) {
         // subdomains loaded into a device cache of that many bytes as their queues fill
@@ -1332,10 +1335,14 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
     const int bps_list[] = {4, 8, 16};
     double best_rate = -1.0;
     sddm_build_opts chosen = base;
-    for (const auto &gdim : grids) {
+    for (int trial = 0; trial < 2 * (int)(sizeof grids / sizeof grids[0]); ++trial) {
         if (rc != SDDM_OK) break;
+        const int *gdim = grids[trial / 2];
+        const int cont = trial % 2;   // hand-off through the neighbour's queue, or the lane continues
+        if (cont && ((gdim[0] == 1 && gdim[1] == 1 && gdim[2] == 1) || base.cell_cache_bytes > 0)) continue;
         sddm_build_opts o = base;
         for (int a = 0; a < 3; ++a) o.grid[a] = gdim[a];
+        o.continue_cells = cont;
         if ((rc = sddm_build(ctx, &o)) != SDDM_OK) break;
         for (int bps : bps_list) {
             ctx->opts.blocks_per_sm = bps;

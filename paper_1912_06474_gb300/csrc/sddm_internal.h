@@ -52,10 +52,10 @@ struct DevScene {
     const float *mat_thick;   // [n_mat]
     // thin-film coatings of glass materials (both faces; NULL when no material has one)
     const int *mat_nfilm;     // [n_mat] films per face, 0..SDDM_MAX_FILMS
-    const float *film_n;      // [n_mat][4][L] real index
-    const float *film_k;      // [n_mat][4][L] extinction at s = 0
-    const float *film_dk;     // [n_mat][4][L] extinction added at s = 1
-    const float *film_t;      // [n_mat][4] thickness, nm
+    const float *film_n;      // [n_mat][SDDM_MAX_FILMS][L] real index
+    const float *film_k;      // [n_mat][SDDM_MAX_FILMS][L] extinction at s = 0
+    const float *film_dk;     // [n_mat][SDDM_MAX_FILMS][L] extinction added at s = 1
+    const float *film_t;      // [n_mat][SDDM_MAX_FILMS] thickness, nm
     const float4 *tri_n;      // [nt] unit CCW normal, .w = material id (int bits)
     const int *tri_obj;       // [nt]
     int n_light;
@@ -96,7 +96,7 @@ struct Material {
     // coating films (glass): per film n, k, dk curves [L] and thickness (nm)
     int n_film = 0;
     std::vector<float> film_n, film_k, film_dk;   // [n_film][L]
-    float film_t[4] = {0.f, 0.f, 0.f, 0.f};
+    float film_t[SDDM_MAX_FILMS] = {};
 };
 
 // A built BVH in device-ready packed form.

@@ -126,11 +126,16 @@ def test_surrogate_on_coated_glass(oracle_mod, sddm, room):
 def test_surrogate_gain_against_film_count(sddm):
     """What the trained network gains over the exact stack as the stack grows:
     4M (cos, bin, s) rows of a pane coated with 1, 3, 6 and 10 films, device
-    time of the exact transfer-matrix stack against the network (alone, and
-    with its probe and exact fallback), the network retrained on each stack.
-    The exact model's cost grows with the films and the network's does not;
-    the film count where the network first wins is printed and checked against
-    the count this GPU gives (none up to 10: the exact stack stays cheaper)."""
+    time of the exact transfer-matrix stack against the network alone and
+    against the served surrogate (network, per-batch probe and exact
+    fallback), the network retrained on each stack. Measured on a GB300:
+
+    * the exact stack's cost grows with the films, the network's does not;
+    * the network alone is cheaper than the exact stack from 6 films on;
+    * the served surrogate is not cheaper at any of these counts: the thicker
+      stacks' interference fringes in angle and wavelength are harder for the
+      4-64-64-64-2 network to fit, and the batches whose probe fails pay for
+      the network and the exact stack both."""
     films = (1, 3, 6, 10)
     res = {}
     for J in films:
@@ -156,19 +161,18 @@ def test_surrogate_gain_against_film_count(sddm):
                 torch.cuda.synchronize()
                 t[mode] = ev[0].elapsed_time(ev[1]) / 5
             dT = (out["mlp"][1] - out["exact"][1]).abs()
+            served_exact = (out["mlp"][1] != out["mlp_raw"][1]).float().mean().item()
             res[J] = t
-            print(f"{J:2d} films: exact {t['exact']:.3f} ms, network {t['mlp_raw']:.3f} ms, network with probe and "
-                  f"fallback {t['mlp']:.3f} ms; served |dT| mean {dT.mean().item():.2e} max {dT.max().item():.2e}; "
-                  f"training loss {rep['final_loss']:.1e}")
+            print(f"{J:2d} films: exact {t['exact']:.3f} ms, network {t['mlp_raw']:.3f} ms, served surrogate "
+                  f"{t['mlp']:.3f} ms ({served_exact:.0%} of rows by the exact fallback); served |dT| mean "
+                  f"{dT.mean().item():.2e}; training loss {rep['final_loss']:.1e}")
             assert dT.mean().item() <= 1e-3
         finally:
             ctx.close()
-    # the exact stack's cost grows with the films, the network's stays flat
     assert res[10]["exact"] > 3.0 * res[1]["exact"]
-    assert res[10]["mlp_raw"] < 1.5 * res[1]["mlp_raw"]
-    wins = [J for J in films if res[J]["mlp"] < res[J]["exact"]]
-    slope = (res[10]["exact"] - res[1]["exact"]) / 9.0
-    cross = 1 + (res[1]["mlp"] - res[1]["exact"]) / slope
-    print(f"network wins first at {wins[0] if wins else 'none of'} {films if not wins else ''} films; "
-          f"linear extrapolation of the exact cost reaches the network's at {cross:.1f} films")
-    assert not wins
+    assert res[10]["mlp_raw"] < 1.3 * res[1]["mlp_raw"]
+    net_wins = [J for J in films if res[J]["mlp_raw"] < res[J]["exact"]]
+    served_wins = [J for J in films if res[J]["mlp"] < res[J]["exact"]]
+    print(f"network alone cheaper than the exact stack at {net_wins} films; served surrogate at {served_wins}")
+    assert net_wins == [6, 10]
+    assert served_wins == []
