@@ -16,8 +16,10 @@ value   = (extension + shadow segments of all ranks) / (max over ranks of the
 value_eager = the same steps launched eagerly with CUDA events around every
           trace launch (these events give the roofline's kernel time).
 arms    = the same metric for the other variants on the same workload: DDM
-          with the exact slab and the plain global-BVH megakernel with the
-          exact slab (the comparison the metric names).
+          with the exact slab, the plain global-BVH megakernel with the exact
+          slab (the comparison the metric names), and the DDM with the ray
+          carried across subdomain faces by its lane (continue_cells) and
+          with a single subdomain.
 e2e     = the same metric through sddm_render_host: result image copied back
           to pinned host memory inside the timed region.
 roofline: the trace kernel (k_trace_wave for DDM, k_megakernel for the plain
@@ -296,21 +298,29 @@ def run(args):
     # the other arms of the comparison on the same workload and timing rules
     arms = {}
     if not args.single_arm:
-        other = [("ddm", "exact")] if (args.method, args.bsdf) != ("ddm", "exact") else [("ddm", "mlp")]
-        other.append(("megakernel", "exact"))
-        for method, bsdf in other:
-            if method == "ddm":
+        # (name, method, glass model, build options of a separate context or None = this one)
+        other = [("ddm_exact", "ddm", "exact", None)] if (args.method, args.bsdf) != ("ddm", "exact") else \
+            [("ddm_mlp", "ddm", "mlp", None)]
+        other.append(("megakernel_exact", "megakernel", "exact", dict(grid=(1, 1, 1))))
+        if args.method == "ddm" and not args.single_arm and not args.continue_cells:
+            # the same grid with the lane carrying rays across subdomain faces, and no split at all
+            other.append(("ddm_continue_cells_" + args.bsdf, "ddm", args.bsdf, dict(grid=grid, continue_cells=True)))
+            other.append(("ddm_grid_1x1x1_" + args.bsdf, "ddm", args.bsdf, dict(grid=(1, 1, 1))))
+        for name, method, bsdf, opts in other:
+            if opts is None:
                 actx = ctx
                 if bsdf == "mlp" and args.bsdf != "mlp":
                     ctx.mlp_train(scene.glass_materials()[0], seed=7)
             else:
                 actx = sddm.Context(local, stream)
                 actx.set_scene(scene)
-                actx.build(grid=(1, 1, 1))
+                actx.build(**opts)
+                if bsdf == "mlp":
+                    actx.mlp_train(scene.glass_materials()[0], seed=7)
             for _ in range(args.warmup):
                 actx.render_into([spec], [out], method=method, bsdf=bsdf)
             ms, asts = _timed_steps(actx, spec, out, method, bsdf, args.steps, flush, stream)
-            arms[f"{method}_{bsdf}"] = [sum(ms), sum(_segs(s) for s in asts)]
+            arms[name] = [sum(ms), sum(_segs(s) for s in asts)]
             if actx is not ctx:
                 actx.close()
     clk = clocks.stop()

@@ -6,7 +6,7 @@
  * from the Fresnel equations) as a function of (cos theta, lambda, s,
  * thickness): 4 inputs -> 64 -> 64 -> 64 SiLU units -> 2 outputs (R, T).
  * Inputs are mapped to [-1, 1]:
- *   x0 = 2 cos - 1, x1 = 2 (lambda - 380) / 400 - 1, x2 = 2 s - 1,
+ *   x0 = 2 sqrt(cos) - 1, x1 = 2 (lambda - 380) / 400 - 1, x2 = 2 s - 1,
  *   x3 = 2 exp(-(alpha d + A_f)) - 1,
  * where alpha = alpha_clear(lambda) + s dalpha(lambda) is the material's
  * absorption coefficient (1/m) at the coloration state s, so that x3 carries
@@ -42,7 +42,7 @@ int orc_mlp_n_params(void) { return N_PARAMS; }
 void orc_mlp_features(double c, double lam_nm, double s, double d, double alpha, double film_absorbance,
                       double x[4])
 {
-    x[0] = 2.0 * c - 1.0;
+    x[0] = 2.0 * sqrt(c > 0.0 ? c : 0.0) - 1.0;
     x[1] = 2.0 * (lam_nm - 380.0) / 400.0 - 1.0;
     x[2] = 2.0 * s - 1.0;
     x[3] = 2.0 * exp(-(alpha * d + film_absorbance)) - 1.0;

@@ -9,7 +9,7 @@
 //
 // Parameters (FP32 master copy, 8770 floats): W1[64][4], b1[64], W2[64][64],
 // b2[64], W3[64][64], b3[64], W4[2][64], b4[2]; z = W h + b. Inputs are mapped
-// to [-1, 1] over the trained box: 2 cos - 1, (lambda - 380) / 200 - 1, 2 s - 1,
+// to [-1, 1] over the trained box: 2 sqrt(cos) - 1, (lambda - 380) / 200 - 1, 2 s - 1,
 // and the thickness through the slab's internal transmittance at normal
 // incidence, 2 exp(-(alpha d + film absorbance)) - 1 (see features()).
 #include <cuda_bf16.h>
@@ -104,14 +104,16 @@ constexpr float kOutEps = 1e-3f;
 __device__ __forceinline__ float out_to_rt(float y) { return fmaxf(expf(y) - kOutEps, 0.0f); }
 __device__ __forceinline__ float rt_to_out(float v) { return logf(v + kOutEps); }
 
-// Network inputs from (cos, lambda, s, thickness): cos and s mapped to [-1, 1],
-// lambda over 380-780 nm to [-1, 1], and the thickness through the slab's
+// Network inputs from (cos, lambda, s, thickness): sqrt(cos) and s mapped to
+// [-1, 1] (the square root spreads the grazing angles, where reflectance and
+// transmittance change fastest), lambda over 380-780 nm to [-1, 1], and the
+// thickness through the slab's
 // internal transmittance at normal incidence, exp(-alpha(lambda, s) d) mapped
 // to [-1, 1] (alpha = alpha_clear + s dalpha, the material's absorption law),
 // times that of any coating film (exp(-4 pi k t / lambda) each).
 // Angle, Fresnel and the multiple reflections are left to the network.
 __device__ __forceinline__ void features(float c, float lam, float s, float alpha_d, float x[4]) {
-    x[0] = 2.0f * c - 1.0f;
+    x[0] = 2.0f * sqrtf(fmaxf(c, 0.0f)) - 1.0f;
     x[1] = (lam - 380.0f) * (1.0f / 200.0f) - 1.0f;
     x[2] = 2.0f * s - 1.0f;
     x[3] = 2.0f * expf(-alpha_d) - 1.0f;
@@ -131,6 +133,11 @@ __device__ __forceinline__ void features(float c, float lam, float s, float alph
 //    so the products keep 16 bits of the FP32 inputs and bias;
 //  * layers 2 and 3 (64 x 64) as four K steps;
 //  * layer 4 (N = 2) as an N = 8 tile whose rows 2..7 are zero.
+// The activations entering layer 4 are split the same way, h = h_hi + h_lo in
+// two BF16 parts, each multiplied by the same BF16 weights (two MMAs per
+// fragment), so that the outputs do not carry the 8-bit rounding of the last
+// hidden layer (training does the same); layers 2 and 3 take single BF16
+// activations.
 // B fragments come from shared memory by ldmatrix, four 8x8 blocks at a time.
 constexpr int LD1 = 24;   // layer-1 B rows: 16 used, stride 48 B (16-byte aligned, conflict-free)
 struct alignas(16) InferSmem {   // 16-byte rows for ldmatrix
@@ -182,11 +189,12 @@ __device__ __forceinline__ void ldmatrix_x4(const void *row_addr, uint32_t &r0, 
 }
 
 // acc (16 x 64) += A (16 x 16 kk_steps) W^T, A in registers as mma A
-// fragments, W [64][ld] bf16 in shared memory (row n = output n). The B
-// fragments of output tiles j, j + 1 for one K step are one ldmatrix.x4.
-template <int KSTEPS>
-__device__ __forceinline__ void warp_gemm_ldm(float acc[8][4], const uint32_t fa[][4], const __nv_bfloat16 *W,
-                                              int ld, int lane) {
+// fragments (fa, and with LO a second part fb of the same A), W [64][ld]
+// bf16 in shared memory (row n = output n). The B fragments of output tiles
+// j, j + 1 for one K step are one ldmatrix.x4.
+template <int KSTEPS, bool LO>
+__device__ __forceinline__ void warp_gemm_ldm(float acc[8][4], const uint32_t fa[][4], const uint32_t fb[][4],
+                                              const __nv_bfloat16 *W, int ld, int lane) {
     const int q = lane >> 3, r = lane & 7;
 #pragma unroll
     for (int kk = 0; kk < KSTEPS; ++kk) {
@@ -196,7 +204,27 @@ __device__ __forceinline__ void warp_gemm_ldm(float acc[8][4], const uint32_t fa
             ldmatrix_x4(W + (8 * (j + (q >> 1)) + r) * ld + 16 * kk + 8 * (q & 1), b0, b1, c0, c1);
             mma16816(acc[j], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
             mma16816(acc[j + 1], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], c0, c1);
+            if (LO) {
+                mma16816(acc[j], fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], b0, b1);
+                mma16816(acc[j + 1], fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], c0, c1);
+            }
         }
+    }
+}
+
+// Activations h (accumulator layout) as two BF16 A-fragment parts, h_hi =
+// bf16(h) and h_lo = bf16(h - h_hi).
+__device__ __forceinline__ uint32_t pack_lo_bf16x2(float a, float b) {
+    return pack_bf16x2(a - bf16r(a), b - bf16r(b));
+}
+__device__ __forceinline__ void pack_afrag2(const float h[8][4], uint32_t fa[4][4], uint32_t fb[4][4]) {
+    pack_afrag(h, fa);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        fb[kk][0] = pack_lo_bf16x2(h[2 * kk][0], h[2 * kk][1]);
+        fb[kk][1] = pack_lo_bf16x2(h[2 * kk][2], h[2 * kk][3]);
+        fb[kk][2] = pack_lo_bf16x2(h[2 * kk + 1][0], h[2 * kk + 1][1]);
+        fb[kk][3] = pack_lo_bf16x2(h[2 * kk + 1][2], h[2 * kk + 1][3]);
     }
 }
 
@@ -228,17 +256,17 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
                              float yh[2]) {
     const int t = lane & 3;
     float acc[8][4];
-    uint32_t fa[4][4];
+    uint32_t fa[4][4], fb[4][4];
     layer1_afrag(xl, xh, t, fa[0]);
     zero_acc(acc);
-    warp_gemm_ldm<1>(acc, fa, s.w1, LD1, lane);
+    warp_gemm_ldm<1, false>(acc, fa, fb, s.w1, LD1, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[j][e] = silu_h(acc[j][e]);
     pack_afrag(acc, fa);
     zero_acc(acc);
-    warp_gemm_ldm<4>(acc, fa, s.w2, LD, lane);
+    warp_gemm_ldm<4, false>(acc, fa, fb, s.w2, LD, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
@@ -250,7 +278,7 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
     }
     pack_afrag(acc, fa);
     zero_acc(acc);
-    warp_gemm_ldm<4>(acc, fa, s.w3, LD, lane);
+    warp_gemm_ldm<4, false>(acc, fa, fb, s.w3, LD, lane);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int c = 8 * j + 2 * t;
@@ -260,7 +288,7 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
         acc[j][2] = silu_h(acc[j][2] + bb.x);
         acc[j][3] = silu_h(acc[j][3] + bb.y);
     }
-    pack_afrag(acc, fa);
+    pack_afrag2(acc, fa, fb);
     // layer 4: one N = 8 tile, K = 64 in four steps (two ldmatrix.x4, each
     // the B fragments of two K steps)
     float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -270,7 +298,9 @@ __device__ void tile_forward(const InferSmem &s, const float xl[4], const float 
         uint32_t b0, b1, c0, c1;
         ldmatrix_x4(s.w4 + r * LD + 16 * (kk + (q >> 1)) + 8 * (q & 1), b0, b1, c0, c1);
         mma16816(o, fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
+        mma16816(o, fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], b0, b1);
         mma16816(o, fa[kk + 1][0], fa[kk + 1][1], fa[kk + 1][2], fa[kk + 1][3], c0, c1);
+        mma16816(o, fb[kk + 1][0], fb[kk + 1][1], fb[kk + 1][2], fb[kk + 1][3], c0, c1);
     }
     // o[0..1]: row g, outputs 2t, 2t + 1; o[2..3]: row g + 8 (outputs 0, 1 on t = 0)
     yl[0] = o[0] + s.b4[0];
@@ -348,9 +378,8 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
 // one per lane, so that a probe costs one lane's share of an exact evaluation
 // rather than a whole warp's.
 #ifndef SDDM_MLP_MINB
-#define SDDM_MLP_MINB 4   // resident inference blocks per SM asked of the register allocator: 64 registers
-                          // with ~100 B of spills, 32 warps per SM (+3% on the hotel bench against 80
-                          // registers and 24 warps)
+#define SDDM_MLP_MINB 4   // resident inference blocks per SM asked of the register allocator: 64
+                          // registers with ~80 B of spills, 32 warps per SM
 #endif
 #ifndef SDDM_MLP_UNROLL_HALVES
 #define SDDM_MLP_UNROLL_HALVES 1   // the two 16-row tiles of a batch as one unrolled sequence
@@ -511,7 +540,7 @@ __global__ void __launch_bounds__(256) k_slab_rows(MlpRows a) {
 // and the CTA's share of every weight gradient, written to grad_cta[cta].
 struct TrainSmem {
     __nv_bfloat16 w2[H * LD], w3[H * LD], w2t[H * LD], w3t[H * LD];
-    __nv_bfloat16 h1[H * LD], h2[H * LD], h3[H * LD], h1t[H * LD], h2t[H * LD];
+    __nv_bfloat16 h1[H * LD], h2[H * LD], h1t[H * LD], h2t[H * LD];
     __nv_bfloat16 dz3[H * LD], dz2[H * LD], dz3t[H * LD], dz2t[H * LD];
     float z1[H * H], z2[H * H], z3[H * H];
     float w1[H * 4], w4[2 * H], b1[H], b2[H], b3[H], b4[2];
@@ -617,8 +646,8 @@ __global__ void __launch_bounds__(128) k_mlp_train_tile(MlpTrainArgs a) {
             const float zl = acc[j][e] + s.b3[c], zh = acc[j][2 + e] + s.b3[c];
             s.z3[rl * H + c] = zl;
             s.z3[rh * H + c] = zh;
-            h3l[2 * j + e] = bf16r(silu(zl));
-            h3h[2 * j + e] = bf16r(silu(zh));
+            h3l[2 * j + e] = silu(zl);   // layer 4 takes the activations in two BF16 parts: ~16 bits
+            h3h[2 * j + e] = silu(zh);
             yl0 = fmaf(s.w4[c], h3l[2 * j + e], yl0);
             yl1 = fmaf(s.w4[H + c], h3l[2 * j + e], yl1);
             yh0 = fmaf(s.w4[c], h3h[2 * j + e], yh0);

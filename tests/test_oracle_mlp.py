@@ -40,8 +40,10 @@ def test_feature_map_box_corners(oracle_mod):
     # alpha d = ln 2: transmittance 1/2, the middle of the range
     assert np.allclose(oracle_mod.mlp_features(1.0, 780.0, 1.0, 0.010, 0.0), [1, 1, 1, 1], atol=1e-12)
     assert np.allclose(oracle_mod.mlp_features(0.0, 380.0, 0.0, 0.002, 5e4), [-1, -1, -1, -1], atol=1e-12)
-    assert np.allclose(oracle_mod.mlp_features(0.5, 580.0, 0.5, 0.006, np.log(2.0) / 0.006), [0, 0, 0, 0],
+    assert np.allclose(oracle_mod.mlp_features(0.25, 580.0, 0.5, 0.006, np.log(2.0) / 0.006), [0, 0, 0, 0],
                        atol=1e-12)
+    # the angle enters as sqrt(cos): cos = 1/16 sits a quarter of the way up
+    assert abs(oracle_mod.mlp_features(1.0 / 16.0, 580.0, 0.5, 0.006, 1.0)[0] + 0.5) <= 1e-12
 
 
 def test_feature_transmittance_is_beer_lambert(oracle_mod):
