@@ -392,7 +392,8 @@ def run(args):
         line["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     # the second workload runs with the default hotel-room configuration only
     default_run = (args.width, args.height, args.spp, args.method, args.bsdf, args.grid, args.single_arm,
-                   args.continue_cells) == (512, 512, 16, "ddm", "mlp", None, False, False)
+                   args.continue_cells, args.facade_renders, args.facade_spp) == \
+        (512, 512, 16, "ddm", "mlp", None, False, False, 16, 64)
     if not args.no_facade and world == 1 and default_run:
         del ctx, out, image
         torch.cuda.empty_cache()
@@ -425,9 +426,11 @@ def facade_leg(local, stream, flush, args):
 
     from paper_1912_06474_gb300 import scenes, sddm
     scene = scenes.facade_room(L=81, seed=0)
-    specs = scenes.facade_renders(scene)
+    specs = scenes.facade_renders(scene, n_renders=args.facade_renders, spp=args.facade_spp)
     grid = (8, 8, 4)
-    cfg = {"workload": FACADE_WORKLOAD, "triangles": scene.n_tris, "renders": len(specs), "width": specs[0].width,
+    name = FACADE_WORKLOAD if (args.facade_renders, args.facade_spp) == (16, 64) else \
+        f"facade_room_5M_tris_{args.facade_renders}x1920x1080_{args.facade_spp}spp_d8_L81_ddm8x8x4_mlp"
+    cfg = {"workload": name, "triangles": scene.n_tris, "renders": len(specs), "width": specs[0].width,
            "height": specs[0].height, "spp": specs[0].spp, "max_depth": specs[0].max_depth, "lambda_bins": 81,
            "panes": len(scene.glass_materials()), "method": "ddm", "grid": list(grid), "bsdf": "mlp",
            "l2": "inputs larger than L2 (BVHs ~0.6 GB), flushed before the step"}
@@ -520,7 +523,8 @@ def facade_leg(local, stream, flush, args):
     g, rf = np.concatenate(got), np.concatenate(ref)
     res["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(g - rf) / np.linalg.norm(rf))
     res["cpu_baseline"] = {"value": oseg / ot / 1e6, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-                           "sample": f"256 seeded pixels x 64 spp of each of the 16 renders ({oseg} segments, "
+                           "sample": f"256 seeded pixels x {specs[0].spp} spp of each of the {len(specs)} renders "
+                                     f"({oseg} segments, "
                                      f"{ot:.1f} s wall; oracle BVH build {build_s:.1f} s not counted)"}
     return res
 
@@ -537,6 +541,9 @@ def main():
     ap.add_argument("--paths-in-flight", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-facade", action="store_true", help="skip the full-size facade-room workload")
+    ap.add_argument("--facade-only", action="store_true", help="run only the facade-room workload")
+    ap.add_argument("--facade-renders", type=int, default=16, help="renders of the facade batch (16 = its workload)")
+    ap.add_argument("--facade-spp", type=int, default=64, help="samples per pixel of the facade renders (64)")
     ap.add_argument("--single-arm", action="store_true", help="time only the selected method and glass model")
     ap.add_argument("--width", type=int, default=512)
     ap.add_argument("--height", type=int, default=512)
@@ -552,6 +559,11 @@ def main():
         args.bsdf = "exact"   # the surrogate is served by the DDM path's dense query pass only
     if args.impl == "reference":
         run_reference(args)
+    elif args.facade_only:   # the second workload alone (a smaller batch for profiling with these flags)
+        import torch
+        torch.cuda.set_device(0)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        print(json.dumps(facade_leg(0, torch.cuda.current_stream(), flush, args)), flush=True)
     else:
         run(args)
 
