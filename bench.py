@@ -66,6 +66,41 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# Tensor FLOP per (query, bin) row of the surrogate network as its kernel issues
+# them on the tensor cores: layer 1 (4 inputs, K padded to 16 with the second
+# BF16 part of the inputs and the bias), layers 2 and 3 (64 x 64), 2 FLOP per
+# MAC; algorithmic, the padding not counted. Layer 4 (64 x 2) runs on the FP32
+# pipes and is left out.
+MLP_TENSOR_FLOP_PER_ROW = 2 * (4 * 64 + 64 * 64 + 64 * 64)
+
+
+def _bf16_peak():
+    """Dense BF16 TFLOP/s: the sustained measurement (the surrogate kernel is
+    timed inside a long step), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops_sustained"]), "measured sustained"
+    except Exception:
+        return 1700.0, "fallback sustained"
+
+
+def _mlp_tensor(ests):
+    """Tensor-pipe roofline of the surrogate network kernel (k_mlp_net) from the
+    event-timed steps: algorithmic tensor FLOP of the rows it evaluated over its
+    summed device time."""
+    ms = sum(s.get("mlp_ms", 0.0) for s in ests)
+    rows = sum(s.get("mlp_rows", 0) for s in ests)
+    if ms <= 0 or rows <= 0:
+        return None
+    peak, kind = _bf16_peak()
+    achieved = rows * MLP_TENSOR_FLOP_PER_ROW / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "k_mlp_net", "achieved": round(achieved, 2), "peak": peak,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "peak_kind": kind,
+            "flop_per_row": MLP_TENSOR_FLOP_PER_ROW, "rows_per_step": rows // len(ests),
+            "ms_per_step": round(ms / len(ests), 4)}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -384,6 +419,7 @@ def run(args):
         "segments_per_step": segs // (args.steps * world), "clocks": clk,
         "mlp_fallback_batches_per_step": fallbacks // args.steps if args.bsdf == "mlp" else None,
         "mlp_fallback_fraction": round(fallbacks / mlp_batches, 4) if mlp_batches else None,
+        "mlp_tensor": _mlp_tensor(ests) if args.bsdf == "mlp" else None,
     }
     if not args.no_cpu_baseline and world == 1:
         info, pix, ref = cpu_baseline(width=args.width, height=args.height, spp=args.spp)
@@ -494,6 +530,7 @@ def facade_leg(local, stream, flush, args):
         "gpu_launches": int(st["kernel_launches"]),
         "mlp_fallback_fraction": round(st["mlp_fallbacks"] / st["mlp_batches"], 4) if st["mlp_batches"] else None,
         "mlp_batches_per_step": st["mlp_batches"],
+        "mlp_tensor": _mlp_tensor([tst]),
         "arms": arms,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None, "traffic": None,

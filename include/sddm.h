@@ -130,11 +130,13 @@ typedef struct {
     int64_t cache_loads;      /* cell_cache_bytes > 0: subdomain BVHs copied into the cache */
     int64_t cache_hits;       /* ... (cell, wave) uses that found the subdomain already resident */
     int64_t cache_bytes_loaded; /* ... bytes copied from host memory */
+    double mlp_ms;            /* SDDM_PROFILE_TIME_TRACE: summed device time of the surrogate network kernel */
+    int64_t mlp_rows;         /* (query, bin) rows the surrogate network evaluated */
 } sddm_stats;
 
 /* Profiling switches (sddm_set_profiling), off by default. */
 enum {
-    SDDM_PROFILE_TIME_TRACE = 1,        /* CUDA events around every trace-kernel launch */
+    SDDM_PROFILE_TIME_TRACE = 1,        /* CUDA events around every trace and surrogate-network launch */
     SDDM_PROFILE_COUNT_TRAVERSAL = 2,   /* count nodes, triangle tests and ray visits */
     SDDM_PROFILE_EAGER = 4              /* launch every kernel from the host (no CUDA graph replay) */
 };

@@ -37,19 +37,24 @@ namespace sddm {
 DDMBuffers::~DDMBuffers() {
     if (mem) cudaFree(mem);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaEvent_t e : mlp_events) cudaEventDestroy(e);
 }
 
-cudaError_t DDMBuffers::event_pair(cudaEvent_t &a, cudaEvent_t &b) {
-    while (events.size() < (size_t)events_used + 2) {
+static cudaError_t next_event_pair(std::vector<cudaEvent_t> &pool, int &used, cudaEvent_t &a, cudaEvent_t &b) {
+    while (pool.size() < (size_t)used + 2) {
         cudaEvent_t e;
         cudaError_t err = cudaEventCreate(&e);
         if (err != cudaSuccess) return err;
-        events.push_back(e);
+        pool.push_back(e);
     }
-    a = events[events_used];
-    b = events[events_used + 1];
-    events_used += 2;
+    a = pool[used];
+    b = pool[used + 1];
+    used += 2;
     return cudaSuccess;
+}
+cudaError_t DDMBuffers::event_pair(cudaEvent_t &a, cudaEvent_t &b) { return next_event_pair(events, events_used, a, b); }
+cudaError_t DDMBuffers::mlp_event_pair(cudaEvent_t &a, cudaEvent_t &b) {
+    return next_event_pair(mlp_events, mlp_events_used, a, b);
 }
 
 struct KArgs {
@@ -973,6 +978,8 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
         mr.raw = 0;
         mr.fallbacks = run.counters + 4;
         mr.batches = run.counters + 8;
+        mr.rows = run.counters + 9;
+        mr.err = run.error_flag;
     }
 
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
@@ -1068,9 +1075,13 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
             k_glass_gather<<<glass_blocks, 256, 0, s>>>(a);
             DDM_CHECK(cudaGetLastError());
             *run.launches += 1;
-            if (use_mlp)
-                DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s));
-            else
+            if (use_mlp) {
+                cudaEvent_t m0 = nullptr, m1 = nullptr;
+                if (run.time_trace && (e = buf.mlp_event_pair(m0, m1)) != cudaSuccess)
+                    return cuda_fail(e, "sddm_render: events");
+                DDM_CHECK(launch_mlp_rows(mr, run.sm_count, s, m0, m1));
+                *run.launches += mr.raw ? 0 : 1;   // the probe pass
+            } else
                 DDM_CHECK(launch_slab_rows(mr, run.sm_count, s));
             *run.launches += 2;
         }

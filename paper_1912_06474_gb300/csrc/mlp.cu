@@ -1,11 +1,9 @@
 // Learned surrogate of the glass slab's R and T (a stand-in for the exact
 // Fresnel-equation glass of Sec. 6): a 4 -> 64 -> 64 -> 64 -> 2 SiLU
-// network evaluated and trained with BF16 tensor-core MMAs (m16n8k16, FP32
-// accumulation). The layers are 64 wide, so a warp carries a 16-row tile
-// through the whole network: the accumulator fragments of one layer, after
-// SiLU and rounding to BF16, are exactly the A fragments of the next layer,
-// so activations stay in registers from layer to layer and never leave the
-// SM. Layer 1 (K = 4) and the output layer (N = 2) run on the FP32 pipes.
+// network with BF16 weights and FP32 accumulation. Inference runs its three
+// 64-wide layers on the tcgen05 tensor cores, 128 rows per CTA with the
+// accumulators in tensor memory; training uses warp-level m16n8k16 MMAs on
+// 16-row tiles whose activations stay in registers from layer to layer.
 //
 // Parameters (FP32 master copy, 8770 floats): W1[64][4], b1[64], W2[64][64],
 // b2[64], W3[64][64], b3[64], W4[2][64], b4[2]; z = W h + b. Inputs are mapped
@@ -80,18 +78,6 @@ __device__ __forceinline__ void warp_gemm(float acc[8][4], const __nv_bfloat16 *
     }
 }
 
-// Activations h (accumulator layout: h[j][0..1] row g, cols 8j + 2t + {0,1};
-// h[j][2..3] row g + 8) as BF16 A fragments of the next layer's mma.
-__device__ __forceinline__ void pack_afrag(const float h[8][4], uint32_t fa[4][4]) {
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        fa[kk][0] = pack_bf16x2(h[2 * kk][0], h[2 * kk][1]);
-        fa[kk][1] = pack_bf16x2(h[2 * kk][2], h[2 * kk][3]);
-        fa[kk][2] = pack_bf16x2(h[2 * kk + 1][0], h[2 * kk + 1][1]);
-        fa[kk][3] = pack_bf16x2(h[2 * kk + 1][2], h[2 * kk + 1][3]);
-    }
-}
-
 __device__ __forceinline__ void zero_acc(float acc[8][4]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
@@ -120,39 +106,152 @@ __device__ __forceinline__ void features(float c, float lam, float s, float alph
 }
 
 // ------------------------------------------------------------- inference
-// The hidden layers' weights and biases are stored halved: the layer then
-// produces h = z / 2 directly (halving is exact in binary floating point, so
-// the activations are bit for bit those of the unscaled layer), and
-// SiLU(z) = h + h tanh(h) costs one SFU operation and one FMA.
+// The network runs on the fifth-generation tensor cores (tcgen05): a CTA of
+// four warps carries a tile of 128 rows through the hidden layers, one row
+// per thread. For each layer one thread issues the MMAs (M = 128, N = 64,
+// K = 16 each, BF16 operands from shared memory, FP32 accumulators in tensor
+// memory), the CTA waits on an mbarrier that the tensor core arrives on when
+// they are done, and every warp reads back its 32 rows of accumulators
+// (tensor-memory lanes 32w .. 32w + 31 belong to warp w), applies SiLU and
+// writes the BF16 activations into the A operand of the next layer.
 //
-// All four layers run on the tensor cores (m16n8k16, BF16 operands, FP32
-// accumulation):
-//  * layer 1 (K = 4) as one K = 16 step whose A row is [x_hi(4) | x_lo(4) |
-//    1 | 1 | 0 ...] and whose B row for output n is [W1n(4) | W1n(4) | b_hi |
-//    b_lo | 0 ...]: each input split into two BF16 parts and the bias into two,
-//    so the products keep 16 bits of the FP32 inputs and bias;
-//  * layers 2 and 3 (64 x 64) as four K steps;
-//  * layer 4 (N = 2) as an N = 8 tile whose rows 2..7 are zero.
-// The activations entering layer 4 are split the same way, h = h_hi + h_lo in
-// two BF16 parts, each multiplied by the same BF16 weights (two MMAs per
-// fragment), so that the outputs do not carry the 8-bit rounding of the last
-// hidden layer (training does the same); layers 2 and 3 take single BF16
-// activations.
-// B fragments come from shared memory by ldmatrix, four 8x8 blocks at a time.
-constexpr int LD1 = 24;   // layer-1 B rows: 16 used, stride 48 B (16-byte aligned, conflict-free)
-struct alignas(16) InferSmem {   // 16-byte rows for ldmatrix
-    __nv_bfloat16 w1[H * LD1];              // [64][16]: W1 / 2 twice, b1 / 2 as hi + lo
-    __nv_bfloat16 w2[H * LD], w3[H * LD];   // W / 2
-    __nv_bfloat16 w4[8 * LD];               // rows 0, 1: W4; rows 2..7: 0
-    float b2[H], b3[H];                     // b / 2
+// The hidden layers' weights and biases are stored halved: a layer then
+// produces h = z / 2 directly (halving is exact in binary floating point, so
+// the activations are bit for bit those of the unscaled layer), and SiLU(z) =
+// h + h tanh(h) costs one SFU operation and one FMA.
+//  * Layer 1 (K = 4) is one K = 16 step whose A row is [x_hi(4) | x_lo(4) | 1 |
+//    1 | 0 ...] and whose B row for output n is [W1n(4) | W1n(4) | b_hi | b_lo |
+//    0 ...]: inputs and bias each split into two BF16 parts, so the products
+//    keep 16 bits of the FP32 inputs and bias.
+//  * Layers 2 and 3 (64 x 64) are four K steps over the activations plus one
+//    over a constant A chunk [1 | 1 | 0 ...] against [b_hi | b_lo | 0 ...]:
+//    the bias in two BF16 parts, added by the tensor core.
+//  * Layer 4 (N = 2) runs in FP32 on the CUDA cores from the FP32 activations
+//    of layer 3 and the BF16-rounded output weights (training multiplies the
+//    same weights by the activations split into two BF16 parts).
+//
+// Operands sit in shared memory in the tensor core's K-major layout without
+// swizzle: 8-row x 16-byte core matrices, the core matrices of one 8-row group
+// side by side along K (128 B apart, the leading-dimension offset) and the
+// 8-row groups one after the other (the stride offset).
+constexpr int kTcRows = 128;          // rows per tile = threads per CTA = TMEM lanes
+constexpr int kTcCols = 64;           // TMEM columns: one 128 x 64 FP32 accumulator
+constexpr int kChA = 10;              // A chunks per 8-row group: 8 activations + bias ones + zero
+constexpr int kChB1 = 2;              // layer-1 B: K = 16
+constexpr int kChB = 10;              // layers 2, 3 B: K = 64 + bias step
+constexpr uint32_t kMbarTries = 1u << 22;   // bounded waits: ~seconds, then the CTA reports and stops
+
+struct __align__(128) TcSmem {
+    __nv_bfloat16 a[kTcRows * kChA * 8];    // activations / inputs, K-major core matrices
+    __nv_bfloat16 b1[H * kChB1 * 8];
+    __nv_bfloat16 b2[H * kChB * 8], b3[H * kChB * 8];
+    float w4[2][H];                         // BF16-rounded output weights (FP32 layer 4)
     float b4[2];
+    unsigned long long mbar;
+    uint32_t tmem;
+    int abort;
 };
 
-__device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
-    for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
-        const int r = i >> 6, c = i & 63;
-        s.w2[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W2 + i]);
-        s.w3[r * LD + c] = __float2bfloat16_rn(0.5f * p[OFF_W3 + i]);
+// Element offset of (row, k) in a K-major operand of `nch` 16-byte chunks per row.
+__device__ __forceinline__ int kmaj(int row, int k, int nch) {
+    return (row >> 3) * (nch * 64) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading- and stride-dimension
+// byte offsets (16-byte units), descriptor version 1 (bits 46-47), no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 D (bits 4-5 = 1), BF16 A and B
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at bit 24.
+constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t kIdescHidden = tc_idesc(kTcRows, H);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// The mbarrier receives one arrival when every MMA this thread issued so far is complete.
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Generic-proxy shared-memory writes made visible to the tensor core's reads.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t i = 0; i < kMbarTries; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 64 consecutive FP32 accumulator columns of this thread's TMEM lane; the
+// wait is in the same statement, so no use of the registers can precede it.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+          "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+          "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// SiLU of z given h = z / 2.
+__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
+
+// Weights into the CTA's operand layout (once per CTA), and the constant
+// bias chunks of every A row.
+__device__ void tc_load_weights(TcSmem &s, const float *__restrict__ p) {
+    for (int i = threadIdx.x; i < H * kChB * 8; i += blockDim.x) {
+        const int n = i / (kChB * 8), k = i % (kChB * 8);
+        float v2 = 0.0f, v3 = 0.0f;
+        if (k < H) {
+            v2 = 0.5f * p[OFF_W2 + H * n + k];
+            v3 = 0.5f * p[OFF_W3 + H * n + k];
+        } else if (k < H + 2) {
+            const float c2 = 0.5f * p[OFF_B2 + n], c3 = 0.5f * p[OFF_B3 + n];
+            v2 = k == H ? bf16r(c2) : c2 - bf16r(c2);
+            v3 = k == H ? bf16r(c3) : c3 - bf16r(c3);
+        }
+        s.b2[kmaj(n, k, kChB)] = __float2bfloat16_rn(v2);
+        s.b3[kmaj(n, k, kChB)] = __float2bfloat16_rn(v3);
     }
     for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
         const int n = i >> 4, k = i & 15;
@@ -164,149 +263,43 @@ __device__ void load_infer_weights(InferSmem &s, const float *__restrict__ p) {
             const float hi = bf16r(b);
             v = k == 8 ? hi : b - hi;
         }
-        s.w1[n * LD1 + k] = __float2bfloat16_rn(v);
+        s.b1[kmaj(n, k, kChB1)] = __float2bfloat16_rn(v);
     }
-    for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
-        const int n = i >> 6, k = i & 63;
-        s.w4[n * LD + k] = __float2bfloat16_rn(n < 2 ? p[OFF_W4 + H * n + k] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        s.b2[i] = 0.5f * p[OFF_B2 + i];
-        s.b3[i] = 0.5f * p[OFF_B3 + i];
-    }
+    for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) s.w4[i / H][i % H] = bf16r(p[OFF_W4 + i]);
     if (threadIdx.x < 2) s.b4[threadIdx.x] = p[OFF_B4 + threadIdx.x];
-}
-
-// Four 8x8 BF16 blocks from shared memory (ldmatrix): lane l gives the
-// address of row l & 7 of block l >> 3 and receives, of every block, row
-// (l >> 2), elements 2 (l & 3) and 2 (l & 3) + 1.
-__device__ __forceinline__ void ldmatrix_x4(const void *row_addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                            uint32_t &r3) {
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(row_addr);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-
-// acc (16 x 64) += A (16 x 16 kk_steps) W^T, A in registers as mma A
-// fragments (fa, and with LO a second part fb of the same A), W [64][ld]
-// bf16 in shared memory (row n = output n). The B fragments of output tiles
-// j, j + 1 for one K step are one ldmatrix.x4.
-template <int KSTEPS, bool LO>
-__device__ __forceinline__ void warp_gemm_ldm(float acc[8][4], const uint32_t fa[][4], const uint32_t fb[][4],
-                                              const __nv_bfloat16 *W, int ld, int lane) {
-    const int q = lane >> 3, r = lane & 7;
-#pragma unroll
-    for (int kk = 0; kk < KSTEPS; ++kk) {
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            uint32_t b0, b1, c0, c1;
-            ldmatrix_x4(W + (8 * (j + (q >> 1)) + r) * ld + 16 * kk + 8 * (q & 1), b0, b1, c0, c1);
-            mma16816(acc[j], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
-            mma16816(acc[j + 1], fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], c0, c1);
-            if (LO) {
-                mma16816(acc[j], fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], b0, b1);
-                mma16816(acc[j + 1], fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], c0, c1);
-            }
-        }
+    // A columns 64..79 of every row: [1, 1, 0, ...] against the biases' two parts
+    for (int i = threadIdx.x; i < kTcRows * 16; i += blockDim.x) {
+        const int r = i >> 4, k = 64 + (i & 15);
+        s.a[kmaj(r, k, kChA)] = __float2bfloat16_rn(k < 66 ? 1.0f : 0.0f);
     }
 }
 
-// Activations h (accumulator layout) as two BF16 A-fragment parts, h_hi =
-// bf16(h) and h_lo = bf16(h - h_hi).
-__device__ __forceinline__ uint32_t pack_lo_bf16x2(float a, float b) {
-    return pack_bf16x2(a - bf16r(a), b - bf16r(b));
-}
-__device__ __forceinline__ void pack_afrag2(const float h[8][4], uint32_t fa[4][4], uint32_t fb[4][4]) {
-    pack_afrag(h, fa);
+// This thread's row of layer-1 A: [x_hi | x_lo], then [1, 1, 0 ...].
+__device__ __forceinline__ void tc_put_inputs(TcSmem &s, int row, const float x[4]) {
+    float hi[4], lo[4];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        fb[kk][0] = pack_lo_bf16x2(h[2 * kk][0], h[2 * kk][1]);
-        fb[kk][1] = pack_lo_bf16x2(h[2 * kk][2], h[2 * kk][3]);
-        fb[kk][2] = pack_lo_bf16x2(h[2 * kk + 1][0], h[2 * kk + 1][1]);
-        fb[kk][3] = pack_lo_bf16x2(h[2 * kk + 1][2], h[2 * kk + 1][3]);
+    for (int i = 0; i < 4; ++i) {
+        hi[i] = bf16r(x[i]);
+        lo[i] = x[i] - hi[i];
     }
-}
-
-// SiLU of z given h = z / 2.
-__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
-
-// Layer-1 A fragment of rows g (xl) and g + 8 (xh): this lane's K columns
-// 2t, 2t + 1 (t = 0, 1: high parts of inputs 2t, 2t + 1; t = 2, 3: low parts
-// of inputs 2t - 4, 2t - 3) and 2t + 8, 2t + 9 (t = 0: the two bias ones).
-__device__ __forceinline__ void layer1_afrag(const float xl[4], const float xh[4], int t, uint32_t fa[4]) {
-    const int i = 2 * (t & 1);
-    const bool lo = t >= 2;
-    auto part = [&](float v) {
-        const float hi = bf16r(v);
-        return lo ? v - hi : hi;
-    };
-    fa[0] = pack_bf16x2(part(xl[i]), part(xl[i + 1]));
-    fa[1] = pack_bf16x2(part(xh[i]), part(xh[i + 1]));
-    const uint32_t ones = pack_bf16x2(1.0f, 1.0f);
-    fa[2] = t == 0 ? ones : 0u;
-    fa[3] = t == 0 ? ones : 0u;
+    const uint4 c0 = make_uint4(pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], hi[3]), pack_bf16x2(lo[0], lo[1]),
+                                pack_bf16x2(lo[2], lo[3]));
+    const uint4 c1 = make_uint4(pack_bf16x2(1.0f, 1.0f), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(s.a + kmaj(row, 0, kChA)) = c0;
+    *reinterpret_cast<uint4 *>(s.a + kmaj(row, 8, kChA)) = c1;
 }
 
-// The network on the 16 rows of a warp tile; this thread supplies the inputs
-// of rows g and g + 8 and receives their outputs (on the lanes with t = 0).
-// Activations stay in registers: each layer's accumulators are packed into
-// the next layer's BF16 A fragments.
-__device__ void tile_forward(const InferSmem &s, const float xl[4], const float xh[4], int lane, float yl[2],
-                             float yh[2]) {
-    const int t = lane & 3;
-    float acc[8][4];
-    uint32_t fa[4][4], fb[4][4];
-    layer1_afrag(xl, xh, t, fa[0]);
-    zero_acc(acc);
-    warp_gemm_ldm<1, false>(acc, fa, fb, s.w1, LD1, lane);
+// SiLU of this thread's 64 accumulators (h = z / 2), as BF16 into its A row.
+__device__ __forceinline__ void tc_put_hidden(TcSmem &s, int row, const float v[64]) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j][e] = silu_h(acc[j][e]);
-    pack_afrag(acc, fa);
-    zero_acc(acc);
-    warp_gemm_ldm<4, false>(acc, fa, fb, s.w2, LD, lane);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = 8 * j + 2 * t;
-        const float2 bb = *reinterpret_cast<const float2 *>(s.b2 + c);
-        acc[j][0] = silu_h(acc[j][0] + bb.x);
-        acc[j][1] = silu_h(acc[j][1] + bb.y);
-        acc[j][2] = silu_h(acc[j][2] + bb.x);
-        acc[j][3] = silu_h(acc[j][3] + bb.y);
+    for (int c = 0; c < 8; ++c) {
+        uint4 u;
+        u.x = pack_bf16x2(silu_h(v[8 * c + 0]), silu_h(v[8 * c + 1]));
+        u.y = pack_bf16x2(silu_h(v[8 * c + 2]), silu_h(v[8 * c + 3]));
+        u.z = pack_bf16x2(silu_h(v[8 * c + 4]), silu_h(v[8 * c + 5]));
+        u.w = pack_bf16x2(silu_h(v[8 * c + 6]), silu_h(v[8 * c + 7]));
+        *reinterpret_cast<uint4 *>(s.a + kmaj(row, 8 * c, kChA)) = u;
     }
-    pack_afrag(acc, fa);
-    zero_acc(acc);
-    warp_gemm_ldm<4, false>(acc, fa, fb, s.w3, LD, lane);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = 8 * j + 2 * t;
-        const float2 bb = *reinterpret_cast<const float2 *>(s.b3 + c);
-        acc[j][0] = silu_h(acc[j][0] + bb.x);
-        acc[j][1] = silu_h(acc[j][1] + bb.y);
-        acc[j][2] = silu_h(acc[j][2] + bb.x);
-        acc[j][3] = silu_h(acc[j][3] + bb.y);
-    }
-    pack_afrag2(acc, fa, fb);
-    // layer 4: one N = 8 tile, K = 64 in four steps (two ldmatrix.x4, each
-    // the B fragments of two K steps)
-    float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const int q = lane >> 3, r = lane & 7;
-#pragma unroll
-    for (int kk = 0; kk < 4; kk += 2) {
-        uint32_t b0, b1, c0, c1;
-        ldmatrix_x4(s.w4 + r * LD + 16 * (kk + (q >> 1)) + 8 * (q & 1), b0, b1, c0, c1);
-        mma16816(o, fa[kk][0], fa[kk][1], fa[kk][2], fa[kk][3], b0, b1);
-        mma16816(o, fb[kk][0], fb[kk][1], fb[kk][2], fb[kk][3], b0, b1);
-        mma16816(o, fa[kk + 1][0], fa[kk + 1][1], fa[kk + 1][2], fa[kk + 1][3], c0, c1);
-        mma16816(o, fb[kk + 1][0], fb[kk + 1][1], fb[kk + 1][2], fb[kk + 1][3], c0, c1);
-    }
-    // o[0..1]: row g, outputs 2t, 2t + 1; o[2..3]: row g + 8 (outputs 0, 1 on t = 0)
-    yl[0] = o[0] + s.b4[0];
-    yl[1] = o[1] + s.b4[1];
-    yh[0] = o[2] + s.b4[0];
-    yh[1] = o[3] + s.b4[1];
 }
 
 struct RowIn {
@@ -332,6 +325,21 @@ __device__ __forceinline__ float row_alpha_d(const DevScene &sc, const RowIn &in
     return a;
 }
 
+// The held-out grid of the trained box (mode 2): cos, bin, s and thickness at
+// cell centres of a 17 x L x 5 x 5 grid.
+constexpr int kGridCos = 17, kGridS = 5, kGridD = 5;
+
+// Rows to evaluate: mode 0 explicit rows, mode 1 the renderer's queries
+// expanded over the L bins, mode 2 the held-out grid.
+__device__ __forceinline__ int64_t mlp_total_rows(const MlpRows &a) {
+    if (a.mode == 1) {
+        const int64_t nq0 = (int64_t)*a.n_queries;
+        return (nq0 < a.q_cap ? nq0 : a.q_cap) * a.sc.L;
+    }
+    if (a.mode == 2) return (int64_t)kGridCos * a.sc.L * kGridS * kGridD;
+    return a.n;
+}
+
 __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t total, RowIn &in) {
     if (r >= total) {
         in.c = 0.5f;
@@ -351,7 +359,7 @@ __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t t
         in.d = a.thick[r];
         in.mat = (int)a.mat;
         in.bin = b;
-    } else {
+    } else if (a.mode == 1) {
         const int64_t q = r / L;
         const float4 qq = a.queries[q];
         in.c = qq.x;
@@ -359,6 +367,19 @@ __device__ __forceinline__ bool row_input(const MlpRows &a, int64_t r, int64_t t
         in.d = qq.z;
         in.mat = __float_as_int(qq.w);
         in.bin = (int)(r - q * L);
+    } else {
+        int64_t q = r;
+        const int ic = (int)(q % kGridCos);
+        q /= kGridCos;
+        const int ib = (int)(q % L);
+        q /= L;
+        const int is = (int)(q % kGridS);
+        const int id = (int)(q / kGridS);
+        in.c = (ic + 0.5f) / kGridCos;
+        in.bin = ib;
+        in.s = (is + 0.5f) / kGridS;
+        in.d = a.thick_min + (a.thick_max - a.thick_min) * (id + 0.5f) / kGridD;
+        in.mat = (int)a.mat;
     }
     in.lam = __ldg(a.sc.lam + in.bin);
     return true;
@@ -371,43 +392,144 @@ __device__ __forceinline__ float2 exact_row(const MlpRows &a, const RowIn &in) {
     return make_float2(R_, T_);
 }
 
-// Rows are taken 32 at a time by a warp (two 16-row tiles). One row of each
-// batch, chosen by Philox, is also evaluated exactly; if it is off by more
-// than 1e-3 in R or T, or if any row lies outside the trained box, the whole
-// batch is evaluated exactly instead. The probes of 32 batches run together,
-// one per lane, so that a probe costs one lane's share of an exact evaluation
-// rather than a whole warp's.
+__device__ __forceinline__ bool row_in_box(const MlpRows &a, const RowIn &in) {
+    return in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f && in.s >= 0.0f && in.s <= 1.0f &&
+           in.d >= a.thick_min && in.d <= a.thick_max;
+}
+
+__device__ __forceinline__ void store_row(const MlpRows &a, int64_t r, float2 y) {
+    if (a.mode == 0) {
+        a.R[r] = y.x;
+        a.T[r] = y.y;
+    } else {
+        a.results[r] = y;
+    }
+}
+
+// The network over all rows, tile by tile (see the top of this section).
+// Writes the served (R, T) of every row; mode 2 instead records the largest
+// |error| against the exact slab. On a wait that runs out (the tensor core
+// never signalled completion) the CTA reports error 2 and stops.
 #ifndef SDDM_MLP_MINB
-#define SDDM_MLP_MINB 4   // resident inference blocks per SM asked of the register allocator: 64
-                          // registers with ~80 B of spills, 32 warps per SM
-#endif
-#ifndef SDDM_MLP_UNROLL_HALVES
-#define SDDM_MLP_UNROLL_HALVES 1   // the two 16-row tiles of a batch as one unrolled sequence
+#define SDDM_MLP_MINB 5   // resident 128-thread tile CTAs per SM (96 registers; shared memory admits 5)
 #endif
 template <bool FILMS>
-__global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
-    __shared__ InferSmem s;
-    __shared__ float2 out[8][32];
-    __shared__ float4 xin[8][32];   // per warp: the encoded inputs of its 32 rows
-    load_infer_weights(s, a.params);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    // A batch is 32 rows of one query's bins (renderer queries: a batch never
-    // mixes two glass evaluations, so its probe speaks for rows that share
-    // angle, state and thickness) or 32 consecutive explicit rows.
-    const int L = a.sc.L;
-    int64_t total = a.n, n_batches = (a.n + 31) / 32;
-    int nb = 1;
-    if (a.mode == 1) {
-        const int64_t nq0 = (int64_t)*a.n_queries;
-        const int64_t nq = nq0 < a.q_cap ? nq0 : a.q_cap;
-        total = nq * L;
-        nb = (L + 31) / 32;
-        n_batches = nq * nb;
+__global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
+    __shared__ TcSmem s;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar = smem_addr(&s.mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s.tmem)),
+                     "r"((uint32_t)kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t b_first = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;   // this warp's batches: b_first + k nwarps
-    unsigned long long n_fb = 0;
+    if (tid == 0) mbar_init(mbar);
+    tc_load_weights(s, a.params);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
+    const uint32_t sa = smem_addr(s.a), sb1 = smem_addr(s.b1), sb2 = smem_addr(s.b2), sb3 = smem_addr(s.b3);
+    constexpr uint32_t kSboA = kChA * 128, kSboB1 = kChB1 * 128, kSboB = kChB * 128;
+    const int64_t total = mlp_total_rows(a);
+    const int64_t n_tiles = (total + kTcRows - 1) / kTcRows;
+    if (a.rows && blockIdx.x == 0 && tid == 0) atomicAdd(a.rows, (unsigned long long)total);
+    uint32_t phase = 0;
+    // One layer: the A rows written by every thread are made visible to the
+    // tensor core, one thread issues the MMAs and waits for them; false (for
+    // the whole CTA) when the wait ran out.
+    auto layer = [&](int l) -> bool {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            if (l == 1) {
+                tc_mma(tmem, tc_desc(sa, 128, kSboA), tc_desc(sb1, 128, kSboB1), kIdescHidden, 0u);
+            } else {
+                const uint32_t sb = l == 2 ? sb2 : sb3;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    tc_mma(tmem, tc_desc(sa + 256 * ks, 128, kSboA), tc_desc(sb + 256 * ks, 128, kSboB), kIdescHidden,
+                           ks > 0 ? 1u : 0u);
+                tc_mma(tmem, tc_desc(sa + 1024, 128, kSboA), tc_desc(sb + 1024, 128, kSboB), kIdescHidden, 1u);
+            }
+            tc_commit(mbar);
+            const bool done = mbar_wait(mbar, phase);
+            if (!done && a.err && atomicCAS(a.err, 0, 2) == 0) {
+                a.err[1] = 20;   // surrogate inference: the tensor core did not complete
+                a.err[2] = l;
+            }
+            s_ok = done;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        tc_fence_after();
+        return s_ok != 0;
+    };
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t r = tile * kTcRows + tid;
+        RowIn in;
+        const bool valid = row_input(a, r, total, in);
+        float x[4];
+        features(in.c, in.lam, in.s, row_alpha_d<FILMS>(a.sc, in), x);
+        tc_put_inputs(s, tid, x);
+        float v[64];
+        if (!layer(1)) break;
+        tmem_ld64(taddr, v);
+        tc_put_hidden(s, tid, v);
+        if (!layer(2)) break;
+        tmem_ld64(taddr, v);
+        tc_put_hidden(s, tid, v);
+        if (!layer(3)) break;
+        tmem_ld64(taddr, v);
+        float y0 = s.b4[0], y1 = s.b4[1];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const float h = silu_h(v[j]);
+            y0 = fmaf(s.w4[0][j], h, y0);
+            y1 = fmaf(s.w4[1][j], h, y1);
+        }
+        const float2 y = make_float2(out_to_rt(y0), out_to_rt(y1));
+        if (valid) {
+            if (a.mode == 2) {
+                const float2 e = exact_row<FILMS>(a, in);
+                atomicMax(a.grid_err + 0, __float_as_uint(fabsf(e.x - y.x)));
+                atomicMax(a.grid_err + 1, __float_as_uint(fabsf(e.y - y.y)));
+            } else {
+                store_row(a, r, y);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTcCols)
+                     : "memory");
+    }
+}
+
+// Probe and fallback, after the network has served every row. A batch is up
+// to 32 rows of one query's bins (renderer queries: a batch never mixes two
+// glass evaluations, so its probe speaks for rows that share angle, state and
+// thickness) or 32 consecutive explicit rows. One row of each batch, chosen by
+// Philox, is evaluated exactly; if it is off by more than 1e-3 in R or T, or
+// if a row of the batch lies outside the trained box, the whole batch is
+// evaluated exactly instead. Lane k of a warp probes batch k of a round of 32
+// batches, so a probe costs one lane's share of an exact evaluation; failing
+// batches are then redone by the whole warp, one row per lane.
+template <bool FILMS>
+__global__ void __launch_bounds__(256) k_mlp_probe(MlpRows a) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int L = a.sc.L;
+    const int64_t total = mlp_total_rows(a);
+    const int nb = a.mode == 1 ? (L + 31) / 32 : 1;
+    const int64_t n_batches = a.mode == 1 ? total / L * nb : (total + 31) / 32;
     auto batch_rows = [&](int64_t b, int64_t &r0, int &nvalid) {
         if (a.mode == 1) {
             const int64_t qi = b / nb;
@@ -419,83 +541,40 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
             nvalid = total - r0 < 32 ? (int)(total - r0) : 32;
         }
     };
-    auto store = [&](int64_t r, float2 y) {
-        if (a.mode == 0) {
-            a.R[r] = y.x;
-            a.T[r] = y.y;
-        } else {
-            a.results[r] = y;
-        }
-    };
-    // Rounds of up to 32 of the warp's batches: the network serves every row
-    // of them, then lane k probes batch k (one exact row each, all lanes at
-    // once), then every batch whose probe or trained box failed is evaluated
-    // exactly, row per lane.
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t b_first = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;
+    unsigned long long n_fb = 0;
     for (int64_t k0 = 0; b_first + k0 * nwarps < n_batches; k0 += 32) {
-        unsigned box_bad = 0;
-        int n_round = 0;
-        for (int k = 0; k < 32; ++k) {
-            const int64_t b = b_first + (k0 + k) * nwarps;
-            if (b >= n_batches) break;
-            ++n_round;
+        const int64_t b = b_first + (k0 + lane) * nwarps;
+        int bad = 0;
+        if (b < n_batches) {
             int64_t r0;
             int nvalid;
             batch_rows(b, r0, nvalid);
-            // each lane encodes the row of its own index once (the coating
-            // films' absorbance loop included); the tiles read their rows'
-            // inputs from the warp's staging row
-            {
-                RowIn in;
-                row_input(a, lane < nvalid ? r0 + lane : total, total, in);
-                float xr[4];
-                features(in.c, in.lam, in.s, row_alpha_d<FILMS>(a.sc, in), xr);
-                xin[w][lane] = make_float4(xr[0], xr[1], xr[2], xr[3]);
-            }
-            __syncwarp();
-#if SDDM_MLP_UNROLL_HALVES
-#pragma unroll
-#else
-#pragma unroll 1
-#endif
-            for (int half = 0; half < 2; ++half) {
-                if (half == 1 && nvalid <= 16) break;   // warp-uniform: no valid row in the second tile
-                const int kl = 16 * half + g, kh = kl + 8;
-                float yl[2], yh[2];
-                const float4 ql = xin[w][kl], qh = xin[w][kh];
-                const float xl[4] = {ql.x, ql.y, ql.z, ql.w}, xh[4] = {qh.x, qh.y, qh.z, qh.w};
-                tile_forward(s, xl, xh, lane, yl, yh);
-                if (t == 0) {
-                    out[w][kl] = make_float2(out_to_rt(yl[0]), out_to_rt(yl[1]));
-                    out[w][kh] = make_float2(out_to_rt(yh[0]), out_to_rt(yh[1]));
+            RowIn in;
+            // the trained box: one query's rows share cos, s and thickness and
+            // their wavelengths rise with the bin, so its first and last rows
+            // decide; explicit rows are checked one by one
+            if (a.mode == 1) {
+                row_input(a, r0, total, in);
+                bad = !row_in_box(a, in);
+                row_input(a, r0 + nvalid - 1, total, in);
+                bad |= !row_in_box(a, in);
+            } else {
+                for (int i = 0; i < nvalid; ++i) {
+                    row_input(a, r0 + i, total, in);
+                    bad |= !row_in_box(a, in);
                 }
             }
-            __syncwarp();
-            RowIn in;
-            const bool valid = row_input(a, lane < nvalid ? r0 + lane : total, total, in);
-            const bool in_box = in.c >= 0.0f && in.c <= 1.0f && in.lam >= 380.0f && in.lam <= 780.0f &&
-                                in.s >= 0.0f && in.s <= 1.0f && in.d >= a.thick_min && in.d <= a.thick_max;
-            if (!__all_sync(kFull, !valid || in_box)) box_bad |= 1u << k;
-            if (valid) store(r0 + lane, out[w][lane]);
-            __syncwarp();
-        }
-        if (a.raw) continue;
-        // probes: lane k takes the Philox-chosen row of batch k of the round
-        int bad = 0;
-        if (lane < n_round) {
-            const int64_t b = b_first + (k0 + lane) * nwarps;
-            int64_t r0;
-            int nvalid;
-            batch_rows(b, r0, nvalid);
             const uint4 pr = philox4x32_10(make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0u, kSlotProbe),
                                            a.probe_key, 0x50524f42u);
             const int64_t r = r0 + (int)(pr.x % (uint32_t)nvalid);
-            RowIn in;
             row_input(a, r, total, in);
             const float2 e = exact_row<FILMS>(a, in);
             const float2 y = a.mode == 0 ? make_float2(a.R[r], a.T[r]) : a.results[r];
-            bad = fabsf(e.x - y.x) > kMlpProbeTol || fabsf(e.y - y.y) > kMlpProbeTol;
+            bad |= fabsf(e.x - y.x) > kMlpProbeTol || fabsf(e.y - y.y) > kMlpProbeTol;
         }
-        unsigned fall = __ballot_sync(kFull, bad) | box_bad;
+        unsigned fall = __ballot_sync(kFull, bad);
         while (fall) {
             const int k = __ffs(fall) - 1;
             fall &= fall - 1;
@@ -503,10 +582,9 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
             int nvalid;
             batch_rows(b_first + (k0 + k) * nwarps, r0, nvalid);
             RowIn in;
-            if (row_input(a, lane < nvalid ? r0 + lane : total, total, in)) store(r0 + lane, exact_row<FILMS>(a, in));
+            if (lane < nvalid && row_input(a, r0 + lane, total, in)) store_row(a, r0 + lane, exact_row<FILMS>(a, in));
             if (lane == 0) ++n_fb;
         }
-        __syncwarp();
     }
     if (a.fallbacks && n_fb) atomicAdd(a.fallbacks, n_fb);
     if (a.batches && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.batches, (unsigned long long)n_batches);
@@ -516,11 +594,7 @@ __global__ void __launch_bounds__(256, SDDM_MLP_MINB) k_mlp_rows(MlpRows a) {
 // glass evaluations of a bounce as one dense, divergence-free pass.
 template <bool FILMS>
 __global__ void __launch_bounds__(256) k_slab_rows(MlpRows a) {
-    int64_t total = a.n;
-    if (a.mode == 1) {
-        const int64_t nq = (int64_t)*a.n_queries;
-        total = (nq < a.q_cap ? nq : a.q_cap) * a.sc.L;
-    }
+    const int64_t total = mlp_total_rows(a);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
         RowIn in;
@@ -876,83 +950,55 @@ __global__ void k_mlp_init(float *p, uint32_t seed) {
     p[i] = bound * (2.0f * u01(u.x) - 1.0f);
 }
 
-// Max |error| of R and T over a held-out grid of the trained box (cos, bin, s, d).
-__global__ void k_mlp_grid_error(MlpRows a, unsigned int *max_err) {
-    __shared__ InferSmem s;
-    load_infer_weights(s, a.params);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int L = a.sc.L;
-    const int nc = 17, ns = 5, nd = 5;
-    const int64_t total = (int64_t)nc * L * ns * nd;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    auto grid_in = [&](int64_t r, RowIn &in) {
-        int64_t q = r;
-        const int ic = (int)(q % nc);
-        q /= nc;
-        const int ib = (int)(q % L);
-        q /= L;
-        const int is = (int)(q % ns);
-        q /= ns;
-        const int id = (int)q;
-        in.c = (ic + 0.5f) / nc;
-        in.bin = ib;
-        in.lam = __ldg(a.sc.lam + ib);
-        in.s = (is + 0.5f) / ns;
-        in.d = a.thick_min + (a.thick_max - a.thick_min) * (id + 0.5f) / nd;
-        in.mat = (int)a.mat;
-    };
-    for (int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w; b * 16 < total; b += nwarps) {
-        const int64_t r0 = b * 16;
-        RowIn il, ih;
-        grid_in(min(r0 + g, total - 1), il);
-        grid_in(min(r0 + g + 8, total - 1), ih);
-        float xl[4], xh[4], yl[2], yh[2];
-        features(il.c, il.lam, il.s, row_alpha_d(a.sc, il), xl);
-        features(ih.c, ih.lam, ih.s, row_alpha_d(a.sc, ih), xh);
-        tile_forward(s, xl, xh, lane, yl, yh);
-        if (t == 0) {
-            const float2 el = exact_row(a, il), eh = exact_row(a, ih);
-            atomicMax(max_err + 0,
-                      __float_as_uint(fmaxf(fabsf(el.x - out_to_rt(yl[0])), fabsf(eh.x - out_to_rt(yh[0])))));
-            atomicMax(max_err + 1,
-                      __float_as_uint(fmaxf(fabsf(el.y - out_to_rt(yl[1])), fabsf(eh.y - out_to_rt(yh[1])))));
-        }
-        __syncwarp();
-    }
-}
-
 }  // namespace
 
 size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 
-#ifndef SDDM_MLP_BLOCKS_PER_SM
-#define SDDM_MLP_BLOCKS_PER_SM 4   // inference blocks (8 warps, ~41 KB shared memory) per SM
-#endif
 // Blocks of a grid-stride row kernel: per SM, the most that fit at once (at
 // most `cap`), so that the grid is one whole wave.
 template <typename K>
-static int resident_per_sm(K kernel, int cap) {
+static int resident_per_sm(K kernel, int threads, int cap) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) return cap;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) return cap;
     return n < cap ? n : cap;
 }
 
-cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
-    const int blocks = sm_count * (a.sc.mat_nfilm ? resident_per_sm(k_mlp_rows<true>, SDDM_MLP_BLOCKS_PER_SM)
-                                                  : resident_per_sm(k_mlp_rows<false>, SDDM_MLP_BLOCKS_PER_SM));
+// Tile CTAs per SM: as many as the registers and shared memory allow
+// (__launch_bounds__ asks for SDDM_MLP_MINB). Tensor memory has 512 columns
+// per SM and each CTA holds kTcCols of them, so up to 512 / kTcCols resident
+// CTAs never wait on one another's allocation.
+static_assert(SDDM_MLP_MINB * kTcCols <= 512, "tensor-memory columns of the resident tile CTAs");
+template <bool FILMS>
+static cudaError_t launch_mlp_net(const MlpRows &a, int sm_count, cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_net<FILMS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_mlp_net<FILMS><<<sm_count * SDDM_MLP_MINB, kTcRows, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1) {
+    cudaError_t e = ev0 ? cudaEventRecord(ev0, stream) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = a.sc.mat_nfilm ? launch_mlp_net<true>(a, sm_count, stream) : launch_mlp_net<false>(a, sm_count, stream);
+    if (e == cudaSuccess && ev1) e = cudaEventRecord(ev1, stream);
+    if (e != cudaSuccess || a.raw) return e;
     if (a.sc.mat_nfilm)
-        k_mlp_rows<true><<<blocks, 256, 0, stream>>>(a);
+        k_mlp_probe<true><<<sm_count * resident_per_sm(k_mlp_probe<true>, 256, 8), 256, 0, stream>>>(a);
     else
-        k_mlp_rows<false><<<blocks, 256, 0, stream>>>(a);
+        k_mlp_probe<false><<<sm_count * resident_per_sm(k_mlp_probe<false>, 256, 8), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream) {
     if (a.sc.mat_nfilm)
-        k_slab_rows<true><<<sm_count * resident_per_sm(k_slab_rows<true>, 8), 256, 0, stream>>>(a);
+        k_slab_rows<true><<<sm_count * resident_per_sm(k_slab_rows<true>, 256, 8), 256, 0, stream>>>(a);
     else
-        k_slab_rows<false><<<sm_count * resident_per_sm(k_slab_rows<false>, 8), 256, 0, stream>>>(a);
+        k_slab_rows<false><<<sm_count * resident_per_sm(k_slab_rows<false>, 256, 8), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -989,15 +1035,18 @@ cudaError_t launch_mlp_init(float *params, uint32_t seed, cudaStream_t stream) {
 }
 
 cudaError_t launch_mlp_grid_error(const float *params, const DevScene &sc, uint32_t mat, float dmin, float dmax,
-                                  unsigned int *max_err, cudaStream_t stream) {
+                                  unsigned int *max_err, int *err, int sm_count, cudaStream_t stream) {
     MlpRows a{};
     a.params = params;
     a.sc = sc;
     a.mat = mat;
     a.thick_min = dmin;
     a.thick_max = dmax;
-    k_mlp_grid_error<<<152, 256, 0, stream>>>(a, max_err);
-    return cudaGetLastError();
+    a.mode = 2;
+    a.raw = 1;
+    a.grid_err = max_err;
+    a.err = err;
+    return launch_mlp_rows(a, sm_count, stream);
 }
 
 }  // namespace sddm

@@ -829,6 +829,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
 
     if ((e = cudaEventRecord(ctx->ev0, s)) != cudaSuccess) return cuda_fail(e, "sddm_render: event");
     ctx->ddm_buf.events_used = 0;
+    ctx->ddm_buf.mlp_events_used = 0;
     int64_t launches = 0;
     const int time_trace = (ctx->profile & SDDM_PROFILE_TIME_TRACE) != 0;
     const int count_trav = (ctx->profile & SDDM_PROFILE_COUNT_TRAVERSAL) != 0;
@@ -1015,6 +1016,14 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         }
         st->trace_ms = tms;
         st->trace_launches = ctx->ddm_buf.events_used / 2;
+        double mms = 0.0;
+        for (int k = 0; k + 1 < ctx->ddm_buf.mlp_events_used; k += 2) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ctx->ddm_buf.mlp_events[k], ctx->ddm_buf.mlp_events[k + 1]);
+            mms += x;
+        }
+        st->mlp_ms = mms;
+        st->mlp_rows = (int64_t)cnt[9];
     }
     return SDDM_OK;
 }
@@ -1229,6 +1238,8 @@ int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d,
         tot.cache_loads += sj.cache_loads;
         tot.cache_hits += sj.cache_hits;
         tot.cache_bytes_loaded += sj.cache_bytes_loaded;
+        tot.mlp_ms += sj.mlp_ms;
+        tot.mlp_rows += sj.mlp_rows;
         tot.gpu_ms += sj.gpu_ms;
         tot.kernel_launches += sj.kernel_launches + (j > 1 ? 1 : 0);
         ptot.photons += pj.photons;
@@ -1477,14 +1488,21 @@ int sddm_mlp_train(sddm_ctx *ctx, uint32_t mat, const sddm_mlp_train_opts *opts,
     }
     if ((e = cudaEventRecord(ctx->ev1, s))) return cuda_fail(e, "sddm_mlp_train: event");
     unsigned int *errs = reinterpret_cast<unsigned int *>(ctx->mlp_scalar.as<char>() + 16);
-    if ((e = cudaMemsetAsync(errs, 0, 8, s)) ||
-        (e = launch_mlp_grid_error(net->params.as<float>(), ctx->dev, mat, o.thick_min, o.thick_max, errs, s)))
+    if ((e = ctx->d_err.ensure(16)) || (e = cudaMemsetAsync(ctx->d_err.p, 0, 16, s)) ||
+        (e = cudaMemsetAsync(errs, 0, 8, s)) ||
+        (e = launch_mlp_grid_error(net->params.as<float>(), ctx->dev, mat, o.thick_min, o.thick_max, errs,
+                                   ctx->d_err.as<int>(), ctx->sm_count, s)))
         return cuda_fail(e, "sddm_mlp_train: held-out error");
     float loss = 0.f;
     unsigned int me[2] = {0, 0};
+    int derr[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(&loss, ctx->mlp_scalar.p, 4, cudaMemcpyDeviceToHost, s)) ||
-        (e = cudaMemcpyAsync(me, errs, 8, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+        (e = cudaMemcpyAsync(me, errs, 8, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(derr, ctx->d_err.p, sizeof derr, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
         return cuda_fail(e, "sddm_mlp_train: execution");
+    if (derr[0] != 0)
+        return fail(SDDM_ERR_TIMEOUT, "sddm_mlp_train: the surrogate's tensor-core evaluation did not complete");
     // the training samples are not needed afterwards
     ctx->mlp_X.release();
     ctx->mlp_Y.release();
@@ -1652,10 +1670,18 @@ int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, 
         a.mode = 0;
         a.raw = mode == SDDM_BSDF_MLP_RAW;
         a.fallbacks = nullptr;
+        int derr[4] = {0, 0, 0, 0};
         cudaError_t e = cudaSetDevice(ctx->device);
+        if (e == cudaSuccess) e = ctx->d_err.ensure(16);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err.p, 0, 16, ctx->stream);
+        a.err = ctx->d_err.as<int>();
         if (e == cudaSuccess) e = launch_mlp_rows(a, ctx->sm_count, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(derr, ctx->d_err.p, sizeof derr, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-        return e == cudaSuccess ? SDDM_OK : cuda_fail(e, "sddm_glass_eval (surrogate)");
+        if (e != cudaSuccess) return cuda_fail(e, "sddm_glass_eval (surrogate)");
+        if (derr[0] != 0)
+            return fail(SDDM_ERR_TIMEOUT, "sddm_glass_eval: the surrogate's tensor-core evaluation did not complete");
+        return SDDM_OK;
     }
     if (mode != SDDM_BSDF_EXACT) return fail(SDDM_ERR_INVALID_ARG, "sddm_glass_eval: unknown mode");
     cudaError_t e = cudaSetDevice(ctx->device);

@@ -85,8 +85,11 @@ struct DDMBuffers {
     size_t bytes = 0;
     std::vector<cudaEvent_t> events;   // start/stop pairs of timed trace launches
     int events_used = 0;
+    std::vector<cudaEvent_t> mlp_events;   // start/stop pairs of timed surrogate-network launches
+    int mlp_events_used = 0;
     ~DDMBuffers();
     cudaError_t event_pair(cudaEvent_t &a, cudaEvent_t &b);
+    cudaError_t mlp_event_pair(cudaEvent_t &a, cudaEvent_t &b);
 };
 
 struct DDMRun {
@@ -97,7 +100,8 @@ struct DDMRun {
     int max_depth;
     float *sample_xyz;
     int32_t *first_prim;
-    unsigned long long *counters;   // ext, shadow, glass, crossings, fallbacks, nodes, tris, visits, mlp batches
+    unsigned long long *counters;   // ext, shadow, glass, crossings, fallbacks, nodes, tris, visits, mlp batches,
+                                    // mlp rows
     int *error_flag;
     int sm_count, blocks_per_sm;
     int64_t queue_capacity;

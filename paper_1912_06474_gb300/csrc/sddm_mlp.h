@@ -12,8 +12,9 @@ constexpr int kMlpParams = 8770;
 constexpr int kMlpRowsPerCta = 64;       // training tile
 constexpr float kMlpProbeTol = 1e-3f;    // |dR|, |dT| above which a 32-row batch falls back to exact
 
-// Rows to evaluate: either explicit per-row inputs (test hook) or the
-// renderer's glass queries, each expanded over the L wavelength bins.
+// Rows to evaluate: explicit per-row inputs (mode 0, the test hook), the
+// renderer's glass queries, each expanded over the L wavelength bins (mode
+// 1), or a held-out grid of the trained box (mode 2, training report).
 struct MlpRows {
     const float *params;              // FP32 master weights [8770]
     DevScene sc;
@@ -34,8 +35,15 @@ struct MlpRows {
     int raw;                          // 1: network output only, no probe or fallback
     unsigned long long *fallbacks;    // 32-row batches that fell back to the exact slab
     unsigned long long *batches;      // 32-row batches evaluated (probe batches; NULL: not counted)
+    int *err;                         // device error word [4] (NULL: not reported); 2 = a wait ran out
+    unsigned int *grid_err;           // mode 2: largest |dR|, |dT| as float bits [2]
+    unsigned long long *rows;         // rows the network evaluated (NULL: not counted)
 };
-cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream);
+// The network over every row (tensor cores), then, unless raw, the probes
+// and the exact fallback of failing batches: two kernels on `stream`. With
+// ev0 / ev1 given, they are recorded around the network kernel.
+cudaError_t launch_mlp_rows(const MlpRows &a, int sm_count, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                            cudaEvent_t ev1 = nullptr);
 // The exact slab over the same rows (no network).
 cudaError_t launch_slab_rows(const MlpRows &a, int sm_count, cudaStream_t stream);
 
@@ -56,7 +64,8 @@ cudaError_t launch_mlp_data(const DevScene &sc, uint32_t mat, float state_unused
                             float thick_min, float thick_max, float *X, float *Y, cudaStream_t stream);
 cudaError_t launch_mlp_init(float *params, uint32_t seed, cudaStream_t stream);
 cudaError_t launch_mlp_grid_error(const float *params, const DevScene &sc, uint32_t mat, float thick_min,
-                                  float thick_max, unsigned int *max_err2, cudaStream_t stream);
+                                  float thick_max, unsigned int *max_err2, int *err, int sm_count,
+                                  cudaStream_t stream);
 size_t mlp_train_smem_bytes();
 
 }  // namespace sddm

@@ -79,7 +79,8 @@ class Stats(C.Structure):
                 ("gpu_ms", C.c_double), ("kernel_launches", C.c_int64), ("trace_ms", C.c_double),
                 ("trace_launches", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("ray_visits", C.c_int64), ("mlp_batches", C.c_int64), ("cache_loads", C.c_int64),
-                ("cache_hits", C.c_int64), ("cache_bytes_loaded", C.c_int64)]
+                ("cache_hits", C.c_int64), ("cache_bytes_loaded", C.c_int64), ("mlp_ms", C.c_double),
+                ("mlp_rows", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
