@@ -149,7 +149,6 @@ struct __align__(128) TcSmem {
     float b4[2];
     unsigned long long mbar;
     uint32_t tmem;
-    int abort;
 };
 
 // Element offset of (row, k) in a K-major operand of `nch` 16-byte chunks per row.
@@ -416,7 +415,6 @@ __device__ __forceinline__ void store_row(const MlpRows &a, int64_t r, float2 y)
 template <bool FILMS>
 __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
     __shared__ TcSmem s;
-    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t mbar = smem_addr(&s.mbar);
     if (warp == 0) {
@@ -439,13 +437,15 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
     const int64_t n_tiles = (total + kTcRows - 1) / kTcRows;
     if (a.rows && blockIdx.x == 0 && tid == 0) atomicAdd(a.rows, (unsigned long long)total);
     uint32_t phase = 0;
+    bool failed = false;   // this thread's wait on the tensor core ran out
     // One layer: the A rows written by every thread are made visible to the
-    // tensor core, one thread issues the MMAs and waits for them; false (for
-    // the whole CTA) when the wait ran out.
+    // tensor core, the CTA synchronises (and learns whether any thread's
+    // previous wait ran out: then it stops, false), one thread issues the
+    // MMAs, and every thread waits on the mbarrier for their completion.
     auto layer = [&](int l) -> bool {
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(failed)) return false;
         if (tid == 0) {
             tc_fence_after();
             if (l == 1) {
@@ -459,17 +459,11 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
                 tc_mma(tmem, tc_desc(sa + 1024, 128, kSboA), tc_desc(sb + 1024, 128, kSboB), kIdescHidden, 1u);
             }
             tc_commit(mbar);
-            const bool done = mbar_wait(mbar, phase);
-            if (!done && a.err && atomicCAS(a.err, 0, 2) == 0) {
-                a.err[1] = 20;   // surrogate inference: the tensor core did not complete
-                a.err[2] = l;
-            }
-            s_ok = done;
         }
+        failed = !mbar_wait(mbar, phase);
         phase ^= 1u;
-        __syncthreads();
         tc_fence_after();
-        return s_ok != 0;
+        return true;
     };
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t r = tile * kTcRows + tid;
@@ -504,6 +498,10 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
                 store_row(a, r, y);
             }
         }
+    }
+    if (failed && a.err && atomicCAS(a.err, 0, 2) == 0) {
+        a.err[1] = 20;   // surrogate inference: the tensor core did not complete
+        a.err[2] = (int)blockIdx.x;
     }
     tc_fence_before();
     __syncthreads();
