@@ -138,7 +138,10 @@ typedef struct {
 enum {
     SDDM_PROFILE_TIME_TRACE = 1,        /* CUDA events around every trace and surrogate-network launch */
     SDDM_PROFILE_COUNT_TRAVERSAL = 2,   /* count nodes, triangle tests and ray visits */
-    SDDM_PROFILE_EAGER = 4              /* launch every kernel from the host (no CUDA graph replay) */
+    SDDM_PROFILE_EAGER = 4,             /* launch every kernel from the host (no CUDA graph replay) */
+    SDDM_PROFILE_TEST_MLP_TIMEOUT = 8   /* test of the failure path: the first CTA of the surrogate network
+                                           issues no layer-1 MMA, so its bounded wait on the tensor core runs
+                                           out (after 2^10 tries); the call returns SDDM_ERR_TIMEOUT */
 };
 
 /* ---------------------------------------------------------------- context */

@@ -140,6 +140,7 @@ constexpr int kChA = 10;              // A chunks per 8-row group: 8 activations
 constexpr int kChB1 = 2;              // layer-1 B: K = 16
 constexpr int kChB = 10;              // layers 2, 3 B: K = 64 + bias step
 constexpr uint32_t kMbarTries = 1u << 22;   // bounded waits: ~seconds, then the CTA reports and stops
+constexpr uint32_t kMbarTriesTest = 1u << 10;   // the failure-path test's wait on an MMA never issued
 
 struct __align__(128) TcSmem {
     __nv_bfloat16 a[kTcRows * kChA * 8];    // activations / inputs, K-major core matrices
@@ -193,8 +194,8 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t i = 0; i < kMbarTries; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t tries) {
+    for (uint32_t i = 0; i < tries; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -438,6 +439,9 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
     if (a.rows && blockIdx.x == 0 && tid == 0) atomicAdd(a.rows, (unsigned long long)total);
     uint32_t phase = 0;
     bool failed = false;   // this thread's wait on the tensor core ran out
+    // failure-path test: CTA 0 issues nothing, so its first wait runs out
+    const bool skip = a.test_timeout && blockIdx.x == 0;
+    const uint32_t tries = skip ? kMbarTriesTest : kMbarTries;
     // One layer: the A rows written by every thread are made visible to the
     // tensor core, the CTA synchronises (and learns whether any thread's
     // previous wait ran out: then it stops, false), one thread issues the
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
         fence_async_smem();
         tc_fence_before();
         if (__syncthreads_or(failed)) return false;
-        if (tid == 0) {
+        if (tid == 0 && !skip) {
             tc_fence_after();
             if (l == 1) {
                 tc_mma(tmem, tc_desc(sa, 128, kSboA), tc_desc(sb1, 128, kSboB1), kIdescHidden, 0u);
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
             }
             tc_commit(mbar);
         }
-        failed = !mbar_wait(mbar, phase);
+        failed = !mbar_wait(mbar, phase, tries);
         phase ^= 1u;
         tc_fence_after();
         return true;

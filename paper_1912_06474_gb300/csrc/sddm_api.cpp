@@ -1634,7 +1634,8 @@ int sddm_mlp_grad(sddm_ctx *ctx, int n, const float *X, const float *Y, const fl
 
 int sddm_set_profiling(sddm_ctx *ctx, int flags) {
     if (!ctx) return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: ctx is NULL");
-    if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL | SDDM_PROFILE_EAGER))
+    if (flags & ~(SDDM_PROFILE_TIME_TRACE | SDDM_PROFILE_COUNT_TRAVERSAL | SDDM_PROFILE_EAGER |
+                  SDDM_PROFILE_TEST_MLP_TIMEOUT))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_set_profiling: unknown flag");
     ctx->profile = flags;
     ctx->graphs_enabled = flags == 0;   // events inside a replayed graph give no elapsed times
@@ -1670,6 +1671,7 @@ int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, 
         a.mode = 0;
         a.raw = mode == SDDM_BSDF_MLP_RAW;
         a.fallbacks = nullptr;
+        a.test_timeout = (ctx->profile & SDDM_PROFILE_TEST_MLP_TIMEOUT) != 0;
         int derr[4] = {0, 0, 0, 0};
         cudaError_t e = cudaSetDevice(ctx->device);
         if (e == cudaSuccess) e = ctx->d_err.ensure(16);

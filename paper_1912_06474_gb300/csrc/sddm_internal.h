@@ -13,7 +13,7 @@ namespace sddm {
 
 // Statistics counters of a render call, u64 each (layout at DevScene users'
 // `counters` fields): ext, shadow, glass, crossings, fallbacks, nodes, tris,
-// visits, surrogate batches; the rest spare.
+// visits, surrogate batches, surrogate rows; the rest spare.
 constexpr int kNumCounters = 16;
 
 constexpr int kMaxL = 256;

@@ -38,6 +38,7 @@ struct MlpRows {
     int *err;                         // device error word [4] (NULL: not reported); 2 = a wait ran out
     unsigned int *grid_err;           // mode 2: largest |dR|, |dT| as float bits [2]
     unsigned long long *rows;         // rows the network evaluated (NULL: not counted)
+    int test_timeout;                 // 1: CTA 0 issues no layer-1 MMA and waits 2^10 tries (failure-path test)
 };
 // The network over every row (tensor cores), then, unless raw, the probes
 // and the exact fallback of failing batches: two kernels on `stream`. With

@@ -363,11 +363,13 @@ class Context:
                     paths_in_flight=best.paths_in_flight, bvh_in_host_memory=bool(best.bvh_in_host_memory),
                     cell_cache_bytes=best.cell_cache_bytes, continue_cells=bool(best.continue_cells))
 
-    def set_profiling(self, time_trace=False, count_traversal=False, eager=False):
+    def set_profiling(self, time_trace=False, count_traversal=False, eager=False, test_mlp_timeout=False):
         """sddm_set_profiling: per-launch trace-kernel events, traversal counters,
-        or eager launches (all three disable CUDA graph replay)."""
+        or eager launches (all three disable CUDA graph replay); test_mlp_timeout
+        makes the surrogate network's wait on the tensor core run out (a test
+        of the failure path)."""
         _check(lib.sddm_set_profiling(self._h, (1 if time_trace else 0) | (2 if count_traversal else 0)
-                                      | (4 if eager else 0)))
+                                      | (4 if eager else 0) | (8 if test_mlp_timeout else 0)))
 
     # -- learned glass surrogate ------------------------------------------------
     def mlp_train(self, mat, samples=0, steps=0, batch=0, lr=0.0, seed=0, thick_min=0.0, thick_max=0.0,

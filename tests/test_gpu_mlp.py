@@ -174,3 +174,31 @@ def test_checkpoint_round_trip(sddm, room41, trained, tmp_path):
     rep2 = ctx2.mlp_train(g, steps=200, resume=True, seed=7, samples=1 << 18)
     assert rep2["steps"] == rep["steps"] + 200
     ctx2.close()
+
+
+def test_tensor_core_wait_runs_out_and_reports(sddm, room41):
+    """Failure path of the surrogate's bounded wait on the tensor core: with
+    the test switch the first CTA issues no MMA, its wait on the mbarrier runs
+    out after its try limit, the kernel frees its tensor memory and returns,
+    and the call reports SDDM_ERR_TIMEOUT. The context stays usable: the same
+    rows evaluated afterwards equal a fresh evaluation."""
+    rng = np.random.default_rng(41)
+    ctx = sddm.Context(0)
+    ctx.set_scene(room41)
+    ctx.build()
+    g = room41.glass_materials()[0]
+    ctx.mlp_set_weights(g, _xavier(rng))
+    n = 4096
+    args = [torch.from_numpy(a).cuda() for a in (rng.uniform(0, 1, n).astype(np.float32),
+                                                 rng.integers(0, room41.L, n).astype(np.int32),
+                                                 rng.uniform(0, 1, n).astype(np.float32),
+                                                 np.full(n, 0.004, np.float32))]
+    R0, T0 = ctx.glass_eval(g, *args, mode="mlp_raw")
+    ctx.set_profiling(test_mlp_timeout=True)
+    with pytest.raises(sddm.SddmError) as ei:
+        ctx.glass_eval(g, *args, mode="mlp_raw")
+    assert ei.value.code == sddm.ERR_TIMEOUT
+    ctx.set_profiling()
+    R1, T1 = ctx.glass_eval(g, *args, mode="mlp_raw")
+    assert torch.equal(R0, R1) and torch.equal(T0, T1)
+    ctx.close()
