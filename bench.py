@@ -8,6 +8,11 @@ suns behind them, a ceiling lamp -- at 512x512 px, 16 spp, max depth 5, 41
 wavelength bins, traced by domain decomposition over a 4x4x2 grid of
 subdomains with the glass evaluated by the learned surrogate (probe and exact
 fallback on); --method megakernel / --bsdf exact select the other variants.
+Hand-off schedule (--handoff-waves, default 1): in the first wave of a bounce
+every ray leaving its subdomain is handed to the neighbour's queue; the second
+wave traces the rays from those queues and carries the few that cross further
+faces on in the same thread, instead of one more wave (launch, sort, barrier)
+per face; 0 hands off in every wave (dims x + y + z - 2 waves).
 
 value   = (extension + shadow segments of all ranks) / (max over ranks of the
           summed device time of the K timed steps), inputs resident in HBM,
@@ -17,9 +22,10 @@ value_eager = the same steps launched eagerly with CUDA events around every
           trace launch (these events give the roofline's kernel time).
 arms    = the same metric for the other variants on the same workload: DDM
           with the exact slab, the plain global-BVH megakernel with the exact
-          slab (the comparison the metric names), and the DDM with the ray
-          carried across subdomain faces by its lane (continue_cells) and
-          with a single subdomain.
+          slab (the comparison the metric names), and the DDM with the
+          neighbour-queue hand-off in every wave, with the ray carried across
+          every face by its thread (continue_cells), and with a single
+          subdomain.
 e2e     = the same metric through sddm_render_host: result image copied back
           to pinned host memory inside the timed region.
 roofline: the trace kernel (k_trace_wave for DDM, k_megakernel for the plain
@@ -72,6 +78,17 @@ def _peaks():
 # MAC; algorithmic, the padding not counted. Layer 4 (64 x 2) runs on the FP32
 # pipes and is left out.
 MLP_TENSOR_FLOP_PER_ROW = 2 * (4 * 64 + 64 * 64 + 64 * 64)
+
+
+def _handoff_name(args):
+    if getattr(args, "method", "ddm") != "ddm":
+        return None
+    if args.continue_cells:
+        return "lane continues"
+    if args.handoff_waves:
+        k = args.handoff_waves
+        return f"neighbour queue for {k} wave{'s' if k > 1 else ''}, then the thread carries the rest"
+    return "neighbour queue"
 
 
 def _bf16_peak():
@@ -281,8 +298,8 @@ def run(args):
     ctx.set_scene(scene)
     t0 = time.perf_counter()
     ctx.build(grid=grid, blocks_per_sm=args.blocks_per_sm, paths_in_flight=args.paths_in_flight,
-              continue_cells=args.continue_cells)
-    cfg["ddm_handoff"] = "lane continues" if args.continue_cells else "neighbour queue"
+              continue_cells=args.continue_cells, handoff_waves=args.handoff_waves)
+    cfg["ddm_handoff"] = _handoff_name(args)
     build_s = time.perf_counter() - t0
     cfg["build_s"] = round(build_s, 3)
     if args.bsdf == "mlp":   # the surrogate is trained once, before and outside the timed steps
@@ -338,7 +355,10 @@ def run(args):
             [("ddm_mlp", "ddm", "mlp", None)]
         other.append(("megakernel_exact", "megakernel", "exact", dict(grid=(1, 1, 1))))
         if args.method == "ddm" and not args.single_arm and not args.continue_cells:
-            # the same grid with the lane carrying rays across subdomain faces, and no split at all
+            # the same grid with the neighbour-queue hand-off in every wave, with the lane
+            # carrying rays across every face from the first wave, and no split at all
+            if args.handoff_waves:
+                other.append(("ddm_queue_every_wave_" + args.bsdf, "ddm", args.bsdf, dict(grid=grid)))
             other.append(("ddm_continue_cells_" + args.bsdf, "ddm", args.bsdf, dict(grid=grid, continue_cells=True)))
             other.append(("ddm_grid_1x1x1_" + args.bsdf, "ddm", args.bsdf, dict(grid=(1, 1, 1))))
         for name, method, bsdf, opts in other:
@@ -386,7 +406,10 @@ def run(args):
         import hashlib
         with open(os.path.join(ROOT, "profiles", "trace_traffic.json")) as f:
             tt = json.load(f)
+        # a capture counts for the hand-off schedule it was taken with
         ent = tt.get(f"{args.method}:{cfg['workload']}")
+        if ent and ent.get("ddm_handoff", "neighbour queue") != cfg["ddm_handoff"]:
+            ent = None
         if ent and ent.get("valid", False):
             m = hashlib.sha256()
             for src in ent["sources"]:
@@ -428,8 +451,8 @@ def run(args):
         line["image_rel_rmse_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     # the second workload runs with the default hotel-room configuration only
     default_run = (args.width, args.height, args.spp, args.method, args.bsdf, args.grid, args.single_arm,
-                   args.continue_cells, args.facade_renders, args.facade_spp) == \
-        (512, 512, 16, "ddm", "mlp", None, False, False, 16, 64)
+                   args.continue_cells, args.handoff_waves, args.facade_renders, args.facade_spp) == \
+        (512, 512, 16, "ddm", "mlp", None, False, False, 1, 16, 64)
     if not args.no_facade and world == 1 and default_run:
         del ctx, out, image
         torch.cuda.empty_cache()
@@ -473,7 +496,8 @@ def facade_leg(local, stream, flush, args):
     ctx = sddm.Context(local, stream)
     ctx.set_scene(scene)
     t0 = time.perf_counter()
-    ctx.build(grid=grid)
+    ctx.build(grid=grid, handoff_waves=args.handoff_waves)
+    cfg["ddm_handoff"] = _handoff_name(args)
     cfg["build_s"] = round(time.perf_counter() - t0, 3)
     train = ctx.mlp_train(scene.glass_materials()[0], seed=7)
     cfg["surrogate_training"] = {k: (round(v, 6) if isinstance(v, float) else v) for k, v in train.items()}
@@ -508,6 +532,15 @@ def facade_leg(local, stream, flush, args):
     ctx.render_into(one, scratch, method="ddm", bsdf="exact")
     am, ast = _timed_steps(ctx, one, scratch, "ddm", "exact", 1, flush, stream, batch=True)
     arms["ddm_exact_render0_64spp"] = round(_segs(ast[0]) / (am[0] / 1e3) / 1e6, 3)
+    if args.handoff_waves and not args.single_arm:   # render 0 with the queue hand-off in every wave
+        qc = sddm.Context(local, stream)
+        qc.set_scene(scene)
+        qc.build(grid=grid)
+        qc.mlp_train(scene.glass_materials()[0], seed=7)
+        qc.render_into(one, scratch, method="ddm", bsdf="mlp")
+        am, ast = _timed_steps(qc, one, scratch, "ddm", "mlp", 1, flush, stream, batch=True)
+        arms["ddm_mlp_queue_every_wave_render0_64spp"] = round(_segs(ast[0]) / (am[0] / 1e3) / 1e6, 3)
+        qc.close()
     mk = sddm.Context(local, stream)
     mk.set_scene(scene)
     mk.build(grid=(1, 1, 1))
@@ -587,6 +620,9 @@ def main():
     ap.add_argument("--spp", type=int, default=16)
     ap.add_argument("--continue-cells", action="store_true",
                     help="DDM: the tracing lane carries a ray on into the neighbouring subdomain (one wave per bounce)")
+    ap.add_argument("--handoff-waves", type=int, default=1,
+                    help="DDM: waves of neighbour-queue hand-off per bounce before one wave in which the thread "
+                         "carries the remaining rays across faces (0: hand-off in every wave)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("GX", "GY", "GZ"),
                     help="subdomain grid of the DDM arm (default 4 4 2, the hotel-room configuration)")
     args = ap.parse_args()

@@ -85,6 +85,12 @@ typedef struct {
                                  hand-off through the neighbour's queue); results are identical. 0 = the
                                  ray record is handed to the neighbour's queue for the next wave (Sec. 5's
                                  interface exchange). Not with cell_cache_bytes */
+    int handoff_waves;        /* with continue_cells = 0: 0 = every wave of a bounce hands the rays that leave
+                                 a subdomain to the neighbour's queue (dims x + y + z - 2 waves); k > 0 =
+                                 the first k waves do, then one more wave traces every remaining ray to its
+                                 end, the thread carrying it across subdomain faces (the few rays that
+                                 cross many faces no longer cost a wave each); results are identical. Not
+                                 with cell_cache_bytes */
 } sddm_build_opts;
 
 typedef struct {
@@ -317,7 +323,9 @@ int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d,
                                        float radius, float caustic_radius, float alpha, sddm_stats *st,
                                        sddm_photon_stats *pst);
 
-/* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}), the
+/* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}) with its
+ * hand-off schedule (neighbour queues every wave, the thread carrying rays
+ * across faces, or two queue waves and then the thread), the
  * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per
  * chunk ({2^21, 2^22, 2^23}; the ray queues are sized from it, two rays per
  * path, so they cannot overflow) for these renders, by timing short pilot

@@ -835,6 +835,20 @@ __global__ void k_finalize(KArgs a) {
     a.sample_xyz[3 * q + 2] = a.ps.acc[2 * np + q];
 }
 
+// Waves of one bounce: dims x + y + z - 2 with the neighbour-queue hand-off
+// (each wave moves every ray at least one cell along a monotone axis), one
+// when the lane carries rays across faces, handoff_waves + 1 for the mixed
+// schedule (hand-off waves, then one wave that carries the rest).
+static int ddm_waves(const DDMScene &g) {
+    const int full = std::max(1, g.dims[0] + g.dims[1] + g.dims[2] - 2);
+    if (g.continue_cells) return 1;
+    return g.handoff_waves > 0 ? std::min(g.handoff_waves + 1, full) : full;
+}
+// Whether the lane carries rays across faces in wave w of `waves`.
+static int ddm_wave_continues(const DDMScene &g, int w, int waves) {
+    return g.continue_cells || (g.handoff_waves > 0 && w == waves - 1);
+}
+
 #include "ddm_photon.cuh"
 
 __global__ void k_image_probe() {}
@@ -984,7 +998,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
 
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
     const unsigned scatter_blocks = whole_waves(k_scatter, 256, 0, sm, (unsigned)sm * 4);
-    const int waves = run.g.continue_cells ? 1 : std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
+    const int waves = ddm_waves(run.g);
     const size_t ctl_bytes = 32 + 4 * (size_t)nb;
     const unsigned cont_blocks = whole_waves(k_shade_continue, 256, sizeof(int) * (size_t)nb, sm, path_blocks);
     // the glass count and gather passes share one partition of the path slots
@@ -1022,6 +1036,7 @@ static int trace_chunk(const DDMRun &run, const PhotonGridView &pmv, const Photo
     for (int b = 1; b <= run.max_depth + 1; ++b) {
         for (int w = 0; w < waves; ++w) {
             a.last_wave = w == waves - 1;
+            a.g.continue_cells = ddm_wave_continues(run.g, w, waves);
             DDM_CHECK(cudaMemsetAsync(Q.fill, 0, 4 * (size_t)nb, s));
             if (!cache) {
                 k_scatter<<<scatter_blocks, 256, 0, s>>>(a);

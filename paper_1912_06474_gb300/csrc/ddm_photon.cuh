@@ -348,7 +348,7 @@ int ddm_photon_pass(const DDMPhotonRun &run, DDMBuffers &buf, cudaStream_t s) {
     const unsigned path_blocks = (unsigned)std::min<int64_t>((np + 255) / 256, (int64_t)sm * 16);
     const int trace_blocks = sm * (run.blocks_per_sm > 0 ? run.blocks_per_sm : 8);
     const int scatter_blocks = sm * 4;
-    const int waves = run.g.continue_cells ? 1 : std::max(1, run.g.dims[0] + run.g.dims[1] + run.g.dims[2] - 2);
+    const int waves = ddm_waves(run.g);
     const size_t ctl_bytes = 32 + 4 * (size_t)nb;
     const size_t bins_smem = sizeof(int) * (size_t)nb;
     cudaError_t e;
@@ -367,6 +367,7 @@ int ddm_photon_pass(const DDMPhotonRun &run, DDMBuffers &buf, cudaStream_t s) {
             PM_CHECK(cudaGetLastError());
             PM_CHECK(cudaMemsetAsync(Q.ctl, 0, ctl_bytes, s));
             a.last_wave = w == waves - 1;
+            a.g.continue_cells = ddm_wave_continues(run.g, w, waves);
             k_trace_wave<false><<<trace_blocks, 128, 0, s>>>(a);
             PM_CHECK(cudaGetLastError());
             *run.launches += 2;

@@ -389,6 +389,9 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: cell_cache_bytes and bvh_in_host_memory exclude each other");
     if (o.continue_cells < 0 || o.continue_cells > 1 || (o.continue_cells && o.cell_cache_bytes > 0))
         return fail(SDDM_ERR_INVALID_ARG, "sddm_build: continue_cells is 0 or 1, and not with cell_cache_bytes");
+    if (o.handoff_waves < 0 || (o.handoff_waves > 0 && (o.continue_cells || o.cell_cache_bytes > 0)))
+        return fail(SDDM_ERR_INVALID_ARG,
+                    "sddm_build: handoff_waves >= 0, and not with continue_cells or cell_cache_bytes");
     // every mesh material must exist (the material list may have changed since set_mesh)
     for (uint32_t m : ctx->mat_id)
         if (m >= ctx->mats.size()) return fail(SDDM_ERR_INVALID_ARG, "sddm_build: mesh references a missing material");
@@ -598,6 +601,7 @@ int sddm_build(sddm_ctx *ctx, const sddm_build_opts *opts) {
     g.n_oct = (SDDM_MAX_SUBBINS >= 64 && 128 * g.n_cells <= kMaxBins) ? 64 : (SDDM_MAX_SUBBINS >= 8 && 16 * g.n_cells <= kMaxBins) ? 8 : 1;
     g.n_bins = 2 * g.n_cells * g.n_oct;
     g.continue_cells = o.continue_cells;
+    g.handoff_waves = o.handoff_waves;
     ctx->cache.release();
     if (o.cell_cache_bytes > 0) {
         // subdomains loaded into a device cache of that many bytes as their queues fill
@@ -1346,14 +1350,17 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
     const int bps_list[] = {4, 8, 16};
     double best_rate = -1.0;
     sddm_build_opts chosen = base;
-    for (int trial = 0; trial < 2 * (int)(sizeof grids / sizeof grids[0]); ++trial) {
+    for (int trial = 0; trial < 3 * (int)(sizeof grids / sizeof grids[0]); ++trial) {
         if (rc != SDDM_OK) break;
-        const int *gdim = grids[trial / 2];
-        const int cont = trial % 2;   // hand-off through the neighbour's queue, or the lane continues
-        if (cont && ((gdim[0] == 1 && gdim[1] == 1 && gdim[2] == 1) || base.cell_cache_bytes > 0)) continue;
+        const int *gdim = grids[trial / 3];
+        // hand-off schedule: the neighbour's queue every wave (0), the lane carries
+        // rays across faces (1), or two queue waves and then the lane (2)
+        const int sched = trial % 3;
+        if (sched && ((gdim[0] == 1 && gdim[1] == 1 && gdim[2] == 1) || base.cell_cache_bytes > 0)) continue;
         sddm_build_opts o = base;
         for (int a = 0; a < 3; ++a) o.grid[a] = gdim[a];
-        o.continue_cells = cont;
+        o.continue_cells = sched == 1;
+        o.handoff_waves = sched == 2 ? 2 : 0;
         if ((rc = sddm_build(ctx, &o)) != SDDM_OK) break;
         for (int bps : bps_list) {
             ctx->opts.blocks_per_sm = bps;

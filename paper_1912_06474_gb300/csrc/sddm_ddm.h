@@ -36,6 +36,8 @@ struct DDMScene {
     const int *root;      // [n_cells] root node of each cell
     int64_t node_cap, tri_cap;   // node and triangle records addressable from nodes / tris
     int continue_cells;   // 1: a ray leaving a cell is carried on by the same lane (one wave per bounce)
+    int handoff_waves;    // > 0: waves of neighbour-queue hand-off per bounce before a last wave in which the
+                          // lane carries every remaining ray on (continue_cells 0)
     // per cell: bounding planes (x-, x+, y-, y+), (z-, z+, -, -) and the
     // neighbours across those faces (-1 outside the grid), 2 entries each
     const float4 *cell_planes;

@@ -45,7 +45,8 @@ class SddmError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("grid", C.c_int * 3), ("leaf_size", C.c_int), ("sah_bins", C.c_int),
                 ("queue_capacity", C.c_int64), ("blocks_per_sm", C.c_int), ("paths_in_flight", C.c_int64),
-                ("bvh_in_host_memory", C.c_int), ("cell_cache_bytes", C.c_int64), ("continue_cells", C.c_int)]
+                ("bvh_in_host_memory", C.c_int), ("cell_cache_bytes", C.c_int64), ("continue_cells", C.c_int),
+                ("handoff_waves", C.c_int)]
 
 
 class MlpTrainOpts(C.Structure):
@@ -231,10 +232,11 @@ class Context:
         self.n_mat = len(scene.materials)
 
     def build(self, grid=(1, 1, 1), leaf_size=4, sah_bins=16, queue_capacity=0, blocks_per_sm=0,
-              paths_in_flight=0, bvh_in_host_memory=False, cell_cache_bytes=0, continue_cells=False):
+              paths_in_flight=0, bvh_in_host_memory=False, cell_cache_bytes=0, continue_cells=False,
+              handoff_waves=0):
         o = BuildOpts((C.c_int * 3)(*grid), leaf_size, sah_bins, queue_capacity, blocks_per_sm,
                       paths_in_flight, 1 if bvh_in_host_memory else 0, int(cell_cache_bytes),
-                      1 if continue_cells else 0)
+                      1 if continue_cells else 0, int(handoff_waves))
         _check(lib.sddm_build(self._h, C.byref(o)))
         self.build_opts = o
 
@@ -361,7 +363,8 @@ class Context:
         return dict(grid=tuple(best.grid), leaf_size=best.leaf_size, sah_bins=best.sah_bins,
                     queue_capacity=best.queue_capacity, blocks_per_sm=best.blocks_per_sm,
                     paths_in_flight=best.paths_in_flight, bvh_in_host_memory=bool(best.bvh_in_host_memory),
-                    cell_cache_bytes=best.cell_cache_bytes, continue_cells=bool(best.continue_cells))
+                    cell_cache_bytes=best.cell_cache_bytes, continue_cells=bool(best.continue_cells),
+                    handoff_waves=best.handoff_waves)
 
     def set_profiling(self, time_trace=False, count_traversal=False, eager=False, test_mlp_timeout=False):
         """sddm_set_profiling: per-launch trace-kernel events, traversal counters,

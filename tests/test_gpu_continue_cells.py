@@ -1,9 +1,10 @@
 """A ray that leaves its subdomain without a hit is either handed to the
 neighbour's queue for the next wave (Sec. 5's interface exchange) or carried
-on by the same lane into the neighbour's BVH within the wave. The two
-schedules trace each ray through the same subdomains with the same hit
-windows, so images, segment and crossing counts are identical; the
-throughput of both is printed."""
+on by the same lane into the neighbour's BVH within the wave; the mixed
+schedule hands rays over for the first waves of a bounce and then carries
+the rest. All schedules trace each ray through the same subdomains with the
+same hit windows, so images, segment and crossing counts are identical; the
+throughput of each is printed."""
 import pytest
 
 from paper_1912_06474_gb300 import scenes
@@ -11,6 +12,10 @@ from paper_1912_06474_gb300 import scenes
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA device")]
+
+SCHEDULES = {"queue hand-off": {}, "lane continues": dict(continue_cells=True),
+             "1 queue wave, then the lane": dict(handoff_waves=1),
+             "2 queue waves, then the lane": dict(handoff_waves=2)}
 
 
 @pytest.mark.parametrize("which,grid", [("tiny", (2, 2, 2)), ("hotel", (4, 4, 2))])
@@ -25,16 +30,22 @@ def test_continue_across_cells_matches_queue_handoff(which, grid):
     ctx = sddm.Context(0)
     ctx.set_scene(sc)
     out, st, rate = {}, {}, {}
-    for cont in (False, True):
-        ctx.build(grid=grid, continue_cells=cont)
+    for name, opts in SCHEDULES.items():
+        ctx.build(grid=grid, **opts)
         ctx.render([spec], method="ddm")
         imgs, s = ctx.render([spec], method="ddm")
-        out[cont], st[cont] = imgs[0].clone(), s
-        rate[cont] = (s["segments_ext"] + s["segments_shadow"]) / (s["gpu_ms"] * 1e3)
-    print(f"{which} {grid}: queue hand-off {rate[False]:.0f} Mseg/s, lane continues {rate[True]:.0f} Mseg/s")
-    assert torch.equal(out[False], out[True])
-    for k in ("segments_ext", "segments_shadow", "crossings", "glass_queries"):
-        assert st[False][k] == st[True][k], k
+        out[name], st[name] = imgs[0].clone(), s
+        rate[name] = (s["segments_ext"] + s["segments_shadow"]) / (s["gpu_ms"] * 1e3)
+    print(f"{which} {grid}: " + ", ".join(f"{k} {v:.0f} Mseg/s" for k, v in rate.items()))
+    ref = "queue hand-off"
+    for name in SCHEDULES:
+        assert torch.equal(out[ref], out[name]), name
+        for k in ("segments_ext", "segments_shadow", "crossings", "glass_queries"):
+            assert st[ref][k] == st[name][k], (name, k)
     with pytest.raises(sddm.SddmError):
         ctx.build(grid=grid, continue_cells=True, cell_cache_bytes=1 << 30)
+    with pytest.raises(sddm.SddmError):
+        ctx.build(grid=grid, handoff_waves=2, cell_cache_bytes=1 << 30)
+    with pytest.raises(sddm.SddmError):
+        ctx.build(grid=grid, handoff_waves=2, continue_cells=True)
     ctx.close()
