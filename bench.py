@@ -395,7 +395,7 @@ def run(args):
     visits, crossings = cst["ray_visits"], cst["crossings"]
     n_ext = cst["segments_ext"]
     if args.method == "ddm":
-        bytes_step = (48 * visits + 48 * crossings + 32 * n_ext + 64 * cst["node_visits"] + 48 * cst["tri_tests"])
+        bytes_step = _trace_bytes(cst)
     else:   # megakernel: per segment a 16 B hit record, node and triangle fetches
         bytes_step = 16 * n_ext + 64 * cst["node_visits"] + 48 * cst["tri_tests"]
     trace_s = trace_ms / 1e3 / args.steps
@@ -436,7 +436,8 @@ def run(args):
                      "trace_ms_per_step": round(trace_ms / args.steps, 4),
                      "trace_launches_per_step": trace_launches // args.steps,
                      "nodes_per_visit": round(cst["node_visits"] / max(visits, 1), 2),
-                     "tris_per_visit": round(cst["tri_tests"] / max(visits, 1), 2)},
+                     "tris_per_visit": round(cst["tri_tests"] / max(visits, 1), 2),
+                     "crossings": crossings, "crossings_carried_by_thread": cst.get("ray_continues", 0)},
         "value_eager": round(eager_segs / (eager_total / 1e3) / 1e6, 3),
         "arms": arm_vals,
         "segments_per_step": segs // (args.steps * world), "clocks": clk,
@@ -468,10 +469,13 @@ FACADE_WORKLOAD = "facade_room_5M_tris_16x1920x1080_64spp_d8_L81_ddm8x8x4_mlp"
 
 def _trace_bytes(cst):
     """Algorithmic bytes of the DDM trace kernel for the counted render: ray
-    record reads (48 B per visit), hand-offs (48 B), hit records (32 B per
-    extension segment), node (64 B) and triangle (48 B) fetches."""
-    return (48 * cst["ray_visits"] + 48 * cst["crossings"] + 32 * cst["segments_ext"] + 64 * cst["node_visits"]
-            + 48 * cst["tri_tests"])
+    record reads (48 B per visit that starts from a queue), hand-offs through a
+    queue (48 B), hit records (32 B per extension segment), node (64 B) and
+    triangle (48 B) fetches. A crossing the tracing thread carries on itself
+    moves no ray record."""
+    cont = cst.get("ray_continues", 0)
+    return (48 * (cst["ray_visits"] - cont) + 48 * (cst["crossings"] - cont) + 32 * cst["segments_ext"]
+            + 64 * cst["node_visits"] + 48 * cst["tri_tests"])
 
 
 def facade_leg(local, stream, flush, args):
@@ -571,7 +575,8 @@ def facade_leg(local, stream, flush, args):
                      "bytes_sample": tbytes, "trace_ms_sample": round(tst["trace_ms"], 3),
                      "trace_launches_sample": tst["trace_launches"],
                      "nodes_per_visit": round(cst["node_visits"] / max(cst["ray_visits"], 1), 2),
-                     "tris_per_visit": round(cst["tri_tests"] / max(cst["ray_visits"], 1), 2)},
+                     "tris_per_visit": round(cst["tri_tests"] / max(cst["ray_visits"], 1), 2),
+                     "crossings": cst["crossings"], "crossings_carried_by_thread": cst.get("ray_continues", 0)},
         "clocks": clk,
     }
     del ctx

@@ -138,6 +138,8 @@ typedef struct {
     int64_t cache_bytes_loaded; /* ... bytes copied from host memory */
     double mlp_ms;            /* SDDM_PROFILE_TIME_TRACE: summed device time of the surrogate network kernel */
     int64_t mlp_rows;         /* (query, bin) rows the surrogate network evaluated */
+    int64_t ray_continues;    /* SDDM_PROFILE_COUNT_TRAVERSAL: crossings the tracing thread carried on itself
+                                 (continue_cells, handoff_waves): no ray record staged or read back */
 } sddm_stats;
 
 /* Profiling switches (sddm_set_profiling), off by default. */

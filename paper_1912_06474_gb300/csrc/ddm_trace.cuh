@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t np = a.ps.np;
-    unsigned long long n_cross = 0, n_vis = 0;
+    unsigned long long n_cross = 0, n_vis = 0, n_cont = 0;   // n_cont: crossings carried on by the lane
     TravCount tc;
 
     __shared__ float4 s_push[128 / 32][3 * kPushBuf];   // per-warp hand-off buffers
@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
                 tw = (rfl & kRayShadow) ? fminf(t_exit + g.eps, t_max) : t_exit + g.eps;
                 ++n_cross;
                 ++n_vis;
+                if (COUNT) ++n_cont;
                 done = true;
                 fin = false;
             } else {
@@ -415,5 +416,7 @@ __global__ void __launch_bounds__(128, SDDM_TRACE_MIN_BLOCKS) k_trace_wave(KArgs
     if (COUNT) {
         __syncthreads();
         block_count3(a.counters + 5, tc.nodes, a.counters + 6, tc.tris, a.counters + 7, n_vis);
+        __syncthreads();   // the reduction's shared slots are read by thread 0 above
+        block_count3(a.counters + 10, n_cont, nullptr, 0, nullptr, 0);
     }
 }

@@ -1012,6 +1012,7 @@ int sddm_render(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_stats *st)
         st->node_visits = count_trav ? (int64_t)cnt[5] : 0;
         st->tri_tests = count_trav ? (int64_t)cnt[6] : 0;
         st->ray_visits = count_trav ? (int64_t)cnt[7] : 0;
+        st->ray_continues = count_trav ? (int64_t)cnt[10] : 0;
         double tms = 0.0;
         for (int k = 0; k + 1 < ctx->ddm_buf.events_used; k += 2) {
             float x = 0.f;

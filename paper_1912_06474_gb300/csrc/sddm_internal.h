@@ -13,7 +13,8 @@ namespace sddm {
 
 // Statistics counters of a render call, u64 each (layout at DevScene users'
 // `counters` fields): ext, shadow, glass, crossings, fallbacks, nodes, tris,
-// visits, surrogate batches, surrogate rows; the rest spare.
+// visits, surrogate batches, surrogate rows, crossings carried on by the
+// tracing thread; the rest spare.
 constexpr int kNumCounters = 16;
 
 constexpr int kMaxL = 256;

@@ -81,7 +81,7 @@ class Stats(C.Structure):
                 ("trace_launches", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("ray_visits", C.c_int64), ("mlp_batches", C.c_int64), ("cache_loads", C.c_int64),
                 ("cache_hits", C.c_int64), ("cache_bytes_loaded", C.c_int64), ("mlp_ms", C.c_double),
-                ("mlp_rows", C.c_int64)]
+                ("mlp_rows", C.c_int64), ("ray_continues", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

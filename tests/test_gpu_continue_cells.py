@@ -49,3 +49,28 @@ def test_continue_across_cells_matches_queue_handoff(which, grid):
     with pytest.raises(sddm.SddmError):
         ctx.build(grid=grid, handoff_waves=2, continue_cells=True)
     ctx.close()
+
+
+def test_carried_crossings_are_counted():
+    """The counting trace kernel splits interface crossings into hand-offs
+    through a neighbour's queue and crossings the tracing thread carries on
+    itself: none carried with the queue in every wave, all of them with the
+    lane carrying rays from the first wave, some with one queue wave."""
+    from paper_1912_06474_gb300 import sddm
+    sc = scenes.hotel_room(L=41, seed=0)
+    spec = scenes.hotel_room_render(sc, 128, 128, 4, 5, seed=0)
+    ctx = sddm.Context(0)
+    ctx.set_scene(sc)
+    ctx.set_profiling(count_traversal=True)
+    got = {}
+    for name, opts in (("queue", {}), ("lane", dict(continue_cells=True)), ("mixed", dict(handoff_waves=1))):
+        ctx.build(grid=(4, 4, 2), **opts)
+        _, s = ctx.render([spec], method="ddm")
+        got[name] = (s["crossings"], s["ray_continues"])
+    ctx.close()
+    crossings = got["queue"][0]
+    assert crossings > 0 and all(c == crossings for c, _ in got.values())
+    assert got["queue"][1] == 0
+    assert got["lane"][1] == crossings
+    assert 0 < got["mixed"][1] < crossings
+    print("crossings", crossings, "carried by the thread with one queue wave:", got["mixed"][1])
