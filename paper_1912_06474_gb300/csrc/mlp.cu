@@ -142,13 +142,20 @@ constexpr int kChB = 10;              // layers 2, 3 B: K = 64 + bias step
 constexpr uint32_t kMbarTries = 1u << 22;   // bounded waits: ~seconds, then the CTA reports and stops
 constexpr uint32_t kMbarTriesTest = 1u << 10;   // the failure-path test's wait on an MMA never issued
 
-struct __align__(128) TcSmem {
-    __nv_bfloat16 a[kTcRows * kChA * 8];    // activations / inputs, K-major core matrices
-    __nv_bfloat16 b1[H * kChB1 * 8];
-    __nv_bfloat16 b2[H * kChB * 8], b3[H * kChB * 8];
+// The weights in the CTA's operand layout, packed once in global memory
+// (k_mlp_pack, after every change of the parameters) and copied into each
+// CTA's shared memory by one bulk TMA copy.
+struct __align__(128) TcWeights {
+    __nv_bfloat16 b1[H * kChB1 * 8];        // B of layer 1: W1 / 2 twice, b1 / 2 as hi + lo
+    __nv_bfloat16 b2[H * kChB * 8], b3[H * kChB * 8];   // W / 2, bias / 2 as hi + lo in K columns 64, 65
     float w4[2][H];                         // BF16-rounded output weights (FP32 layer 4)
     float b4[2];
-    unsigned long long mbar;
+};
+static_assert(sizeof(TcWeights) % 16 == 0, "bulk copies move multiples of 16 bytes");
+struct __align__(128) TcSmem {
+    TcWeights w;
+    __nv_bfloat16 a[kTcRows * kChA * 8];    // activations / inputs, K-major core matrices
+    unsigned long long mbar, mbar_w;        // MMA completion; weights arrived
     uint32_t tmem;
 };
 
@@ -236,9 +243,9 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
 // SiLU of z given h = z / 2.
 __device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
 
-// Weights into the CTA's operand layout (once per CTA), and the constant
-// bias chunks of every A row.
-__device__ void tc_load_weights(TcSmem &s, const float *__restrict__ p) {
+// The FP32 parameters into the operand layout of TcWeights (one CTA).
+__global__ void __launch_bounds__(256) k_mlp_pack(const float *__restrict__ p, TcWeights *out) {
+    TcWeights &s = *out;
     for (int i = threadIdx.x; i < H * kChB * 8; i += blockDim.x) {
         const int n = i / (kChB * 8), k = i % (kChB * 8);
         float v2 = 0.0f, v3 = 0.0f;
@@ -267,11 +274,20 @@ __device__ void tc_load_weights(TcSmem &s, const float *__restrict__ p) {
     }
     for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) s.w4[i / H][i % H] = bf16r(p[OFF_W4 + i]);
     if (threadIdx.x < 2) s.b4[threadIdx.x] = p[OFF_B4 + threadIdx.x];
-    // A columns 64..79 of every row: [1, 1, 0, ...] against the biases' two parts
+}
+
+// A columns 64..79 of every row: [1, 1, 0, ...] against the biases' two parts.
+__device__ void tc_put_bias_columns(TcSmem &s) {
     for (int i = threadIdx.x; i < kTcRows * 16; i += blockDim.x) {
         const int r = i >> 4, k = 64 + (i & 15);
         s.a[kmaj(r, k, kChA)] = __float2bfloat16_rn(k < 66 ? 1.0f : 0.0f);
     }
+}
+
+// Byte offset of the packed image behind the FP32 parameters in one buffer.
+constexpr size_t kImageOffset = (kMlpParams * sizeof(float) + 127) / 128 * 128;
+__device__ __forceinline__ const TcWeights *weight_image(const float *params) {
+    return reinterpret_cast<const TcWeights *>(reinterpret_cast<const char *>(params) + kImageOffset);
 }
 
 // This thread's row of layer-1 A: [x_hi | x_lo], then [1, 1, 0 ...].
@@ -417,28 +433,43 @@ template <bool FILMS>
 __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
     __shared__ TcSmem s;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t mbar = smem_addr(&s.mbar);
+    const uint32_t mbar = smem_addr(&s.mbar), mbar_w = smem_addr(&s.mbar_w);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s.tmem)),
                      "r"((uint32_t)kTcCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) mbar_init(mbar);
-    tc_load_weights(s, a.params);
+    if (tid == 0) {
+        mbar_init(mbar);
+        mbar_init(mbar_w);
+    }
+    __syncthreads();
+    // the packed weights by one bulk copy (the TMA engine), completion on mbar_w
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_w),
+                     "r"((uint32_t)sizeof(TcWeights))
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(&s.w)),
+                     "l"(weight_image(a.params)), "r"((uint32_t)sizeof(TcWeights)), "r"(mbar_w)
+                     : "memory");
+    }
+    tc_put_bias_columns(s);
+    const bool w_ok = mbar_wait(mbar_w, 0u, kMbarTries);
     fence_async_smem();
     tc_fence_before();
-    __syncthreads();
+    const bool w_failed = __syncthreads_or(!w_ok) != 0;
     tc_fence_after();
     const uint32_t tmem = s.tmem;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
-    const uint32_t sa = smem_addr(s.a), sb1 = smem_addr(s.b1), sb2 = smem_addr(s.b2), sb3 = smem_addr(s.b3);
+    const uint32_t sa = smem_addr(s.a), sb1 = smem_addr(s.w.b1), sb2 = smem_addr(s.w.b2), sb3 = smem_addr(s.w.b3);
     constexpr uint32_t kSboA = kChA * 128, kSboB1 = kChB1 * 128, kSboB = kChB * 128;
     const int64_t total = mlp_total_rows(a);
     const int64_t n_tiles = (total + kTcRows - 1) / kTcRows;
     if (a.rows && blockIdx.x == 0 && tid == 0) atomicAdd(a.rows, (unsigned long long)total);
     uint32_t phase = 0;
-    bool failed = false;   // this thread's wait on the tensor core ran out
+    bool failed = w_failed;   // this thread's wait on the tensor core (or on the weights) ran out
     // failure-path test: CTA 0 issues nothing, so its first wait runs out
     const bool skip = a.test_timeout && blockIdx.x == 0;
     const uint32_t tries = skip ? kMbarTriesTest : kMbarTries;
@@ -485,12 +516,12 @@ __global__ void __launch_bounds__(kTcRows, SDDM_MLP_MINB) k_mlp_net(MlpRows a) {
         tc_put_hidden(s, tid, v);
         if (!layer(3)) break;
         tmem_ld64(taddr, v);
-        float y0 = s.b4[0], y1 = s.b4[1];
+        float y0 = s.w.b4[0], y1 = s.w.b4[1];
 #pragma unroll
         for (int j = 0; j < H; ++j) {
             const float h = silu_h(v[j]);
-            y0 = fmaf(s.w4[0][j], h, y0);
-            y1 = fmaf(s.w4[1][j], h, y1);
+            y0 = fmaf(s.w.w4[0][j], h, y0);
+            y1 = fmaf(s.w.w4[1][j], h, y1);
         }
         const float2 y = make_float2(out_to_rt(y0), out_to_rt(y1));
         if (valid) {
@@ -1028,6 +1059,14 @@ cudaError_t launch_mlp_adam(float *params, float *m, float *v, const float *grad
 cudaError_t launch_mlp_data(const DevScene &sc, uint32_t mat, float, int64_t n, uint32_t seed, float dmin, float dmax,
                             float *X, float *Y, cudaStream_t stream) {
     k_mlp_data<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(sc, mat, n, seed, dmin, dmax, X, Y);
+    return cudaGetLastError();
+}
+
+size_t mlp_param_buffer_bytes() { return kImageOffset + sizeof(TcWeights); }
+
+cudaError_t launch_mlp_pack(float *params, cudaStream_t stream) {
+    k_mlp_pack<<<1, 256, 0, stream>>>(params, reinterpret_cast<TcWeights *>(reinterpret_cast<char *>(params) +
+                                                                           kImageOffset));
     return cudaGetLastError();
 }
 

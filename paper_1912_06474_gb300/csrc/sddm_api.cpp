@@ -1421,7 +1421,8 @@ static int mlp_net_for(sddm_ctx *ctx, uint32_t mat, bool create, sddm_ctx::MlpNe
         id = (int)ctx->nets.size() - 1;
         cudaError_t e;
         sddm_ctx::MlpNet &n = *ctx->nets.back();
-        if ((e = n.params.ensure(kMlpParams * 4)) || (e = n.m.ensure(kMlpParams * 4)) || (e = n.v.ensure(kMlpParams * 4)))
+        if ((e = n.params.ensure(mlp_param_buffer_bytes())) || (e = n.m.ensure(kMlpParams * 4)) ||
+            (e = n.v.ensure(kMlpParams * 4)))
             return cuda_fail(e, "surrogate: allocation");
         for (size_t m = 0; m < ctx->mats.size(); ++m)
             if (same_curves(ctx->mats[m], ctx->mats[mat]) && ctx->net_of_mat[m] < 0) ctx->net_of_mat[m] = id;
@@ -1496,8 +1497,8 @@ int sddm_mlp_train(sddm_ctx *ctx, uint32_t mat, const sddm_mlp_train_opts *opts,
     }
     if ((e = cudaEventRecord(ctx->ev1, s))) return cuda_fail(e, "sddm_mlp_train: event");
     unsigned int *errs = reinterpret_cast<unsigned int *>(ctx->mlp_scalar.as<char>() + 16);
-    if ((e = ctx->d_err.ensure(16)) || (e = cudaMemsetAsync(ctx->d_err.p, 0, 16, s)) ||
-        (e = cudaMemsetAsync(errs, 0, 8, s)) ||
+    if ((e = launch_mlp_pack(net->params.as<float>(), s)) || (e = ctx->d_err.ensure(16)) ||
+        (e = cudaMemsetAsync(ctx->d_err.p, 0, 16, s)) || (e = cudaMemsetAsync(errs, 0, 8, s)) ||
         (e = launch_mlp_grid_error(net->params.as<float>(), ctx->dev, mat, o.thick_min, o.thick_max, errs,
                                    ctx->d_err.as<int>(), ctx->sm_count, s)))
         return cuda_fail(e, "sddm_mlp_train: held-out error");
@@ -1551,6 +1552,7 @@ int sddm_mlp_set_weights(sddm_ctx *ctx, uint32_t mat, const float *params, float
     int rc = mlp_net_for(ctx, mat, true, &net);
     if (rc != SDDM_OK) return rc;
     cudaError_t e = cudaMemcpyAsync(net->params.p, params, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_mlp_pack(net->params.as<float>(), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(net->m.p, 0, kMlpParams * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(net->v.p, 0, kMlpParams * 4, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -1604,6 +1606,7 @@ int sddm_mlp_load(sddm_ctx *ctx, uint32_t mat, const char *path) {
     int rc = mlp_net_for(ctx, mat, true, &net);
     if (rc != SDDM_OK) return rc;
     cudaError_t e = cudaMemcpyAsync(net->params.p, buf.data(), kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = launch_mlp_pack(net->params.as<float>(), ctx->stream);
     if (!e) e = cudaMemcpyAsync(net->m.p, buf.data() + kMlpParams, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
     if (!e) e = cudaMemcpyAsync(net->v.p, buf.data() + 2 * kMlpParams, kMlpParams * 4, cudaMemcpyHostToDevice, ctx->stream);
     if (!e) e = cudaStreamSynchronize(ctx->stream);

@@ -64,6 +64,11 @@ cudaError_t launch_mlp_adam(float *params, float *m, float *v, const float *grad
 cudaError_t launch_mlp_data(const DevScene &sc, uint32_t mat, float state_unused, int64_t n, uint32_t seed,
                             float thick_min, float thick_max, float *X, float *Y, cudaStream_t stream);
 cudaError_t launch_mlp_init(float *params, uint32_t seed, cudaStream_t stream);
+// The parameter buffer holds the FP32 parameters and, behind them, the weights
+// packed in the inference kernel's tensor-core operand layout; launch_mlp_pack
+// rewrites the packed copy from the parameters (after every change of them).
+size_t mlp_param_buffer_bytes();
+cudaError_t launch_mlp_pack(float *params, cudaStream_t stream);
 cudaError_t launch_mlp_grid_error(const float *params, const DevScene &sc, uint32_t mat, float thick_min,
                                   float thick_max, unsigned int *max_err2, int *err, int sm_count,
                                   cudaStream_t stream);

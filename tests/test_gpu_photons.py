@@ -244,3 +244,28 @@ def test_progressive_photon_map(oracle_mod, sddm, method, grid):
     print(f"\n  progressive {method}: {passes} passes, {pst['photons']} photons, rel-RMSE {err:.2e}")
     assert pst["photons"] == passes * n
     assert err <= 1e-3
+
+
+def test_photon_pass_hand_off_schedules_agree(sddm):
+    """The photon pass runs through the same subdomain waves as camera paths:
+    with the neighbour queue in every wave, with one queue wave and then the
+    tracing thread, and with the thread from the first wave, the photons take
+    the same paths (equal stored counts and photon segments). The images agree
+    to float rounding: the photons of a grid cell are gathered in the order the
+    grid's scatter placed them, which atomic appends leave open."""
+    sc = scenes.tiny_room(L=16)
+    spec = scenes.RenderSpec(64, 48, 4, 5, seed=3, camera=sc.camera, nee=True)
+    out = {}
+    ctx = sddm.Context(0)
+    try:
+        ctx.set_scene(sc)
+        for name, opts in (("queue", {}), ("mixed", dict(handoff_waves=1)), ("lane", dict(continue_cells=True))):
+            ctx.build(grid=(2, 2, 2), **opts)
+            img, st, pst = ctx.render_photon_map(spec, 100000, 0.15, method="ddm")
+            out[name] = (img.clone(), pst["stored"], pst["photon_segments"])
+    finally:
+        ctx.close()
+    ref = out["queue"][0].cpu().numpy()
+    for name in ("mixed", "lane"):
+        assert out["queue"][1:] == out[name][1:], name
+        assert rel_rmse(out[name][0].cpu().numpy(), ref) <= 1e-6, name
