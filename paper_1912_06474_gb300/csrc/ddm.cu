@@ -667,7 +667,10 @@ __global__ void __launch_bounds__(256, SDDM_SHS_MINB) k_shade_spectral(KArgs a) 
             }
         }
     }
-    block_count3(a.counters + 2, n_glass, nullptr, 0, nullptr, 0);
+    // counted per warp (no block barrier at the end: warps whose paths had less
+    // work leave at once instead of waiting for the block's slowest warp)
+    for (int off = 16; off > 0; off >>= 1) n_glass += __shfl_down_sync(0xffffffffu, n_glass, off);
+    if ((threadIdx.x & 31) == 0 && n_glass) atomicAdd(a.counters + 2, n_glass);
 }
 
 // Continuation half of shading: next-event sample toward the lights and the
