@@ -500,7 +500,7 @@ def facade_leg(local, stream, flush, args):
     ctx = sddm.Context(local, stream)
     ctx.set_scene(scene)
     t0 = time.perf_counter()
-    ctx.build(grid=grid, handoff_waves=args.handoff_waves)
+    ctx.build(grid=grid, handoff_waves=args.handoff_waves, blocks_per_sm=args.blocks_per_sm)
     cfg["ddm_handoff"] = _handoff_name(args)
     cfg["build_s"] = round(time.perf_counter() - t0, 3)
     train = ctx.mlp_train(scene.glass_materials()[0], seed=7)
