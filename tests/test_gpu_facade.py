@@ -53,8 +53,9 @@ def test_facade_room(oracle_mod):
 
 def test_facade_full_configuration_batched_surrogate(oracle_mod):
     """The facade workload at its full size, in one call: 16 renders of
-    1920x1080 px at 64 spp, depth 8, 81 bins, DDM over 8x8x4 subdomains, the
-    glass of all 8 panes (one set of curves, each pane its own s) served by one
+    1920x1080 px at 64 spp, depth 8, 81 bins, DDM over 8x8x4 subdomains with
+    the benchmark's hand-off schedule (one neighbour-queue wave per bounce,
+    then the tracing thread carries the rest), the glass of all 8 panes (one set of curves, each pane its own s) served by one
     trained surrogate with probe and exact fallback; the same batch once more
     with the exact slab. Both are checked against the FP64 oracle on a seeded
     subset of 4096 pixels of every render (65,536 pixels):
@@ -73,7 +74,7 @@ def test_facade_full_configuration_batched_surrogate(oracle_mod):
     sc = scenes.facade_room(L=81, seed=0)
     ctx = sddm.Context(0)
     ctx.set_scene(sc)
-    ctx.build(grid=(8, 8, 4))
+    ctx.build(grid=(8, 8, 4), handoff_waves=1)
     rep = ctx.mlp_train(sc.glass_materials()[0], seed=7)
     specs = scenes.facade_renders(sc)   # 16 x 1920x1080 x 64 spp, depth 8
     assert len(specs) == 16 and specs[0].n_paths == 1920 * 1080 * 64
