@@ -406,7 +406,11 @@ int sddm_set_profiling(sddm_ctx *ctx, int flags);
 /* Glass slab R and T (Sec. 6, Fresnel equations) for n queries of glass
  * material `mat`: cos_theta[n] in [0,1], bin index bin[n] in [0,L), state
  * s[n], thickness_m[n]. All four inputs and R[n], T[n] are DEVICE arrays.
- * mode = sddm_bsdf_mode. */
+ * mode = sddm_bsdf_mode: the exact slab, or the trained surrogate network on
+ * the tensor cores with (SDDM_BSDF_MLP) or without (SDDM_BSDF_MLP_RAW) the
+ * per-batch probe and exact fallback. SDDM_ERR_MLP_UNTRAINED if the material
+ * has no network; SDDM_ERR_TIMEOUT if the network kernel's bounded wait on the
+ * tensor core ran out (the kernel stopped and freed its tensor memory). */
 int sddm_glass_eval(sddm_ctx *ctx, uint32_t mat, int n, const float *cos_theta, const int32_t *bin,
                     const float *s, const float *thickness_m, float *R, float *T, int mode);
 
