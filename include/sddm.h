@@ -327,7 +327,7 @@ int sddm_render_progressive_photon_map(sddm_ctx *ctx, const sddm_render_desc *d,
 
 /* Pick the subdomain grid ({1,1,1}, {2,2,2}, {4,4,2}, {8,4,4}) with its
  * hand-off schedule (neighbour queues every wave, the thread carrying rays
- * across faces, or two queue waves and then the thread), the
+ * across faces, or one queue wave and then the thread), the
  * persistent trace blocks per SM ({4, 8, 16}) and then the paths in flight per
  * chunk ({2^21, 2^22, 2^23}; the ray queues are sized from it, two rays per
  * path, so they cannot overflow) for these renders, by timing short pilot

@@ -1355,13 +1355,13 @@ int sddm_autotune(sddm_ctx *ctx, const sddm_render_desc *d, int n, sddm_build_op
         if (rc != SDDM_OK) break;
         const int *gdim = grids[trial / 3];
         // hand-off schedule: the neighbour's queue every wave (0), the lane carries
-        // rays across faces (1), or two queue waves and then the lane (2)
+        // rays across faces (1), or one queue wave and then the lane (2)
         const int sched = trial % 3;
         if (sched && ((gdim[0] == 1 && gdim[1] == 1 && gdim[2] == 1) || base.cell_cache_bytes > 0)) continue;
         sddm_build_opts o = base;
         for (int a = 0; a < 3; ++a) o.grid[a] = gdim[a];
         o.continue_cells = sched == 1;
-        o.handoff_waves = sched == 2 ? 2 : 0;
+        o.handoff_waves = sched == 2 ? 1 : 0;
         if ((rc = sddm_build(ctx, &o)) != SDDM_OK) break;
         for (int bps : bps_list) {
             ctx->opts.blocks_per_sm = bps;
